@@ -1,0 +1,139 @@
+/*
+ * apsp.h -- C ABI of libapsp.so: exact all-pairs shortest paths on dense n x n distance
+ * matrices over the (min,+) semiring, for NVIDIA GB300 (sm_103a).
+ *
+ * The problem (the paper, Sec. 2 and Sec. 3.1): given a cost matrix H whose entry [i][j] is
+ * the cost of the edge i -> j, produce d[i][j], the length of a shortest directed path from
+ * i to j.  Sec. 2 Eq. 1 gives the Floyd-Warshall recurrence
+ *     d^{k+1}[i][j] = min{ d^k[i][j], d^k[i][k] + d^k[k][j] },
+ * and Sec. 3 Eq. 2 the (min,+) product Z[i][j] = min_k (X[i][k] + Y[k][j]) on which every
+ * entry point below rests.
+ *
+ * Conventions for every call
+ * --------------------------
+ *  - Matrices are row-major in DEVICE memory, with a leading dimension (elements between
+ *    the starts of consecutive rows) ld >= number of columns.  The caller owns every buffer;
+ *    the library never frees caller memory and keeps no pointer after a call returns.
+ *  - dtype: APSP_I32 (int32) or APSP_F32 (float32).  Arithmetic happens in that type.
+ *  - "No edge / unreachable":
+ *      int32: a sentinel inf (pointer to an int32; NULL means APSP_INF_I32 = 0x3FFFFFFF),
+ *             1 <= inf <= 0x3FFFFFFF.  Every entry >= inf is unreachable and is written back
+ *             as exactly inf.  Because inf + inf < 2^31, sums never overflow and saturation
+ *             is the plain min against inf.
+ *      float32: a sentinel inf (pointer to a float; NULL means +infinity).  Every entry
+ *             >= the sentinel becomes +infinity, and unreachable results are +infinity.
+ *  - Weights must be >= 0 (Sec. 3.1 assumes no negative cycles; this library takes the
+ *    stronger, checkable condition).  A negative entry, or a NaN, is a data error.
+ *  - stream: a cudaStream_t passed as void* (NULL = the legacy default stream).  Every call
+ *    is asynchronous on that stream and may be captured into a CUDA graph provided the
+ *    caller supplies the workspace (ws != NULL).
+ *  - ws / ws_bytes: caller workspace in device memory (256-byte aligned, at least the size
+ *    reported by the matching *_workspace_bytes function).  ws == NULL makes the library
+ *    allocate it with cudaMallocAsync on `stream` and free it with cudaFreeAsync after the
+ *    work, both stream-ordered.
+ *
+ * Errors
+ * ------
+ *  Every entry point returns an apsp_status.  Argument errors (bad sizes, ld < columns,
+ *  unsupported dtype or tile, a workspace that is too small or misaligned, an out-of-range
+ *  sentinel) return APSP_ERR_ARG before anything is launched.  A failed launch or CUDA call
+ *  returns APSP_ERR_CUDA.  Data errors found on the device (negative weight, NaN) cannot be
+ *  returned by an asynchronous call: they set bits of a per-device status word, which stays
+ *  set until apsp_device_status() reads and clears it.  After a data error the contents of
+ *  the matrix are unspecified.
+ */
+#ifndef APSP_H_
+#define APSP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define APSP_INF_I32 0x3FFFFFFF
+#define APSP_VERSION 100
+
+typedef enum apsp_dtype { APSP_I32 = 0, APSP_F32 = 1 } apsp_dtype;
+
+typedef enum apsp_status {
+  APSP_OK = 0,
+  APSP_ERR_ARG = 1,         /* invalid argument; nothing was launched */
+  APSP_ERR_DOMAIN = 2,      /* negative weight or NaN seen on the device */
+  APSP_ERR_NOMEM = 3,       /* workspace allocation failed */
+  APSP_ERR_CUDA = 4,        /* a CUDA call or launch failed */
+  APSP_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+  APSP_ERR_UNSUPPORTED = 6  /* no device of compute capability 10.3, or feature absent */
+} apsp_status;
+
+/* Library version (APSP_VERSION of the build). */
+int apsp_version(void);
+
+/* Static, human-readable name of a status code. */
+const char *apsp_status_str(int status);
+
+/* Synchronises `stream`, then reads and clears the current device's sticky data-status
+ * word into *out (APSP_OK, or APSP_ERR_DOMAIN / APSP_ERR_TIMEOUT if a kernel flagged one).
+ * Returns APSP_OK, or APSP_ERR_CUDA if the synchronisation failed. */
+int apsp_device_status(void *stream, int *out);
+
+/* ---- a1: validate and normalise (Sec. 3.1 assumptions, Sec. 3.4 zero diagonal) --------
+ * In place on the n x n matrix d (leading dimension ld): sets d[i][i] = 0; maps entries
+ * >= inf to inf (int32) or +infinity (float32); flags negative entries and NaN in the
+ * device status word.  n = 0 is a no-op. */
+int apsp_normalise(void *d, int64_t n, int64_t ld, int dtype, const void *inf, void *stream);
+
+/* ---- a2: tropical GEMM, the (min,+) product of Sec. 3 Eq. 2 ---------------------------
+ *   accumulate = 0:  C[i][j] = min(inf, min_k A[i][k] + B[k][j])
+ *   accumulate = 1:  C[i][j] = min(C[i][j], min_k A[i][k] + B[k][j])
+ * A is M x K (lda), B is K x N (ldb), C is M x N (ldc), all row-major in device memory.
+ * Entries of A, B (and C when accumulating) must already lie in [0, inf] (int32) or be
+ * >= 0 or +infinity (float32); apsp_normalise produces that form.  C must not overlap A
+ * or B.  K = 0 gives C = inf (or leaves C unchanged when accumulating); M = 0 or N = 0 is a
+ * no-op.  The workspace holds a transposed copy of B. */
+size_t tropical_gemm_workspace_bytes(int64_t M, int64_t N, int64_t K, int dtype);
+int tropical_gemm(void *C, const void *A, const void *B, int64_t M, int64_t N, int64_t K,
+                  int64_t lda, int64_t ldb, int64_t ldc, int dtype, const void *inf,
+                  int accumulate, void *ws, size_t ws_bytes, void *stream);
+
+/* ---- a3-a5: blocked Floyd-Warshall (Eq. 1 organised over b x b tiles) -----------------
+ * Closes d (n x n, leading dimension ld) in place: after the call d[i][j] is the shortest
+ * path length i -> j (inf / +infinity if none).  Runs a1 first.  For each diagonal block
+ * kb: phase 1 closes tile (kb,kb) by Eq. 1; phase 2 updates the row and column panels of kb
+ * by a (min,+) product with the closed tile; phase 3 updates every other tile by
+ * D[i][j] = min(D[i][j], D[i][kb] (x) D[kb][j]).
+ * tile: block size b; 0 selects the default (128).  Supported: 128.
+ * The workspace holds a transposed copy of one row panel (n x b). */
+size_t apsp_fw_workspace_bytes(int64_t n, int dtype, int tile);
+int apsp_fw(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int tile, void *ws,
+            size_t ws_bytes, void *stream);
+
+/* ---- a6: R-Kleene (Sec. 3.3, Eq. 4) -----------------------------------------------------
+ * Closes d in place by the 2 x 2 block recursion H = [[A, B], [C, D]]:
+ *   A = A*;  B = A (x) B;  C = C (x) A;  D = min(D, C (x) B);  D = D*;
+ *   B = B (x) D;  C = D (x) C;  A = min(A, B (x) C).
+ * Blocks of size <= cutoff are closed by blocked Floyd-Warshall.  The split point is a
+ * multiple of 128.  cutoff: 0 selects the default (256); it must be >= 128.
+ * The workspace holds a transposed operand and a copy of the operand being overwritten
+ * (two blocks of at most ceil(n/2) x ceil(n/2) elements, rounded up to a multiple of 128). */
+size_t apsp_rkleene_workspace_bytes(int64_t n, int dtype, int cutoff);
+int apsp_rkleene(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int cutoff,
+                 void *ws, size_t ws_bytes, void *stream);
+
+/* ---- measurement: CUDA-core (min,+) rate probe -----------------------------------------
+ * Launches `blocks` x `threads` threads, each running `iters` rounds of a register-only
+ * (min,+) update of 32 independent accumulators with the instruction sequence `variant`:
+ *   0: int32 fused add-min (__viaddmin_s32)      1: int32 add then 2-input min
+ *   2: int32 two adds then 3-input min            3: fp32 add then 2-input min
+ *   4: fp32 two adds then 3-input min             5: fp32 packed pair add then 3-input min
+ * Writes a checksum per thread to sink (device, blocks*threads int32) so nothing is dead
+ * code.  Time it with events on `stream`; pairs performed = blocks*threads*iters*64. */
+int apsp_probe_minplus(int variant, int blocks, int threads, int iters, void *sink,
+                       void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* APSP_H_ */

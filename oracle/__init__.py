@@ -1,0 +1,214 @@
+"""CPU oracle for APSP over the (min,+) semiring.  TEST INFRASTRUCTURE ONLY.
+
+Only the test suite, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg
+(``bench.py --impl reference`` and the ``cpu_baseline`` field) may import this package.  The
+product library never does, and this package never imports the product library: the two share
+nothing but the seeded inputs of ``workloads.py``.
+
+What is here, each citing the passage it follows:
+  * ``fw``            -- Eq. 1 (Sec. 2) as the textbook k-i-j triple loop, in C (apsp_oracle.c),
+                         int64 for int32 inputs and fp64 for float32 inputs.
+  * ``minplus``       -- Eq. 2 (Sec. 3), the (min,+) product, as a triple loop in C.
+  * ``dijkstra_rows`` -- single-source distances from chosen sources by array Dijkstra: an
+                         independent algorithm for the same definition, used to check large
+                         matrices row by row.
+  * ``reachability``  -- the transitive closure by breadth-first search (which pairs are
+                         connected at all; needs no arithmetic).
+  * ``check_invariants`` -- properties every closed distance matrix has: zero diagonal,
+                         d <= w, the triangle inequality d[i,j] <= d[i,k] + d[k,j], idempotence
+                         under (min,+) squaring, and the reachability pattern.
+
+Unreachable pairs: int32 matrices use the sentinel ``inf`` (default 0x3FFFFFFF) and every
+result >= inf is reported as exactly inf; float32 matrices use +inf.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "apsp_oracle.c")
+_LIB = os.path.join(_HERE, "_oracle.so")
+INF_I32 = 0x3FFFFFFF
+
+_lib = None
+
+
+def build(out: str = _LIB, plant: int = 0, force: bool = False) -> str:
+    """Compile apsp_oracle.c into a shared library (OpenMP when the compiler has it)."""
+    if not force and plant == 0 and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+        return out
+    base = ["gcc", "-O2", "-std=c99", "-shared", "-fPIC", _SRC, "-o", out + ".tmp", "-lm"]
+    if plant:
+        base.insert(1, f"-DORACLE_PLANT={int(plant)}")
+    r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True, text=True)
+    if r.returncode != 0:
+        r = subprocess.run(base, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("oracle build failed:\n" + r.stderr)
+    os.replace(out + ".tmp", out)
+    return out
+
+
+def _bind(lib):
+    i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+    f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+    I64, INT = ctypes.c_int64, ctypes.c_int
+    lib.oracle_fw_i64.argtypes = [i64p, I64, I64, INT]
+    lib.oracle_fw_f64.argtypes = [f64p, I64, INT]
+    lib.oracle_minplus_i64.argtypes = [i64p, i64p, i64p, I64, I64, I64, I64, INT]
+    lib.oracle_minplus_f64.argtypes = [f64p, f64p, f64p, I64, I64, I64, INT]
+    lib.oracle_dijkstra_rows_i64.argtypes = [i64p, I64, I64, i64p, I64, i64p, INT]
+    lib.oracle_dijkstra_rows_f64.argtypes = [f64p, I64, i64p, I64, f64p, INT]
+    lib.oracle_openmp_enabled.restype = INT
+    for f in ("oracle_fw_i64", "oracle_fw_f64", "oracle_minplus_i64", "oracle_minplus_f64",
+              "oracle_dijkstra_rows_i64", "oracle_dijkstra_rows_f64"):
+        getattr(lib, f).restype = None
+    return lib
+
+
+def load(plant: int = 0):
+    """The oracle library; ``plant`` > 0 builds a deliberately broken variant (tests only)."""
+    global _lib
+    if plant:
+        d = tempfile.mkdtemp(prefix="oracle_plant_")
+        return _bind(ctypes.CDLL(build(os.path.join(d, f"_oracle_plant{plant}.so"), plant=plant)))
+    if _lib is None:
+        _lib = _bind(ctypes.CDLL(build()))
+    return _lib
+
+
+def openmp_enabled() -> bool:
+    return bool(load().oracle_openmp_enabled())
+
+
+def _threads(threads):
+    return int(threads) if threads else 1
+
+
+def fw(h: np.ndarray, inf: int = INF_I32, threads: int | None = None, lib=None) -> np.ndarray:
+    """All-pairs shortest distances of cost matrix h by Eq. 1 (Sec. 2).
+
+    int32 h -> int32 result (computed in int64, >= inf reported as inf);
+    float32/float64 h -> float64 result (computed in fp64, +inf = unreachable).
+    """
+    lib = lib or load()
+    h = np.asarray(h)
+    n = h.shape[0]
+    assert h.shape == (n, n)
+    if h.dtype.kind in "iu":
+        d = np.ascontiguousarray(h, dtype=np.int64).copy()
+        lib.oracle_fw_i64(d, n, int(inf), _threads(threads))
+        return d.astype(np.int32) if h.dtype == np.int32 else d
+    d = np.ascontiguousarray(h, dtype=np.float64).copy()
+    lib.oracle_fw_f64(d, n, _threads(threads))
+    return d
+
+
+def minplus(x: np.ndarray, y: np.ndarray, z: np.ndarray | None = None, inf: int = INF_I32,
+            lib=None) -> np.ndarray:
+    """(min,+) product of Eq. 2: x (M x K) (x) y (K x N), folded into z when z is given."""
+    lib = lib or load()
+    M, K = x.shape
+    K2, N = y.shape
+    assert K == K2
+    if x.dtype.kind in "iu":
+        X = np.ascontiguousarray(x, dtype=np.int64)
+        Y = np.ascontiguousarray(y, dtype=np.int64)
+        Z = np.full((M, N), inf, np.int64) if z is None else np.ascontiguousarray(z, dtype=np.int64).copy()
+        lib.oracle_minplus_i64(Z, X, Y, M, N, K, int(inf), int(z is not None))
+        return Z.astype(np.int32) if x.dtype == np.int32 else Z
+    X = np.ascontiguousarray(x, dtype=np.float64)
+    Y = np.ascontiguousarray(y, dtype=np.float64)
+    Z = np.full((M, N), np.inf) if z is None else np.ascontiguousarray(z, dtype=np.float64).copy()
+    lib.oracle_minplus_f64(Z, X, Y, M, N, K, int(z is not None))
+    return Z
+
+
+def dijkstra_rows(w: np.ndarray, sources, inf: int = INF_I32, threads: int | None = None,
+                  lib=None) -> np.ndarray:
+    """Distances from each source in ``sources`` (array Dijkstra; weights must be >= 0)."""
+    lib = lib or load()
+    n = w.shape[0]
+    src = np.ascontiguousarray(sources, dtype=np.int64)
+    if w.dtype.kind in "iu":
+        W = np.ascontiguousarray(w, dtype=np.int64)
+        out = np.empty((len(src), n), np.int64)
+        lib.oracle_dijkstra_rows_i64(W, n, int(inf), src, len(src), out, _threads(threads))
+        return out.astype(np.int32) if w.dtype == np.int32 else out
+    W = np.ascontiguousarray(w, dtype=np.float64)
+    out = np.empty((len(src), n), np.float64)
+    lib.oracle_dijkstra_rows_f64(W, n, src, len(src), out, _threads(threads))
+    return out
+
+
+def edge_mask(h: np.ndarray, inf: int = INF_I32) -> np.ndarray:
+    """Boolean adjacency (i != j and h[i, j] is an edge)."""
+    m = (h < inf) if h.dtype.kind in "iu" else np.isfinite(h)
+    m = m.copy()
+    np.fill_diagonal(m, False)
+    return m
+
+
+def reachability(h: np.ndarray, inf: int = INF_I32) -> np.ndarray:
+    """reach[i, j] = True iff j is reachable from i (every i reaches itself): BFS per source."""
+    adj = edge_mask(h, inf)
+    n = adj.shape[0]
+    reach = np.zeros((n, n), dtype=bool)
+    nbrs = [np.nonzero(adj[i])[0] for i in range(n)]
+    for s in range(n):
+        seen = reach[s]
+        seen[s] = True
+        frontier = [s]
+        while frontier:
+            nxt = []
+            for u in frontier:
+                for v in nbrs[u]:
+                    if not seen[v]:
+                        seen[v] = True
+                        nxt.append(v)
+            frontier = nxt
+    return reach
+
+
+def check_invariants(d: np.ndarray, h: np.ndarray, inf: int = INF_I32, rtol: float = 0.0,
+                     sample_k: int | None = None, seed: int = 0) -> list[str]:
+    """Return the list of violated properties of a claimed closure d of cost matrix h.
+
+    rtol = 0 demands exact relations (integers); floats allow rtol relative slack.
+    The triangle inequality is checked for every k, or for ``sample_k`` random k.
+    """
+    bad = []
+    n = h.shape[0]
+    if n == 0:
+        return bad
+    isint = h.dtype.kind in "iu"
+    D = d.astype(np.int64) if isint else d.astype(np.float64)
+    H = h.astype(np.int64) if isint else h.astype(np.float64)
+    if isint:
+        H = np.minimum(H, inf)
+    if np.any(np.diagonal(D) != 0):
+        bad.append("diagonal not zero")
+    Hn = H.copy()
+    np.fill_diagonal(Hn, 0)
+    slack = (lambda a: a * (1 + rtol)) if not isint else (lambda a: a)
+    fin = Hn < inf if isint else np.isfinite(Hn)
+    if np.any(D[fin] > slack(Hn[fin])):
+        bad.append("d > w on some edge")
+    ks = range(n) if sample_k is None else np.random.default_rng(seed).choice(n, size=min(n, sample_k), replace=False)
+    for k in ks:
+        via = D[:, k:k + 1] + D[k:k + 1, :]
+        if isint:
+            via = np.minimum(via, inf)
+        if np.any(D > slack(via)):
+            bad.append(f"triangle inequality fails through k={int(k)}")
+            break
+    reach = reachability(h, inf)
+    got = D < inf if isint else np.isfinite(D)
+    if not np.array_equal(reach, got):
+        bad.append("reachability pattern differs from BFS closure")
+    return bad

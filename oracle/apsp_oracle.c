@@ -1,0 +1,213 @@
+/*
+ * apsp_oracle.c -- CPU oracle for all-pairs shortest paths over the (min,+) semiring.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests, the smoke check and the CPU-baseline leg of the
+ * benchmark may load this library.  It shares no source, header, table or helper with the
+ * CUDA path and must never be called from the product library.
+ *
+ * Everything here is the plain definition, written out slowly:
+ *
+ *   - oracle_fw_i64 / oracle_fw_f64: the Floyd-Warshall recurrence of the paper's Eq. 1,
+ *       d^{k+1}[i,j] = min{ d^k[i,j], d^k[i,k] + d^k[k,j] },
+ *     run as the textbook k-i-j triple loop over all n intermediate vertices (Sec. 2).
+ *     Integer inputs are widened to int64 and floating inputs to fp64 by the caller, so no
+ *     sum here can overflow or round differently from the exact path length (fp32 weights
+ *     widen exactly; an fp64 sum of a few hundred fp32 values is exact to ~1e-13 relative).
+ *   - oracle_minplus_i64 / oracle_minplus_f64: the (min,+) product of Eq. 2,
+ *       Z[i,j] = min_k ( X[i,k] + Y[k,j] ),
+ *     as a triple loop, optionally folded into an existing Z (Z = min(Z, X (x) Y)).
+ *   - oracle_dijkstra_rows_i64 / _f64: single-source shortest paths from selected sources by
+ *     textbook O(n^2) array Dijkstra (valid because every weight is >= 0; Sec. 3.1 assumes
+ *     no negative cycles and the generator draws costs >= 0, Sec. 3.4).  It is a second,
+ *     independent algorithm for the same distances, used to check large matrices by rows.
+ *
+ * Conventions shared with the tests (not with the CUDA path):
+ *   - int64: an entry >= inf means "no edge / unreachable"; such operands are skipped and
+ *     every result >= inf is written back as exactly inf.
+ *   - fp64: +infinity means "no edge / unreachable"; IEEE arithmetic does the rest.
+ *   - the diagonal is forced to 0 (a self-loop costs nothing, Sec. 3.4).
+ *   - matrices are dense row-major with leading dimension n.
+ *
+ * `threads` > 1 splits the i loop (for FW, at each fixed k) or the source list (Dijkstra)
+ * over OpenMP threads.  For FW this is race-free because row k itself never changes at step
+ * k: d[k][k] = 0 and weights are non-negative, so d[k][k] + d[k][j] is never < d[k][j].
+ *
+ * Build: gcc -O2 -fopenmp -shared -fPIC apsp_oracle.c -o _oracle.so  (see build.py).
+ * Defining ORACLE_PLANT=<n> compiles a deliberately wrong variant; the tests use those
+ * variants to show that the pins catch each planted mistake.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#ifndef ORACLE_PLANT
+#define ORACLE_PLANT 0
+#endif
+
+static void set_threads(int threads) {
+#ifdef _OPENMP
+  if (threads > 0) omp_set_num_threads(threads);
+#else
+  (void)threads;
+#endif
+}
+
+int oracle_openmp_enabled(void) {
+#ifdef _OPENMP
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+/* Eq. 1 over int64 with an "unreachable" threshold inf. In place on d (n x n). */
+void oracle_fw_i64(int64_t *d, int64_t n, int64_t inf, int threads) {
+  set_threads(threads);
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t j = 0; j < n; ++j)
+      if (d[i * n + j] >= inf) d[i * n + j] = inf;
+#if ORACLE_PLANT != 1 /* plant 1: forget that a vertex reaches itself at cost 0 */
+    d[i * n + i] = 0;
+#endif
+  }
+#if ORACLE_PLANT == 2 /* plant 2: intermediate vertex innermost (i-j-k): not Floyd-Warshall */
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j)
+      for (int64_t k = 0; k < n; ++k)
+        if (d[i * n + k] < inf && d[k * n + j] < inf && d[i * n + k] + d[k * n + j] < d[i * n + j])
+          d[i * n + j] = d[i * n + k] + d[k * n + j];
+#else
+  for (int64_t k = 0; k < n; ++k) {
+    const int64_t *rowk = d + k * n;
+#pragma omp parallel for schedule(static) if (threads > 1)
+    for (int64_t i = 0; i < n; ++i) {
+      int64_t *rowi = d + i * n;
+      const int64_t dik = rowi[k];
+      if (dik >= inf) continue; /* no path i -> k yet: nothing to relax through k */
+      for (int64_t j = 0; j < n; ++j) {
+#if ORACLE_PLANT == 3 /* plant 3: swapped index, d[i][k] + d[j][k] */
+        const int64_t dkj = d[j * n + k];
+#else
+        const int64_t dkj = rowk[j];
+#endif
+        if (dkj >= inf) continue;
+        const int64_t s = dik + dkj;
+        if (s < rowi[j]) rowi[j] = s;
+      }
+    }
+  }
+#endif
+  for (int64_t i = 0; i < n * n; ++i)
+    if (d[i] >= inf) d[i] = inf;
+}
+
+/* Eq. 1 over fp64 with +infinity as "unreachable". In place on d (n x n). */
+void oracle_fw_f64(double *d, int64_t n, int threads) {
+  set_threads(threads);
+  for (int64_t i = 0; i < n; ++i) d[i * n + i] = 0.0;
+  for (int64_t k = 0; k < n; ++k) {
+    const double *rowk = d + k * n;
+#pragma omp parallel for schedule(static) if (threads > 1)
+    for (int64_t i = 0; i < n; ++i) {
+      double *rowi = d + i * n;
+      const double dik = rowi[k];
+      if (isinf(dik)) continue;
+      for (int64_t j = 0; j < n; ++j) {
+        const double s = dik + rowk[j];
+        if (s < rowi[j]) rowi[j] = s;
+      }
+    }
+  }
+}
+
+/* Eq. 2: Z = X (x) Y, or Z = min(Z, X (x) Y) when accumulate != 0.
+ * X is M x K, Y is K x N, Z is M x N, all dense row-major. int64 with threshold inf. */
+void oracle_minplus_i64(int64_t *Z, const int64_t *X, const int64_t *Y, int64_t M, int64_t N,
+                        int64_t K, int64_t inf, int accumulate) {
+  for (int64_t i = 0; i < M; ++i)
+    for (int64_t j = 0; j < N; ++j) {
+      int64_t best = accumulate ? Z[i * N + j] : inf;
+      if (best > inf) best = inf;
+      for (int64_t k = 0; k < K; ++k) {
+#if ORACLE_PLANT == 4 /* plant 4: transposed operand, X[k][i] + Y[j][k] (square cases only) */
+        const int64_t x = X[k * K + i], y = Y[j * N + k];
+#else
+        const int64_t x = X[i * K + k], y = Y[k * N + j];
+#endif
+        if (x >= inf || y >= inf) continue;
+        if (x + y < best) best = x + y;
+      }
+      Z[i * N + j] = best >= inf ? inf : best;
+    }
+}
+
+void oracle_minplus_f64(double *Z, const double *X, const double *Y, int64_t M, int64_t N,
+                        int64_t K, int accumulate) {
+  for (int64_t i = 0; i < M; ++i)
+    for (int64_t j = 0; j < N; ++j) {
+      double best = accumulate ? Z[i * N + j] : INFINITY;
+      for (int64_t k = 0; k < K; ++k) {
+        const double s = X[i * K + k] + Y[k * N + j];
+        if (s < best) best = s;
+      }
+      Z[i * N + j] = best;
+    }
+}
+
+/* Array Dijkstra from each source in src[0..nsrc): out is nsrc x n.
+ * w is the n x n weight matrix (entry >= inf: no edge); the diagonal is ignored. */
+void oracle_dijkstra_rows_i64(const int64_t *w, int64_t n, int64_t inf, const int64_t *src,
+                              int64_t nsrc, int64_t *out, int threads) {
+  set_threads(threads);
+#pragma omp parallel for schedule(dynamic, 1) if (threads > 1)
+  for (int64_t s = 0; s < nsrc; ++s) {
+    int64_t *dist = out + s * n;
+    unsigned char *done = (unsigned char *)calloc((size_t)n, 1);
+    for (int64_t v = 0; v < n; ++v) dist[v] = inf;
+    dist[src[s]] = 0;
+    for (;;) {
+      int64_t u = -1, du = inf;
+      for (int64_t v = 0; v < n; ++v)
+        if (!done[v] && dist[v] < du) { du = dist[v]; u = v; }
+      if (u < 0) break; /* every remaining vertex is unreachable */
+      done[u] = 1;
+      const int64_t *row = w + u * n;
+      for (int64_t v = 0; v < n; ++v) {
+        if (v == u || done[v] || row[v] >= inf) continue;
+        if (du + row[v] < dist[v]) dist[v] = du + row[v];
+      }
+    }
+    for (int64_t v = 0; v < n; ++v)
+      if (dist[v] >= inf) dist[v] = inf;
+    free(done);
+  }
+}
+
+void oracle_dijkstra_rows_f64(const double *w, int64_t n, const int64_t *src, int64_t nsrc,
+                              double *out, int threads) {
+  set_threads(threads);
+#pragma omp parallel for schedule(dynamic, 1) if (threads > 1)
+  for (int64_t s = 0; s < nsrc; ++s) {
+    double *dist = out + s * n;
+    unsigned char *done = (unsigned char *)calloc((size_t)n, 1);
+    for (int64_t v = 0; v < n; ++v) dist[v] = INFINITY;
+    dist[src[s]] = 0.0;
+    for (;;) {
+      int64_t u = -1;
+      double du = INFINITY;
+      for (int64_t v = 0; v < n; ++v)
+        if (!done[v] && dist[v] < du) { du = dist[v]; u = v; }
+      if (u < 0) break;
+      done[u] = 1;
+      const double *row = w + u * n;
+      for (int64_t v = 0; v < n; ++v) {
+        if (v == u || done[v] || isinf(row[v])) continue;
+        if (du + row[v] < dist[v]) dist[v] = du + row[v];
+      }
+    }
+    free(done);
+  }
+}

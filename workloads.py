@@ -1,0 +1,128 @@
+"""Seeded synthetic inputs for the APSP library, its tests and its benchmark.
+
+This module only draws random graphs, sizes and arrival times.  It contains none of the
+shortest-path arithmetic, so both the CUDA path and the CPU oracle can take their inputs
+from it without sharing any of the method.
+
+Cost-matrix convention (the paper's H, Sec. 3.1 and Sec. 3.4): a dense row-major n x n matrix
+whose entry [i, j] is the cost of the edge i -> j, the diagonal is 0, and a missing edge holds
+the "no edge" sentinel: INF_I32 = 0x3FFFFFFF for int32 matrices and +inf for float32 ones.
+
+Graph families:
+  * er_graph: directed Erdos-Renyi, every ordered pair i != j is an edge independently with
+    probability p, weights drawn from a named distribution.  Generation runs in fixed blocks
+    of rows, each from its own PCG64 stream keyed by (seed, block), so the matrix does not
+    depend on how many threads draw it and any row block can be regenerated on its own.
+  * paper_graph: the paper's generator f(V, rho, alpha) of Sec. 3.4: a uniform probability
+    matrix P scaled by rho, a Bernoulli draw per entry, integer costs in [0, alpha], zero
+    diagonal.  rho * P is clipped to [0, 1] (the paper's rho ~ U[0, 100] would otherwise give
+    "probabilities" above 1).
+"""
+from __future__ import annotations
+
+import math
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+INF_I32 = 0x3FFFFFFF
+ROWS_PER_BLOCK = 256
+
+
+def _block_rng(seed: int, block: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64([int(seed), int(block), 0x41505350]))
+
+
+def _fill_block(out, r0, r1, n, p, dtype, dist, lo, hi, seed, block, inf):
+    rng = _block_rng(seed, block)
+    rows = r1 - r0
+    u = rng.random((rows, n))
+    edge = u < p
+    if dtype == np.int32:
+        w = rng.integers(lo, hi, size=(rows, n), endpoint=True, dtype=np.int64)
+        blk = np.where(edge, w, inf).astype(np.int32)
+    else:
+        if dist == "lognormal":
+            w = rng.lognormal(mean=lo, sigma=hi, size=(rows, n))
+        elif dist == "uniform01":  # uniform in (0, 1]
+            w = 1.0 - rng.random((rows, n))
+        elif dist == "uniform":
+            w = rng.uniform(lo, hi, size=(rows, n))
+        else:
+            raise ValueError(f"unknown weight distribution {dist!r}")
+        blk = np.where(edge, w, np.inf).astype(np.float32)
+    idx = np.arange(r0, r1)
+    blk[idx - r0, idx] = 0
+    out[r0:r1] = blk
+
+
+def er_graph(n: int, p: float, dtype="int32", dist: str = "uniform", lo=1, hi=100,
+             seed: int = 0, inf: int = INF_I32, threads: int | None = None) -> np.ndarray:
+    """Directed Erdos-Renyi cost matrix (n x n, row-major, diagonal 0).
+
+    int32: weights uniform integers in [lo, hi], missing edges = inf.
+    float32: dist "lognormal" (lo = mu, hi = sigma), "uniform01" (uniform in (0, 1]) or
+    "uniform" (uniform in [lo, hi)); missing edges = +inf.
+    """
+    dt = np.dtype(dtype)
+    if dt not in (np.dtype(np.int32), np.dtype(np.float32)):
+        raise ValueError("dtype must be int32 or float32")
+    out = np.empty((n, n), dtype=dt)
+    if n == 0:
+        return out
+    nblk = (n + ROWS_PER_BLOCK - 1) // ROWS_PER_BLOCK
+    jobs = [(b * ROWS_PER_BLOCK, min(n, (b + 1) * ROWS_PER_BLOCK), b) for b in range(nblk)]
+    threads = threads or min(16, os.cpu_count() or 1)
+    args = (n, p, dt.type, dist, lo, hi, seed)
+    if threads <= 1 or nblk == 1:
+        for r0, r1, b in jobs:
+            _fill_block(out, r0, r1, *args, b, inf)
+    else:
+        with ThreadPoolExecutor(threads) as ex:
+            list(ex.map(lambda j: _fill_block(out, j[0], j[1], *args, j[2], inf), jobs))
+    return out
+
+
+def paper_graph(V: int, rho: float, alpha: int = 100, seed: int = 0, inf: int = INF_I32) -> np.ndarray:
+    """The generator f(V, rho, alpha) of Sec. 3.4 as an int32 cost matrix (missing = inf)."""
+    rng = np.random.Generator(np.random.PCG64([int(seed), 0x50415052]))
+    P = rng.random((V, V))
+    A = rng.random((V, V)) < np.clip(rho * P, 0.0, 1.0)
+    H = np.where(A, rng.integers(0, alpha, size=(V, V), endpoint=True), inf).astype(np.int32)
+    np.fill_diagonal(H, 0)
+    return H
+
+
+def batch_specs(count: int = 2048, n_lo: int = 32, n_hi: int = 1024, p_lo: float = 0.02,
+                p_hi: float = 0.8, seed: int = 0):
+    """Sizes and densities of a batch: n log-uniform in [n_lo, n_hi], p uniform in [p_lo, p_hi].
+
+    Graph g of the batch is then er_graph(n[g], p[g], seed=1000 + g).
+    """
+    rng = np.random.Generator(np.random.PCG64([int(seed), 0x42415443]))
+    ns = np.rint(np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), size=count))).astype(np.int64)
+    ps = rng.uniform(p_lo, p_hi, size=count)
+    return ns, ps
+
+
+def batch_graphs(ns, ps, dtype="int32", lo=1, hi=100, inf: int = INF_I32):
+    return [er_graph(int(n), float(p), dtype=dtype, lo=lo, hi=hi, seed=1000 + g, inf=inf, threads=1)
+            for g, (n, p) in enumerate(zip(ns, ps))]
+
+
+def poisson_requests(rate: float = 200.0, duration: float = 60.0, n_lo: int = 64, n_hi: int = 8192,
+                     p_lo: float = 0.01, p_hi: float = 0.5, seed: int = 0):
+    """Arrival times (s), sizes, densities and dtypes of a Poisson request stream.
+
+    Even request ids carry int32 weights uniform in [1, 100]; odd ones float32 lognormal(0, 1).
+    """
+    rng = np.random.Generator(np.random.PCG64([int(seed), 0x53455256]))
+    gaps = rng.exponential(1.0 / rate, size=int(rate * duration * 1.5) + 16)
+    t = np.cumsum(gaps)
+    t = t[t < duration]
+    m = len(t)
+    ns = np.rint(np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), size=m))).astype(np.int64)
+    ps = rng.uniform(p_lo, p_hi, size=m)
+    dtypes = np.where(np.arange(m) % 2 == 0, "int32", "float32")
+    return t, ns, ps, dtypes
