@@ -90,12 +90,13 @@ int apsp_normalise(void *d, int64_t n, int64_t ld, int dtype, const void *inf, v
  * A is M x K (lda), B is K x N (ldb), C is M x N (ldc), all row-major in device memory.
  * Entries of A, B (and C when accumulating) must already lie in [0, inf] (int32) or be
  * >= 0 or +infinity (float32); apsp_normalise produces that form.  C must not overlap A
- * or B.  K = 0 gives C = inf (or leaves C unchanged when accumulating); M = 0 or N = 0 is a
- * no-op.  The workspace holds a transposed copy of B. */
-size_t tropical_gemm_workspace_bytes(int64_t M, int64_t N, int64_t K, int dtype);
+ * or B (APSP_ERR_ARG).  K = 0 gives C = inf (or leaves C unchanged when accumulating);
+ * M = 0 or N = 0 is a no-op.  When every base is 16-byte aligned and every leading
+ * dimension a multiple of 4, the TMA-fed engine runs; otherwise a plain-load kernel.
+ * Needs no workspace. */
 int tropical_gemm(void *C, const void *A, const void *B, int64_t M, int64_t N, int64_t K,
                   int64_t lda, int64_t ldb, int64_t ldc, int dtype, const void *inf,
-                  int accumulate, void *ws, size_t ws_bytes, void *stream);
+                  int accumulate, void *stream);
 
 /* ---- a3-a5: blocked Floyd-Warshall (Eq. 1 organised over b x b tiles) -----------------
  * Closes d (n x n, leading dimension ld) in place: after the call d[i][j] is the shortest
@@ -104,8 +105,9 @@ int tropical_gemm(void *C, const void *A, const void *B, int64_t M, int64_t N, i
  * by a (min,+) product with the closed tile; phase 3 updates every other tile by
  * D[i][j] = min(D[i][j], D[i][kb] (x) D[kb][j]).
  * tile: block size b; 0 selects the default (128).  Supported: 128.
- * The workspace holds a transposed copy of one row panel (n x b). */
-size_t apsp_fw_workspace_bytes(int64_t n, int dtype, int tile);
+ * d must be 16-byte aligned.  The workspace is empty when ld is a multiple of 4; otherwise
+ * it holds an aligned copy of the matrix (n x round_up(n, 4) elements). */
+size_t apsp_fw_workspace_bytes(int64_t n, int64_t ld, int dtype, int tile);
 int apsp_fw(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int tile, void *ws,
             size_t ws_bytes, void *stream);
 
@@ -115,9 +117,10 @@ int apsp_fw(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int tile
  *   B = B (x) D;  C = D (x) C;  A = min(A, B (x) C).
  * Blocks of size <= cutoff are closed by blocked Floyd-Warshall.  The split point is a
  * multiple of 128.  cutoff: 0 selects the default (256); it must be >= 128.
- * The workspace holds a transposed operand and a copy of the operand being overwritten
- * (two blocks of at most ceil(n/2) x ceil(n/2) elements, rounded up to a multiple of 128). */
-size_t apsp_rkleene_workspace_bytes(int64_t n, int dtype, int cutoff);
+ * d must be 16-byte aligned.  The workspace holds a copy of the block being overwritten
+ * (h x round_up(h, 4) elements, h = ceil(n/2) rounded up to a multiple of 128, when
+ * n > cutoff) plus, when ld is not a multiple of 4, an aligned copy of the matrix. */
+size_t apsp_rkleene_workspace_bytes(int64_t n, int64_t ld, int dtype, int cutoff);
 int apsp_rkleene(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int cutoff,
                  void *ws, size_t ws_bytes, void *stream);
 

@@ -1,0 +1,198 @@
+"""Python binding of libapsp.so: all-pairs shortest paths over the (min,+) semiring on GB300.
+
+Thin ctypes wrappers with the same names as the C ABI (include/apsp.h).  They only marshal
+arguments: torch CUDA tensors become device pointers, leading dimensions and the current
+stream; every step of the computation runs in the library's CUDA kernels.  There is no CPU
+fallback: if libapsp.so is missing this module raises on import.
+
+    d = torch.from_numpy(h).cuda()          # n x n int32 or float32 cost matrix
+    apsp_fw(d)                               # closed in place: shortest distances
+    apsp_rkleene(d, cutoff=256)              # same result by R-Kleene (Sec. 3.3)
+    tropical_gemm(C, A, B)                   # C = A (x) B, Eq. 2
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libapsp.so")
+
+APSP_I32, APSP_F32 = 0, 1
+APSP_INF_I32 = 0x3FFFFFFF
+STATUS = {0: "ok", 1: "invalid argument", 2: "negative weight or NaN", 3: "out of memory",
+          4: "CUDA error", 5: "device wait timed out", 6: "unsupported"}
+
+
+class ApspError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(code, code)} (status {code})")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libapsp.so not built at {LIB_PATH}; run __graft_entry__.build() "
+                          "(python -m paper_2310_03983_gb300.build)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_size_t
+    sigs = {
+        "apsp_version": ([], i32),
+        "apsp_status_str": ([i32], ctypes.c_char_p),
+        "apsp_device_status": ([vp, ctypes.POINTER(i32)], i32),
+        "apsp_normalise": ([vp, i64, i64, i32, vp, vp], i32),
+        "tropical_gemm": ([vp, vp, vp, i64, i64, i64, i64, i64, i64, i32, vp, i32, vp], i32),
+        "apsp_fw_workspace_bytes": ([i64, i64, i32, i32], sz),
+        "apsp_fw": ([vp, i64, i64, i32, vp, i32, vp, sz, vp], i32),
+        "apsp_rkleene_workspace_bytes": ([i64, i64, i32, i32], sz),
+        "apsp_rkleene": ([vp, i64, i64, i32, vp, i32, vp, sz, vp], i32),
+        "apsp_probe_minplus": ([i32, i32, i32, i32, vp, vp], i32),
+    }
+    for name, (args, res) in sigs.items():
+        f = getattr(lib, name)
+        f.argtypes, f.restype = args, res
+    return lib
+
+
+_lib = _load()
+EXPORTS = ("apsp_version", "apsp_status_str", "apsp_device_status", "apsp_normalise", "tropical_gemm",
+           "apsp_fw_workspace_bytes", "apsp_fw", "apsp_rkleene_workspace_bytes", "apsp_rkleene",
+           "apsp_probe_minplus")
+
+
+def lib():
+    return _lib
+
+
+def _check(code: int, what: str):
+    if code != 0:
+        raise ApspError(code, what)
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.int32:
+        return APSP_I32
+    if t.dtype == torch.float32:
+        return APSP_F32
+    raise TypeError(f"dtype must be int32 or float32, got {t.dtype}")
+
+
+def _mat(t: torch.Tensor, name: str):
+    if not t.is_cuda or t.dim() != 2 or (t.numel() > 0 and t.stride(1) != 1):
+        raise ValueError(f"{name} must be a 2-D CUDA tensor with unit column stride")
+    return t.data_ptr(), t.stride(0) if t.shape[0] > 1 else max(t.shape[1], 1)
+
+
+def _stream(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream if hasattr(s, "cuda_stream") else int(s)
+
+
+def _inf_arg(inf, code):
+    if inf is None:
+        return None, None
+    box = ctypes.c_int32(int(inf)) if code == APSP_I32 else ctypes.c_float(float(inf))
+    return ctypes.cast(ctypes.pointer(box), ctypes.c_void_p), box
+
+
+def apsp_version() -> int:
+    return _lib.apsp_version()
+
+
+def apsp_device_status(stream=None) -> int:
+    """Synchronise the stream, read and clear the device's sticky data-status word."""
+    out = ctypes.c_int32(0)
+    _check(_lib.apsp_device_status(_stream(stream), ctypes.byref(out)), "apsp_device_status")
+    return out.value
+
+
+def apsp_normalise(d: torch.Tensor, inf=None, stream=None):
+    p, ld = _mat(d, "d")
+    code = _dtype_code(d)
+    ip, _keep = _inf_arg(inf, code)
+    _check(_lib.apsp_normalise(p, d.shape[0], ld, code, ip, _stream(stream)), "apsp_normalise")
+    return d
+
+
+def tropical_gemm(C: torch.Tensor, A: torch.Tensor, B: torch.Tensor, accumulate: bool = False, inf=None,
+                  stream=None):
+    """C = A (x) B, or C = min(C, A (x) B) when accumulate (Eq. 2)."""
+    M, K = A.shape
+    K2, N = B.shape
+    if K != K2 or tuple(C.shape) != (M, N):
+        raise ValueError("shape mismatch")
+    code = _dtype_code(C)
+    if A.dtype != C.dtype or B.dtype != C.dtype:
+        raise TypeError("A, B and C must share a dtype")
+    pc, ldc = _mat(C, "C")
+    pa, lda = _mat(A, "A")
+    pb, ldb = _mat(B, "B")
+    ip, _keep = _inf_arg(inf, code)
+    _check(_lib.tropical_gemm(pc, pa, pb, M, N, K, lda, ldb, ldc, code, ip, int(bool(accumulate)),
+                              _stream(stream)), "tropical_gemm")
+    return C
+
+
+def _closure(fn, wsfn, d, inf, param, ws, stream, what):
+    n = d.shape[0]
+    if d.shape[1] != n:
+        raise ValueError("d must be square")
+    p, ld = _mat(d, "d")
+    code = _dtype_code(d)
+    ip, _keep = _inf_arg(inf, code)
+    if ws is None:
+        wp, wb = None, 0
+    else:
+        wp, wb = ws.data_ptr(), ws.numel() * ws.element_size()
+    _check(fn(p, n, ld, code, ip, int(param), wp, wb, _stream(stream)), what)
+    return d
+
+
+def apsp_fw_workspace_bytes(n: int, ld: int, dtype=torch.int32, tile: int = 0) -> int:
+    return _lib.apsp_fw_workspace_bytes(n, ld, APSP_I32 if dtype == torch.int32 else APSP_F32, tile)
+
+
+def apsp_rkleene_workspace_bytes(n: int, ld: int, dtype=torch.int32, cutoff: int = 0) -> int:
+    return _lib.apsp_rkleene_workspace_bytes(n, ld, APSP_I32 if dtype == torch.int32 else APSP_F32, cutoff)
+
+
+def apsp_fw(d: torch.Tensor, inf=None, tile: int = 0, ws: torch.Tensor | None = None, stream=None):
+    """Close d in place by blocked Floyd-Warshall (Eq. 1 over 128 x 128 tiles)."""
+    return _closure(_lib.apsp_fw, _lib.apsp_fw_workspace_bytes, d, inf, tile, ws, stream, "apsp_fw")
+
+
+def apsp_rkleene(d: torch.Tensor, inf=None, cutoff: int = 0, ws: torch.Tensor | None = None, stream=None):
+    """Close d in place by R-Kleene (Sec. 3.3) with blocked-FW leaves of <= cutoff vertices."""
+    return _closure(_lib.apsp_rkleene, _lib.apsp_rkleene_workspace_bytes, d, inf, cutoff, ws, stream,
+                    "apsp_rkleene")
+
+
+def apsp_probe_minplus(variant: int, blocks: int, threads: int, iters: int, sink: torch.Tensor, stream=None):
+    _check(_lib.apsp_probe_minplus(variant, blocks, threads, iters, sink.data_ptr(), _stream(stream)),
+           "apsp_probe_minplus")
+
+
+ALGOS = {"fw": apsp_fw, "rkleene": apsp_rkleene}
+
+
+def solve(h, algo: str = "fw", inf=None, param: int = 0, device=None, out=None):
+    """End-to-end solve of a HOST cost matrix (numpy array or CPU tensor): copy it to the
+    device, close it there, copy the distances back.  Returns a CPU tensor (``out`` if given,
+    pinned memory recommended)."""
+    t = torch.as_tensor(h)
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    d = t.to(dev, non_blocking=True)
+    if algo == "fw":
+        apsp_fw(d, inf=inf, tile=param)
+    elif algo == "rkleene":
+        apsp_rkleene(d, inf=inf, cutoff=param)
+    else:
+        raise ValueError(f"unknown algorithm {algo!r}")
+    if out is None:
+        return d.cpu()
+    out.copy_(d, non_blocking=True)
+    torch.cuda.current_stream(dev).synchronize()
+    return out

@@ -1,0 +1,165 @@
+// common.cuh -- shared device/host helpers of libapsp (sm_103a only).
+//
+// Contents: the (min,+) element operations per dtype, mbarrier and TMA wrappers written as
+// inline PTX, the per-device sticky status word, and host-side error plumbing.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/apsp.h"
+
+#ifndef __CUDACC__
+#error "compile with nvcc"
+#endif
+
+namespace apsp {
+
+// ---------------------------------------------------------------------------------------
+// Status word: one per device, sticky (bits OR-ed in by kernels) until apsp_device_status
+// reads and clears it.  Bit layout: 1 << APSP_ERR_DOMAIN, 1 << APSP_ERR_TIMEOUT.
+// ---------------------------------------------------------------------------------------
+// Kernels receive the word's device address (status_word()) as an argument, so no
+// translation unit needs relocatable device code.
+__device__ __forceinline__ void flag_status(unsigned int *st, int code) {
+  if (st) atomicOr(st, 1u << code);
+}
+
+// Iteration limit of every spin-wait on an mbarrier.  The longest legitimate wait in these
+// kernels is one tile of work (tens of microseconds); 2^24 try_wait calls take between a
+// fraction of a second and a few seconds, so a wait that cannot complete ends the kernel
+// with APSP_ERR_TIMEOUT instead of hanging the GPU.
+constexpr uint32_t kSpinLimit = 1u << 24;
+
+// ---------------------------------------------------------------------------------------
+// (min,+) element operations.  int32 values live in [0, INF] with INF <= 0x3FFFFFFF, so
+// a + b never overflows and min() against an accumulator <= INF saturates for free.
+// ---------------------------------------------------------------------------------------
+template <typename T> struct Ops;
+
+template <> struct Ops<int> {
+  static __device__ __forceinline__ int add(int a, int b) { return a + b; }
+  static __device__ __forceinline__ int mn(int a, int b) { return min(a, b); }
+  // c = min(c, a + b) as one fused DPX operation
+  static __device__ __forceinline__ int addmin(int a, int b, int c) { return __viaddmin_s32(a, b, c); }
+  static __device__ __forceinline__ int min3(int a, int b, int c) { return __vimin3_s32(a, b, c); }
+};
+
+template <> struct Ops<float> {
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float mn(float a, float b) { return fminf(a, b); }
+  static __device__ __forceinline__ float addmin(float a, float b, float c) { return fminf(c, __fadd_rn(a, b)); }
+  static __device__ __forceinline__ float min3(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+  }
+};
+
+// ---------------------------------------------------------------------------------------
+// mbarrier / TMA wrappers (PTX ISA: mbarrier.*, cp.async.bulk.tensor.*)
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity to complete.  Returns false (and flags
+// APSP_ERR_TIMEOUT) if the limit is reached.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned int *st) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  flag_status(st, APSP_ERR_TIMEOUT);
+  return false;
+}
+
+__device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap *m) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(m)) : "memory");
+}
+
+// 2-D tiled TMA load of box {x (inner), y} at coordinates (x, y) into smem, completing
+// `bytes` of transaction count on bar.  x * sizeof(elem) must be a multiple of 16.
+__device__ __forceinline__ void tma_load_2d(void *smem_dst, const CUtensorMap *m, int x, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(smem_dst)),
+      "l"(reinterpret_cast<uint64_t>(m)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ int4 lds128(const void *p) {
+  int4 v;
+  asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(smem_u32(p)));
+  return v;
+}
+
+}  // namespace apsp
+
+// ---------------------------------------------------------------------------------------
+// Host helpers
+// ---------------------------------------------------------------------------------------
+#define APSP_CUDA_TRY(expr)                                \
+  do {                                                     \
+    cudaError_t _e = (expr);                               \
+    if (_e != cudaSuccess) return APSP_ERR_CUDA;           \
+  } while (0)
+
+#define APSP_LAUNCH_CHECK()                                \
+  do {                                                     \
+    if (cudaGetLastError() != cudaSuccess) return APSP_ERR_CUDA; \
+  } while (0)
+
+namespace apsp {
+
+inline int elem_size(int dtype) { return 4; }
+inline bool dtype_ok(int dtype) { return dtype == APSP_I32 || dtype == APSP_F32; }
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline int64_t round_up(int64_t a, int64_t b) { return cdiv(a, b) * b; }
+
+// Number of SMs of the current device (cached per device).
+int sm_count();
+
+// Device address of the current device's status word (nullptr on failure).
+unsigned int *status_word();
+
+// Encode a 2-D row-major tensor map: `rows` x `cols` elements (4 bytes each), leading
+// dimension ld elements, box `box_rows` x `box_cols`, no swizzle, zero OOB fill.
+int make_tmap_2d(CUtensorMap *out, const void *base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                 int box_cols, int dtype);
+
+// Resolve the int32 sentinel (NULL -> APSP_INF_I32) or float sentinel (NULL -> +inf).
+int resolve_inf_i32(const void *inf, int *out);
+int resolve_inf_f32(const void *inf, float *out);
+
+}  // namespace apsp

@@ -1,0 +1,159 @@
+// fw.cu -- a3-a5: blocked Floyd-Warshall over 128 x 128 tiles.
+//
+// Eq. 1 (Sec. 2) relaxes every pair through intermediate vertex k, for k = 0..n-1.  Grouping
+// the k's by 128-vertex blocks kb gives the classic three phases per block:
+//   phase 1  close the diagonal tile (kb, kb) by Eq. 1 restricted to its own vertices;
+//   phase 2  row panel    D[kb][j] = D[kb][kb]* (x) D[kb][j]   (j != kb)
+//            column panel D[i][kb] = D[i][kb] (x) D[kb][kb]*   (i != kb)
+//            one (min,+) product each is exact because the closed tile has a zero diagonal,
+//            so the product already contains the old entry (k = i or k = j term);
+//   phase 3  D[i][j] = min(D[i][j], D[i][kb] (x) D[kb][j])      (i, j != kb)
+//            -- the rank-128 (min,+) update that carries essentially all n^3 of the work.
+// Phases 2 and 3 run on the TMA-fed tropical GEMM engine (tgemm.cu); phase 1 is one CTA.
+#include <algorithm>
+
+#include "closure.cuh"
+
+namespace apsp {
+
+// Phase 1: Eq. 1 on the bk x bk diagonal tile held in shared memory.  At step k, row k and
+// column k do not change (d[k][k] = 0 and weights are non-negative), so every thread can
+// read them while others update the rest of the tile; one barrier per k orders the steps.
+// A thread only writes when the value strictly decreases, so row/column k are never written
+// during step k.
+template <typename T>
+__global__ void __launch_bounds__(1024) fw_diag_kernel(T *d, int64_t ld, int64_t n, int64_t kb) {
+  extern __shared__ uint8_t smem_raw[];
+  T(*S)[kBM] = reinterpret_cast<T(*)[kBM]>(smem_raw);
+  const int64_t kb0 = kb * kBM;
+  const int bk = (int)std::min<int64_t>(kBM, n - kb0);
+  T *base = d + kb0 * ld + kb0;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int e = threadIdx.x; e < kBM * kBM; e += blockDim.x) {
+    const int r = e >> 7, c = e & (kBM - 1);
+    if (r < bk && c < bk) S[r][c] = base[(int64_t)r * ld + c];
+  }
+  __syncthreads();
+  for (int k = 0; k < bk; ++k) {
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr) {
+      const int i = ty + 32 * rr;
+      if (i >= bk) break;
+      const T dik = S[i][k];
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        const int j = tx + 32 * cc;
+        if (j < bk) {
+          const T v = Ops<T>::add(dik, S[k][j]);
+          if (v < S[i][j]) S[i][j] = v;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < kBM * kBM; e += blockDim.x) {
+    const int r = e >> 7, c = e & (kBM - 1);
+    if (r < bk && c < bk) base[(int64_t)r * ld + c] = S[r][c];
+  }
+}
+
+int launch_fw_diag(void *d, int64_t ld, int64_t n, int64_t kb, int dtype, cudaStream_t s) {
+  const int smem = kBM * kBM * 4;
+  if (dtype == APSP_I32) {
+    APSP_CUDA_TRY(cudaFuncSetAttribute(fw_diag_kernel<int>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    fw_diag_kernel<int><<<1, 1024, smem, s>>>(reinterpret_cast<int *>(d), ld, n, kb);
+  } else {
+    APSP_CUDA_TRY(cudaFuncSetAttribute(fw_diag_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    fw_diag_kernel<float><<<1, 1024, smem, s>>>(reinterpret_cast<float *>(d), ld, n, kb);
+  }
+  APSP_LAUNCH_CHECK();
+  return APSP_OK;
+}
+
+// Closes the n x n block at d (16-byte aligned, ld % 4 == 0, already normalised) in place.
+int fw_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, cudaStream_t s) {
+  if (n == 0) return APSP_OK;
+  CUtensorMap mA, mB, mC;
+  int r;
+  if ((r = make_operand_maps(d, n, n, ld, dtype, &mA, &mB, &mC))) return r;
+  const int64_t nb = cdiv(n, kBM);
+  TileProblem p = {};
+  p.n = n;
+  p.nb = nb;
+  p.C = d;
+  p.ldc = ld;
+  p.inf_i = inf_i;
+  p.status = status_word();
+  for (int64_t kb = 0; kb < nb; ++kb) {
+    if ((r = launch_fw_diag(d, ld, n, kb, dtype, s))) return r;
+    if (nb == 1) break;
+    p.kb = kb;
+    p.ntiles = 2 * (nb - 1);
+    if ((r = launch_tgemm(kModeFwPanels, false, dtype, mA, mB, mC, p, s))) return r;
+    p.ntiles = (nb - 1) * (nb - 1);
+    if ((r = launch_tgemm(kModeFwRest, true, dtype, mA, mB, mC, p, s))) return r;
+  }
+  return APSP_OK;
+}
+
+// Shared entry logic of apsp_fw and apsp_rkleene: validation, the workspace (caller's or
+// stream-ordered allocation), repacking when ld breaks 16-byte row alignment, a1, closure.
+int closure_entry(int algo, void *d, int64_t n, int64_t ld, int dtype, const void *inf, int param, void *ws,
+                  size_t ws_bytes, void *stream) {
+  if (!dtype_ok(dtype) || n < 0) return APSP_ERR_ARG;
+  if (n == 0) return APSP_OK;
+  if (!d || ld < n || reinterpret_cast<uintptr_t>(d) % 16 != 0) return APSP_ERR_ARG;
+  if (n > (int64_t)1 << 30) return APSP_ERR_ARG;
+  if (algo == 0 && param != 0 && param != kBM) return APSP_ERR_ARG;
+  if (algo == 1 && param != 0 && param < kBM) return APSP_ERR_ARG;
+  int inf_i = 0;
+  float inf_f = 0.f;
+  if (dtype == APSP_I32 ? resolve_inf_i32(inf, &inf_i) : resolve_inf_f32(inf, &inf_f)) return APSP_ERR_ARG;
+  const size_t need = closure_workspace_bytes(algo, n, ld, param);
+  if (ws && (ws_bytes < need || reinterpret_cast<uintptr_t>(ws) % 256 != 0)) return APSP_ERR_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  void *own = nullptr;
+  if (!ws && need > 0) {
+    if (cudaMallocAsync(&own, need, s) != cudaSuccess) {
+      cudaGetLastError();
+      return APSP_ERR_NOMEM;
+    }
+    ws = own;
+  }
+  int r = APSP_OK;
+  uint8_t *wsp = reinterpret_cast<uint8_t *>(ws);
+  void *work = d;
+  int64_t ldw = ld;
+  if (ld % 4 != 0) {  // repack into an aligned copy at the front of the workspace
+    ldw = round_up(n, 4);
+    work = wsp;
+    wsp += round_up(n * ldw * 4, 256);
+    r = launch_copy2d(work, ldw, d, ld, n, n, s);
+  }
+  if (!r) r = launch_normalise(work, n, ldw, dtype, inf_i, inf_f, s);
+  if (!r) r = algo == 0 ? fw_closure(work, n, ldw, dtype, inf_i, s)
+                        : rkleene_closure(work, n, ldw, dtype, inf_i, param ? param : 256, wsp, s);
+  if (!r && work != d) r = launch_copy2d(d, ld, work, ldw, n, n, s);
+  if (own) cudaFreeAsync(own, s);
+  return r;
+}
+
+size_t closure_workspace_bytes(int algo, int64_t n, int64_t ld, int param) {
+  if (n <= 0) return 0;
+  size_t b = 0;
+  if (ld % 4 != 0) b += (size_t)round_up(n * round_up(n, 4) * 4, 256);
+  if (algo == 1) b += rkleene_scratch_bytes(n, param ? param : 256);
+  return b;
+}
+
+}  // namespace apsp
+
+extern "C" size_t apsp_fw_workspace_bytes(int64_t n, int64_t ld, int dtype, int tile) {
+  (void)dtype; (void)tile;
+  return apsp::closure_workspace_bytes(0, n, ld, 0);
+}
+
+extern "C" int apsp_fw(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int tile, void *ws,
+                       size_t ws_bytes, void *stream) {
+  return apsp::closure_entry(0, d, n, ld, dtype, inf, tile, ws, ws_bytes, stream);
+}

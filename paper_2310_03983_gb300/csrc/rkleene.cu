@@ -1,0 +1,84 @@
+// rkleene.cu -- a6: R-Kleene closure (Sec. 3.3, Eq. 4).
+//
+// The matrix is split as H = [[A, B], [C, D]] (A: first h vertices, D: the rest) and closed by
+//     A = A*;  B = A (x) B;  C = C (x) A;  D = min(D, C (x) B);
+//     D = D*;  B = B (x) D;  C = D (x) C;  A = min(A, B (x) C)
+// recursing on A and D until a block has at most `cutoff` vertices, which blocked
+// Floyd-Warshall closes.  The split h is ceil(m/2) rounded up to a multiple of 128, so every
+// block starts on a TMA-aligned boundary.  Products whose output is also an operand
+// (B = A (x) B, C = C (x) A, B = B (x) D, C = D (x) C) first copy that operand to scratch, so
+// no CTA reads a tile another CTA is writing; the closed factor has a zero diagonal, so the
+// plain product already includes the old entry and needs no extra min.
+#include "closure.cuh"
+
+namespace apsp {
+
+static int64_t split_of(int64_t m) { return round_up(cdiv(m, 2), kBM); }
+
+size_t rkleene_scratch_bytes(int64_t n, int cutoff) {
+  if (n <= cutoff) return 0;
+  const int64_t h = split_of(n);
+  return (size_t)round_up(h * round_up(h, 4) * 4, 256);
+}
+
+int gemm_aligned(void *C, int64_t ldc, const void *A, int64_t lda, const void *B, int64_t ldb, int64_t M, int64_t N,
+                 int64_t K, int dtype, bool acc, int inf_i, cudaStream_t s) {
+  if (M == 0 || N == 0) return APSP_OK;
+  CUtensorMap mA, mB, mC;
+  int r;
+  if ((r = make_operand_maps(A, M, K, lda, dtype, &mA, nullptr, nullptr))) return r;
+  if ((r = make_operand_maps(B, K, N, ldb, dtype, nullptr, &mB, nullptr))) return r;
+  if ((r = make_operand_maps(C, M, N, ldc, dtype, nullptr, nullptr, &mC))) return r;
+  TileProblem p = {};
+  p.M = M; p.N = N; p.K = K;
+  p.tiles_m = cdiv(M, kBM);
+  p.tiles_n = cdiv(N, kBN);
+  p.ntiles = p.tiles_m * p.tiles_n;
+  p.C = C;
+  p.ldc = ldc;
+  p.inf_i = inf_i;
+  p.status = status_word();
+  return launch_tgemm(kModeGemm, acc, dtype, mA, mB, mC, p, s);
+}
+
+static int rk(uint8_t *d, int64_t m, int64_t ld, int dtype, int inf_i, int cutoff, uint8_t *W, cudaStream_t s) {
+  if (m <= cutoff) return fw_closure(d, m, ld, dtype, inf_i, s);
+  const int64_t h = split_of(m), r2 = m - h;
+  const int64_t es = 4;
+  uint8_t *A = d, *B = d + h * es, *C = d + h * ld * es, *D = d + (h * ld + h) * es;
+  int r;
+  // First half closed; paths through it update B, C, D.
+  if ((r = rk(A, h, ld, dtype, inf_i, cutoff, W, s))) return r;
+  int64_t ldw = round_up(r2, 4);
+  if ((r = launch_copy2d(W, ldw, B, ld, h, r2, s))) return r;                                     // W = B
+  if ((r = gemm_aligned(B, ld, A, ld, W, ldw, h, r2, h, dtype, false, inf_i, s))) return r;      // B = A (x) B
+  ldw = round_up(h, 4);
+  if ((r = launch_copy2d(W, ldw, C, ld, r2, h, s))) return r;                                     // W = C
+  if ((r = gemm_aligned(C, ld, W, ldw, A, ld, r2, h, h, dtype, false, inf_i, s))) return r;      // C = C (x) A
+  if ((r = gemm_aligned(D, ld, C, ld, B, ld, r2, r2, h, dtype, true, inf_i, s))) return r;       // D = min(D, C (x) B)
+  // Second half closed; paths through it update B, C, A.
+  if ((r = rk(D, r2, ld, dtype, inf_i, cutoff, W, s))) return r;
+  ldw = round_up(r2, 4);
+  if ((r = launch_copy2d(W, ldw, B, ld, h, r2, s))) return r;                                     // W = B
+  if ((r = gemm_aligned(B, ld, W, ldw, D, ld, h, r2, r2, dtype, false, inf_i, s))) return r;     // B = B (x) D
+  ldw = round_up(h, 4);
+  if ((r = launch_copy2d(W, ldw, C, ld, r2, h, s))) return r;                                     // W = C
+  if ((r = gemm_aligned(C, ld, D, ld, W, ldw, r2, h, r2, dtype, false, inf_i, s))) return r;     // C = D (x) C
+  return gemm_aligned(A, ld, B, ld, C, ld, h, h, r2, dtype, true, inf_i, s);                     // A = min(A, B (x) C)
+}
+
+int rkleene_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, int cutoff, void *scratch, cudaStream_t s) {
+  return rk(reinterpret_cast<uint8_t *>(d), n, ld, dtype, inf_i, cutoff, reinterpret_cast<uint8_t *>(scratch), s);
+}
+
+}  // namespace apsp
+
+extern "C" size_t apsp_rkleene_workspace_bytes(int64_t n, int64_t ld, int dtype, int cutoff) {
+  (void)dtype;
+  return apsp::closure_workspace_bytes(1, n, ld, cutoff);
+}
+
+extern "C" int apsp_rkleene(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int cutoff, void *ws,
+                            size_t ws_bytes, void *stream) {
+  return apsp::closure_entry(1, d, n, ld, dtype, inf, cutoff, ws, ws_bytes, stream);
+}

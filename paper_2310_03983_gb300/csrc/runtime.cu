@@ -1,0 +1,109 @@
+// runtime.cu -- host runtime of libapsp: status word, device queries, TMA descriptor
+// encoding, sentinel handling and the small C-ABI helpers.
+#include <math.h>
+#include <mutex>
+#include <string.h>
+
+#include "common.cuh"
+
+namespace apsp {
+
+__device__ unsigned int g_status = 0;
+
+unsigned int *status_word() {
+  static unsigned int *cached[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (!cached[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return nullptr;
+    cached[dev] = reinterpret_cast<unsigned int *>(p);
+  }
+  return cached[dev];
+}
+
+int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (cached[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+    cached[dev] = v;
+  }
+  return cached[dev];
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn get_encode() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+int make_tmap_2d(CUtensorMap *out, const void *base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                 int box_cols, int dtype) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return APSP_ERR_CUDA;
+  if (reinterpret_cast<uintptr_t>(base) % 16 != 0 || (ld * 4) % 16 != 0) return APSP_ERR_ARG;
+  // TMA needs non-zero extents; a zero-sized operand is never loaded, so any shape works.
+  cuuint64_t dims[2] = {(cuuint64_t)(cols > 0 ? cols : 1), (cuuint64_t)(rows > 0 ? rows : 1)};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUtensorMapDataType t = dtype == APSP_I32 ? CU_TENSOR_MAP_DATA_TYPE_INT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  CUresult r = enc(out, t, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? APSP_OK : APSP_ERR_CUDA;
+}
+
+int resolve_inf_i32(const void *inf, int *out) {
+  int v = inf ? *reinterpret_cast<const int *>(inf) : APSP_INF_I32;
+  if (v < 1 || v > APSP_INF_I32) return 1;
+  *out = v;
+  return 0;
+}
+
+int resolve_inf_f32(const void *inf, float *out) {
+  float v = inf ? *reinterpret_cast<const float *>(inf) : INFINITY;
+  if (!(v > 0.0f)) return 1;  // rejects NaN, zero and negatives
+  *out = v;
+  return 0;
+}
+
+}  // namespace apsp
+
+extern "C" int apsp_version(void) { return APSP_VERSION; }
+
+extern "C" const char *apsp_status_str(int s) {
+  switch (s) {
+    case APSP_OK: return "ok";
+    case APSP_ERR_ARG: return "invalid argument";
+    case APSP_ERR_DOMAIN: return "negative weight or NaN in the input";
+    case APSP_ERR_NOMEM: return "workspace allocation failed";
+    case APSP_ERR_CUDA: return "CUDA error";
+    case APSP_ERR_TIMEOUT: return "bounded device wait timed out";
+    case APSP_ERR_UNSUPPORTED: return "unsupported device or feature";
+    default: return "unknown status";
+  }
+}
+
+extern "C" int apsp_device_status(void *stream, int *out) {
+  if (!out) return APSP_ERR_ARG;
+  APSP_CUDA_TRY(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+  unsigned int bits = 0, zero = 0;
+  APSP_CUDA_TRY(cudaMemcpyFromSymbol(&bits, apsp::g_status, sizeof(bits)));
+  APSP_CUDA_TRY(cudaMemcpyToSymbol(apsp::g_status, &zero, sizeof(zero)));
+  *out = (bits & (1u << APSP_ERR_TIMEOUT)) ? APSP_ERR_TIMEOUT : (bits & (1u << APSP_ERR_DOMAIN)) ? APSP_ERR_DOMAIN : APSP_OK;
+  return APSP_OK;
+}

@@ -1,0 +1,470 @@
+// tgemm.cu -- register-tiled (min,+) product on CUDA cores (the paper's Eq. 2, Sec. 3).
+//
+//   C[i][j] = min( C[i][j] or INF,  min_k A[i][k] + B[k][j] )
+//
+// The paper forms the whole N x N x N tensor of sums and reduces it with a library min
+// (Sec. 3.1); that costs n^3 memory and capped its graphs at 1000 vertices.  Here the same
+// reduction is blocked so that nothing but the n x n operands ever lives in HBM:
+//
+//  * A persistent grid (one CTA per SM, 288 threads) walks a list of 128 x 128 output tiles.
+//  * Warp 8 is the producer: one elected lane issues TMA copies of the 128 x 32 A slab and
+//    the 32 x 128 B slab of each k-step into a 4-stage shared-memory ring (mbarrier
+//    full/empty handshakes), and, when folding into an existing C, the 128 x 128 C tile.
+//  * Warps 0-7 are consumers: each thread owns an 8 x 8 register tile of C (rows
+//    tm + 16 i, columns 4 tn + q + 64 h), reads A as 128-bit row quads (a broadcast within
+//    each quarter-warp) and B as 128-bit column quads (eight lanes cover 32 banks), and
+//    performs one add and one min per (i, j, k): on int32 with the fused DPX add-min, on
+//    fp32 as two adds feeding one 3-input min.
+//  * Epilogue: min with the prefetched C tile, 128-bit coalesced stores.
+//
+// No tensor cores: (min,+) is not a multiply-accumulate.  int32 results are exact; fp32
+// results are bitwise deterministic (min is exact, each candidate sum is one rounding).
+#include <math.h>
+#include <utility>
+
+#include "tgemm.cuh"
+
+namespace apsp {
+
+#ifndef APSP_I32_SEQ
+#define APSP_I32_SEQ 0  // 0: two fused add-mins; 1: two adds then one 3-input min
+#endif
+
+struct TileCoords {
+  int a_row, a_col, b_row, b_col, c_row, c_col;
+  int m_valid, n_valid, k_len;
+};
+
+template <int MODE>
+__device__ __forceinline__ TileCoords tile_coords(const TileProblem &p, int64_t t) {
+  TileCoords tc;
+  if (MODE == kModeGemm) {
+    // Grouped rasterisation: 8 tile-rows advance together so A slabs are reused from L2.
+    const int64_t G = 8;
+    const int64_t per_group = G * p.tiles_n;
+    const int64_t g = t / per_group;
+    const int64_t first_m = g * G;
+    const int64_t gsz = (p.tiles_m - first_m) < G ? (p.tiles_m - first_m) : G;
+    const int64_t r = t - g * per_group;
+    const int m0 = (int)((first_m + r % gsz) * kBM);
+    const int n0 = (int)((r / gsz) * kBN);
+    tc.a_row = m0; tc.a_col = 0;
+    tc.b_row = 0;  tc.b_col = n0;
+    tc.c_row = m0; tc.c_col = n0;
+    tc.m_valid = (int)(p.M - m0 < kBM ? p.M - m0 : kBM);
+    tc.n_valid = (int)(p.N - n0 < kBN ? p.N - n0 : kBN);
+    tc.k_len = (int)p.K;
+  } else {
+    const int64_t nb1 = p.nb - 1;
+    const int kb0 = (int)(p.kb * kBM);
+    const int bk = (int)(p.n - kb0 < kBM ? p.n - kb0 : kBM);
+    int i, j;
+    if (MODE == kModeFwPanels) {
+      if (t < nb1) {  // row panel tile (kb, j): D[kb][j] = D[kb][kb]* (x) D[kb][j]
+        j = (int)(t + (t >= p.kb));
+        tc.a_row = kb0; tc.a_col = kb0;
+        tc.b_row = kb0; tc.b_col = j * kBN;
+        tc.c_row = kb0; tc.c_col = j * kBN;
+      } else {        // column panel tile (i, kb): D[i][kb] = D[i][kb] (x) D[kb][kb]*
+        i = (int)(t - nb1);
+        i += (i >= p.kb);
+        tc.a_row = i * kBM; tc.a_col = kb0;
+        tc.b_row = kb0;     tc.b_col = kb0;
+        tc.c_row = i * kBM; tc.c_col = kb0;
+      }
+    } else {          // D[i][j] = min(D[i][j], D[i][kb] (x) D[kb][j]), i, j != kb
+      i = (int)(t / nb1);
+      j = (int)(t - (int64_t)i * nb1);
+      i += (i >= p.kb);
+      j += (j >= p.kb);
+      tc.a_row = i * kBM; tc.a_col = kb0;
+      tc.b_row = kb0;     tc.b_col = j * kBN;
+      tc.c_row = i * kBM; tc.c_col = j * kBN;
+    }
+    tc.m_valid = (int)(p.n - tc.c_row < kBM ? p.n - tc.c_row : kBM);
+    tc.n_valid = (int)(p.n - tc.c_col < kBN ? p.n - tc.c_col : kBN);
+    tc.k_len = bk;
+  }
+  return tc;
+}
+
+// Two (min,+) pairs into one accumulator: c = min(c, a0 + b0, a1 + b1).
+template <typename T> struct Pair2;
+template <> struct Pair2<int> {
+  static __device__ __forceinline__ int f(int c, int a0, int b0, int a1, int b1) {
+#if APSP_I32_SEQ == 0
+    return __viaddmin_s32(a1, b1, __viaddmin_s32(a0, b0, c));
+#else
+    return __vimin3_s32(c, a0 + b0, a1 + b1);
+#endif
+  }
+};
+template <> struct Pair2<float> {
+  static __device__ __forceinline__ float f(float c, float a0, float b0, float a1, float b1) {
+    return Ops<float>::min3(c, __fadd_rn(a0, b0), __fadd_rn(a1, b1));
+  }
+};
+
+template <typename T> struct Bits;
+template <> struct Bits<int> {
+  static __device__ __forceinline__ int from(int v) { return v; }
+  static __device__ __forceinline__ int to(int v) { return v; }
+};
+template <> struct Bits<float> {
+  static __device__ __forceinline__ float from(int v) { return __int_as_float(v); }
+  static __device__ __forceinline__ int to(float v) { return __float_as_int(v); }
+};
+
+// One full 32-deep k-slab: acc[i][j] = min over k of A[r_i][k] + B[k][c_j].
+template <typename T>
+__device__ __forceinline__ void slab_full(const T *As, const T *Bs, int tm, int tn, T (&acc)[8][8]) {
+#pragma unroll
+  for (int q = 0; q < kBK / 4; ++q) {
+    T a[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int4 v = lds128(As + (tm + 16 * i) * kBK + 4 * q);
+      a[i][0] = Bits<T>::from(v.x); a[i][1] = Bits<T>::from(v.y);
+      a[i][2] = Bits<T>::from(v.z); a[i][3] = Bits<T>::from(v.w);
+    }
+#pragma unroll
+    for (int kk = 0; kk < 4; kk += 2) {
+      T b0[8], b1[8];
+      const T *r0 = Bs + (4 * q + kk) * kBN + 4 * tn;
+      const T *r1 = r0 + kBN;
+      int4 v;
+      v = lds128(r0);      b0[0] = Bits<T>::from(v.x); b0[1] = Bits<T>::from(v.y); b0[2] = Bits<T>::from(v.z); b0[3] = Bits<T>::from(v.w);
+      v = lds128(r0 + 64); b0[4] = Bits<T>::from(v.x); b0[5] = Bits<T>::from(v.y); b0[6] = Bits<T>::from(v.z); b0[7] = Bits<T>::from(v.w);
+      v = lds128(r1);      b1[0] = Bits<T>::from(v.x); b1[1] = Bits<T>::from(v.y); b1[2] = Bits<T>::from(v.z); b1[3] = Bits<T>::from(v.w);
+      v = lds128(r1 + 64); b1[4] = Bits<T>::from(v.x); b1[5] = Bits<T>::from(v.y); b1[6] = Bits<T>::from(v.z); b1[7] = Bits<T>::from(v.w);
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = Pair2<T>::f(acc[i][j], a[i][kk], b0[j], a[i][kk + 1], b1[j]);
+    }
+  }
+}
+
+// The ragged last slab of a tile (kc < 32 valid k), one k at a time.
+template <typename T>
+__device__ __forceinline__ void slab_part(const T *As, const T *Bs, int tm, int tn, int kc, T (&acc)[8][8]) {
+  for (int k = 0; k < kc; ++k) {
+    T a[8], b[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = As[(tm + 16 * i) * kBK + k];
+    const T *r = Bs + k * kBN + 4 * tn;
+    int4 v;
+    v = lds128(r);      b[0] = Bits<T>::from(v.x); b[1] = Bits<T>::from(v.y); b[2] = Bits<T>::from(v.z); b[3] = Bits<T>::from(v.w);
+    v = lds128(r + 64); b[4] = Bits<T>::from(v.x); b[5] = Bits<T>::from(v.y); b[6] = Bits<T>::from(v.z); b[7] = Bits<T>::from(v.w);
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = Ops<T>::mn(acc[i][j], Ops<T>::add(a[i], b[j]));
+  }
+}
+
+template <typename T> __device__ __forceinline__ T acc_init(const TileProblem &p);
+template <> __device__ __forceinline__ int acc_init<int>(const TileProblem &p) { return p.inf_i; }
+template <> __device__ __forceinline__ float acc_init<float>(const TileProblem &p) { return __int_as_float(0x7f800000); }
+
+template <typename T, int MODE, bool ACC>
+__global__ void __launch_bounds__(kThreads, 1)
+    tgemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
+                 const __grid_constant__ CUtensorMap mC, const TileProblem p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  T *sA = reinterpret_cast<T *>(smem);
+  T *sB = reinterpret_cast<T *>(smem + kStages * kAStageBytes);
+  T *sC = reinterpret_cast<T *>(smem + kStages * (kAStageBytes + kBStageBytes));
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * (kAStageBytes + kBStageBytes) + kCBytes);
+  uint64_t *full = bars, *empty = bars + kStages, *cfull = bars + 2 * kStages, *cempty = cfull + 1;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kConsumerWarps);
+    }
+    mbar_init(cfull, 1);
+    mbar_init(cempty, kConsumerWarps);
+    fence_barrier_init();
+  }
+  __syncthreads();
+
+  if (warp == kConsumerWarps) {
+    // ------------------------------- producer --------------------------------------
+    if (lane == 0) {
+      tma_prefetch_desc(&mA);
+      tma_prefetch_desc(&mB);
+      if (ACC) tma_prefetch_desc(&mC);
+      int stage = 0;
+      uint32_t phase = 0, cphase = 0, issued = 0, issued_par = 0;
+      bool c_issued = false, ok = true;
+      uint32_t c_par = 0;
+      for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+        const TileCoords tc = tile_coords<MODE>(p, t);
+        const int nk = (tc.k_len + kBK - 1) / kBK;
+        for (int kt = 0; kt < nk; ++kt) {
+          if (!mbar_wait(&empty[stage], phase ^ 1, p.status)) { ok = false; break; }
+          mbar_arrive_expect_tx(&full[stage], kAStageBytes + kBStageBytes);
+          tma_load_2d(sA + stage * (kBM * kBK), &mA, tc.a_col + kt * kBK, tc.a_row, &full[stage]);
+          tma_load_2d(sB + stage * (kBK * kBN), &mB, tc.b_col, tc.b_row + kt * kBK, &full[stage]);
+          issued |= 1u << stage;
+          issued_par = (issued_par & ~(1u << stage)) | (phase << stage);
+          if (++stage == kStages) { stage = 0; phase ^= 1; }
+        }
+        if (ACC && ok) {
+          if (!mbar_wait(cempty, cphase ^ 1, p.status)) { ok = false; break; }
+          mbar_arrive_expect_tx(cfull, kCBytes);
+          tma_load_2d(sC, &mC, tc.c_col, tc.c_row, cfull);
+          c_issued = true;
+          c_par = cphase;
+          cphase ^= 1;
+        }
+      }
+      // Never leave a bulk copy writing into shared memory of an exiting CTA.
+      for (int s = 0; s < kStages; ++s)
+        if (issued & (1u << s)) mbar_wait(&full[s], (issued_par >> s) & 1, p.status);
+      if (c_issued) mbar_wait(cfull, c_par, p.status);
+    }
+    return;
+  }
+
+  // --------------------------------- consumers -------------------------------------
+  const int tm = (warp & 3) * 4 + (lane >> 3);
+  const int tn = (warp >> 2) * 8 + (lane & 7);
+  T *C = reinterpret_cast<T *>(p.C);
+  int stage = 0;
+  uint32_t phase = 0, cphase = 0;
+  for (int64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
+    const TileCoords tc = tile_coords<MODE>(p, t);
+    const int nk = (tc.k_len + kBK - 1) / kBK;
+    T acc[8][8];
+    const T init = acc_init<T>(p);
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = init;
+    bool ok = true;
+    for (int kt = 0; kt < nk; ++kt) {
+      if (!mbar_wait(&full[stage], phase, p.status)) { ok = false; break; }
+      const T *As = sA + stage * (kBM * kBK);
+      const T *Bs = sB + stage * (kBK * kBN);
+      const int kc = tc.k_len - kt * kBK;
+      if (kc >= kBK) slab_full<T>(As, Bs, tm, tn, acc);
+      else slab_part<T>(As, Bs, tm, tn, kc, acc);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[stage]);
+      if (++stage == kStages) { stage = 0; phase ^= 1; }
+    }
+    if (!ok) return;
+    if (ACC) {
+      if (!mbar_wait(cfull, cphase, p.status)) return;
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int4 v = lds128(sC + (tm + 16 * i) * kBN + 4 * tn + 64 * h);
+          acc[i][4 * h + 0] = Ops<T>::mn(acc[i][4 * h + 0], Bits<T>::from(v.x));
+          acc[i][4 * h + 1] = Ops<T>::mn(acc[i][4 * h + 1], Bits<T>::from(v.y));
+          acc[i][4 * h + 2] = Ops<T>::mn(acc[i][4 * h + 2], Bits<T>::from(v.z));
+          acc[i][4 * h + 3] = Ops<T>::mn(acc[i][4 * h + 3], Bits<T>::from(v.w));
+        }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(cempty);
+      cphase ^= 1;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int rl = tm + 16 * i;
+      if (rl >= tc.m_valid) continue;
+      T *crow = C + (int64_t)(tc.c_row + rl) * p.ldc + tc.c_col;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int cl = 4 * tn + 64 * h;
+        if (cl + 3 < tc.n_valid) {
+          int4 v = make_int4(Bits<T>::to(acc[i][4 * h]), Bits<T>::to(acc[i][4 * h + 1]),
+                             Bits<T>::to(acc[i][4 * h + 2]), Bits<T>::to(acc[i][4 * h + 3]));
+          *reinterpret_cast<int4 *>(crow + cl) = v;
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (cl + q < tc.n_valid) crow[cl + q] = acc[i][4 * h + q];
+        }
+      }
+    }
+  }
+}
+
+template <typename T, int MODE, bool ACC>
+static int launch_one(const CUtensorMap &mA, const CUtensorMap &mB, const CUtensorMap &mC, const TileProblem &p,
+                      cudaStream_t s) {
+  auto k = tgemm_kernel<T, MODE, ACC>;
+  APSP_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes + 1024));
+  const int64_t sms = sm_count();
+  const int grid = (int)(p.ntiles < sms ? p.ntiles : sms);
+  k<<<grid, kThreads, kSmemBytes + 1024, s>>>(mA, mB, mC, p);
+  APSP_LAUNCH_CHECK();
+  return APSP_OK;
+}
+
+template <typename T>
+static int launch_t(int mode, bool acc, const CUtensorMap &mA, const CUtensorMap &mB, const CUtensorMap &mC,
+                    const TileProblem &p, cudaStream_t s) {
+  switch (mode * 2 + (acc ? 1 : 0)) {
+    case 0: return launch_one<T, kModeGemm, false>(mA, mB, mC, p, s);
+    case 1: return launch_one<T, kModeGemm, true>(mA, mB, mC, p, s);
+    case 2: return launch_one<T, kModeFwPanels, false>(mA, mB, mC, p, s);
+    case 5: return launch_one<T, kModeFwRest, true>(mA, mB, mC, p, s);
+    default: return APSP_ERR_ARG;
+  }
+}
+
+int launch_tgemm(int mode, bool acc, int dtype, const CUtensorMap &mA, const CUtensorMap &mB, const CUtensorMap &mC,
+                 const TileProblem &p, cudaStream_t s) {
+  if (p.ntiles <= 0) return APSP_OK;
+  return dtype == APSP_I32 ? launch_t<int>(mode, acc, mA, mB, mC, p, s) : launch_t<float>(mode, acc, mA, mB, mC, p, s);
+}
+
+int make_operand_maps(const void *base, int64_t rows, int64_t cols, int64_t ld, int dtype, CUtensorMap *mA,
+                      CUtensorMap *mB, CUtensorMap *mC) {
+  int r;
+  if (mA && (r = make_tmap_2d(mA, base, rows, cols, ld, kBM, kBK, dtype))) return r;
+  if (mB && (r = make_tmap_2d(mB, base, rows, cols, ld, kBK, kBN, dtype))) return r;
+  if (mC && (r = make_tmap_2d(mC, base, rows, cols, ld, kBM, kBN, dtype))) return r;
+  return APSP_OK;
+}
+
+// ------------------------------ generic fallback --------------------------------------
+// Plain-load tiled kernel for operands that break TMA's 16-byte rules.  64 x 64 tiles,
+// 16-deep k-slabs, 4 x 4 register tile per thread; out-of-range k reads as INF.
+template <typename T>
+__global__ void __launch_bounds__(256) tgemm_generic_kernel(T *C, const T *A, const T *B, int64_t M, int64_t N,
+                                                            int64_t K, int64_t lda, int64_t ldb, int64_t ldc, bool acc,
+                                                            T inf) {
+  __shared__ T As[64][17];
+  __shared__ T Bs[16][64];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t m0 = (int64_t)blockIdx.y * 64, n0 = (int64_t)blockIdx.x * 64;
+  T c[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) c[i][j] = inf;
+  for (int64_t k0 = 0; k0 < K; k0 += 16) {
+    for (int e = threadIdx.x; e < 64 * 16; e += 256) {
+      const int r = e >> 4, k = e & 15;
+      const int64_t gm = m0 + r, gk = k0 + k;
+      As[r][k] = (gm < M && gk < K) ? A[gm * lda + gk] : inf;
+      const int kr = e >> 6, cn = e & 63;
+      const int64_t gk2 = k0 + kr, gn = n0 + cn;
+      Bs[kr][cn] = (gk2 < K && gn < N) ? B[gk2 * ldb + gn] : inf;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) c[i][j] = Ops<T>::mn(c[i][j], Ops<T>::add(As[ty + 16 * i][k], Bs[k][tx + 16 * j]));
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
+      if (gm < M && gn < N) {
+        T v = c[i][j];
+        if (acc) v = Ops<T>::mn(v, C[gm * ldc + gn]);
+        C[gm * ldc + gn] = v;
+      }
+    }
+}
+
+int launch_tgemm_generic(void *C, const void *A, const void *B, int64_t M, int64_t N, int64_t K, int64_t lda,
+                         int64_t ldb, int64_t ldc, int dtype, bool acc, int inf_i, float inf_f, cudaStream_t s) {
+  if (M == 0 || N == 0) return APSP_OK;
+  dim3 grid((unsigned)cdiv(N, 64), (unsigned)cdiv(M, 64));
+  if (grid.y > 65535) return APSP_ERR_ARG;
+  if (dtype == APSP_I32)
+    tgemm_generic_kernel<int><<<grid, 256, 0, s>>>((int *)C, (const int *)A, (const int *)B, M, N, K, lda, ldb, ldc,
+                                                   acc, inf_i);
+  else
+    tgemm_generic_kernel<float><<<grid, 256, 0, s>>>((float *)C, (const float *)A, (const float *)B, M, N, K, lda,
+                                                     ldb, ldc, acc, INFINITY);
+  APSP_LAUNCH_CHECK();
+  return APSP_OK;
+}
+
+// ------------------------------------ copy --------------------------------------------
+__global__ void __launch_bounds__(256) copy2d_kernel(int *dst, int64_t ldd, const int *src, int64_t lds, int64_t rows,
+                                                     int64_t cols, bool vec) {
+  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int *s = src + r * lds;
+    int *d = dst + r * ldd;
+    int64_t c0 = 0;
+    if (vec) {
+      for (int64_t v = threadIdx.x; v < (cols >> 2); v += blockDim.x)
+        reinterpret_cast<int4 *>(d)[v] = reinterpret_cast<const int4 *>(s)[v];
+      c0 = (cols >> 2) << 2;
+    }
+    for (int64_t c = c0 + threadIdx.x; c < cols; c += blockDim.x) d[c] = s[c];
+  }
+}
+
+int launch_copy2d(void *dst, int64_t ldd, const void *src, int64_t lds, int64_t rows, int64_t cols, cudaStream_t s) {
+  if (rows == 0 || cols == 0) return APSP_OK;
+  const bool vec = reinterpret_cast<uintptr_t>(dst) % 16 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0 &&
+                   ldd % 4 == 0 && lds % 4 == 0;
+  const int64_t cap = (int64_t)sm_count() * 8;
+  copy2d_kernel<<<(int)(rows < cap ? rows : cap), 256, 0, s>>>((int *)dst, ldd, (const int *)src, lds, rows, cols, vec);
+  APSP_LAUNCH_CHECK();
+  return APSP_OK;
+}
+
+}  // namespace apsp
+
+// ------------------------------------ C ABI -------------------------------------------
+extern "C" int tropical_gemm(void *C, const void *A, const void *B, int64_t M, int64_t N, int64_t K, int64_t lda,
+                             int64_t ldb, int64_t ldc, int dtype, const void *inf, int accumulate, void *stream) {
+  using namespace apsp;
+  if (!dtype_ok(dtype) || M < 0 || N < 0 || K < 0) return APSP_ERR_ARG;
+  if (M == 0 || N == 0) return APSP_OK;
+  if (!C || (K > 0 && (!A || !B)) || ldc < N || (K > 0 && (lda < K || ldb < N))) return APSP_ERR_ARG;
+  if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX) return APSP_ERR_ARG;
+  // C must not overlap A or B (byte ranges of the strided extents).
+  auto span = [](const void *p, int64_t rows, int64_t cols, int64_t ld) {
+    return std::make_pair((uintptr_t)p, (uintptr_t)p + (uintptr_t)(((rows - 1) * ld + cols) * 4));
+  };
+  auto cs = span(C, M, N, ldc);
+  if (K > 0) {
+    auto as = span(A, M, K, lda), bs = span(B, K, N, ldb);
+    if ((cs.first < as.second && as.first < cs.second) || (cs.first < bs.second && bs.first < cs.second))
+      return APSP_ERR_ARG;
+  }
+  int inf_i = 0;
+  float inf_f = 0.f;
+  if (dtype == APSP_I32 ? resolve_inf_i32(inf, &inf_i) : resolve_inf_f32(inf, &inf_f)) return APSP_ERR_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const bool aligned = (uintptr_t)C % 16 == 0 && (K == 0 || ((uintptr_t)A % 16 == 0 && (uintptr_t)B % 16 == 0)) &&
+                       ldc % 4 == 0 && (K == 0 || (lda % 4 == 0 && ldb % 4 == 0));
+  if (!aligned) return launch_tgemm_generic(C, A, B, M, N, K, lda, ldb, ldc, dtype, accumulate != 0, inf_i, inf_f, s);
+  CUtensorMap mA, mB, mC;
+  int r;
+  if ((r = make_operand_maps(K > 0 ? A : C, K > 0 ? M : 1, K > 0 ? K : 4, K > 0 ? lda : 4, dtype, &mA, nullptr, nullptr)))
+    return r;
+  if ((r = make_operand_maps(K > 0 ? B : C, K > 0 ? K : 1, N, K > 0 ? ldb : ldc, dtype, nullptr, &mB, nullptr))) return r;
+  if ((r = make_operand_maps(C, M, N, ldc, dtype, nullptr, nullptr, &mC))) return r;
+  TileProblem p = {};
+  p.M = M; p.N = N; p.K = K;
+  p.tiles_m = cdiv(M, kBM);
+  p.tiles_n = cdiv(N, kBN);
+  p.ntiles = p.tiles_m * p.tiles_n;
+  p.C = C;
+  p.ldc = ldc;
+  p.inf_i = inf_i;
+  p.inf_f = inf_f;
+  p.status = status_word();
+  return launch_tgemm(kModeGemm, accumulate != 0, dtype, mA, mB, mC, p, s);
+}

@@ -1,0 +1,58 @@
+// tgemm.cuh -- the register-tiled (min,+) "tropical GEMM" engine shared by the standalone
+// product (Eq. 2), blocked Floyd-Warshall phases 2 and 3, and R-Kleene.
+#pragma once
+
+#include "common.cuh"
+
+namespace apsp {
+
+// CTA tile and pipeline shape.
+constexpr int kBM = 128, kBN = 128, kBK = 32, kStages = 4;
+constexpr int kConsumerWarps = 8;
+constexpr int kThreads = (kConsumerWarps + 1) * 32;  // 8 consumer warps + 1 TMA producer warp
+constexpr int kAStageBytes = kBM * kBK * 4;         // A tile [128 m][32 k]
+constexpr int kBStageBytes = kBK * kBN * 4;         // B tile [32 k][128 n]
+constexpr int kCBytes = kBM * kBN * 4;              // C tile [128 m][128 n]
+constexpr int kSmemBytes = kStages * (kAStageBytes + kBStageBytes) + kCBytes + 256;
+
+// Which tiles a launch visits and where their operands live.
+enum TileMode : int {
+  kModeGemm = 0,      // C (M x N) = [min(C,)] A (M x K) (x) B (K x N)
+  kModeFwPanels = 1,  // blocked-FW phase 2: row and column panels of block kb
+  kModeFwRest = 2,    // blocked-FW phase 3: every tile outside block row/column kb
+};
+
+struct TileProblem {
+  int64_t M, N, K;       // GEMM extents (kModeGemm)
+  int64_t tiles_m, tiles_n;
+  int64_t n;             // FW: matrix order
+  int64_t kb, nb;        // FW: current diagonal block and number of blocks (block = 128)
+  void *C;               // output base (GEMM: C; FW: the matrix)
+  int64_t ldc;
+  int64_t ntiles;
+  int inf_i;
+  float inf_f;
+  unsigned int *status;
+};
+
+// Launch one tile pass.  acc: fold into the existing C (min) instead of overwriting it.
+// maps: A box 128 rows x 32 cols, B box 32 rows x 128 cols, C box 128 x 128.
+int launch_tgemm(int mode, bool acc, int dtype, const CUtensorMap &mA, const CUtensorMap &mB, const CUtensorMap &mC,
+                 const TileProblem &p, cudaStream_t s);
+
+// Generic (any alignment, any leading dimension) tropical GEMM used when TMA's alignment
+// rules do not hold.  Same semantics as tropical_gemm.
+int launch_tgemm_generic(void *C, const void *A, const void *B, int64_t M, int64_t N, int64_t K, int64_t lda,
+                         int64_t ldb, int64_t ldc, int dtype, bool acc, int inf_i, float inf_f, cudaStream_t s);
+
+// Tensor maps for a row-major matrix used as A, B and C operands.
+int make_operand_maps(const void *base, int64_t rows, int64_t cols, int64_t ld, int dtype, CUtensorMap *mA,
+                      CUtensorMap *mB, CUtensorMap *mC);
+
+// Strided 2-D copy (rows x cols elements of 4 bytes), used for operand copies.
+int launch_copy2d(void *dst, int64_t ldd, const void *src, int64_t lds, int64_t rows, int64_t cols, cudaStream_t s);
+
+// a1 launcher (normalise.cu)
+int launch_normalise(void *d, int64_t n, int64_t ld, int dtype, int inf_i, float inf_f, cudaStream_t s);
+
+}  // namespace apsp
