@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Throughput of exact all-pairs shortest paths on GB300, one JSON line on stdout.
+
+Default workload (the headline): one blocked Floyd-Warshall closure per step of a directed
+Erdos-Renyi graph with n = 32768 vertices, edge probability 0.05, int32 weights uniform in
+[1, 100], missing edges 0x3FFFFFFF, diagonal 0 (a 4 GiB int32 matrix).  Metric: (min,+)
+Gop/s = 2 n^3 / time per closure (one add and one min per (i, j, k), Eq. 1).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Each step closes its own copy of the input, already resident in HBM before the timed region
+(the copies are 4 GiB each, far larger than the 129 MB L2, so no flush is needed).  Under
+torchrun every rank closes its own replica (no data-path collective: "scaling": "weak"),
+the time is the max over ranks and the value sums all ranks' work.
+
+--impl reference times the CPU oracle (the plain k-i-j triple loop of oracle/) on the host
+cores, on a bounded sample of the same workload: the loop over a prefix of the intermediate
+vertices k of the same n x n matrix, converted to the same unit.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+WORKLOADS = {
+    "apsp_fw_n32768": dict(n=32768, p=0.05, dtype="int32", dist="uniform", lo=1, hi=100, algo="fw"),
+    "apsp_rkleene_n32768": dict(n=32768, p=0.05, dtype="int32", dist="uniform", lo=1, hi=100, algo="rkleene",
+                                param=256),
+    "tgemm_n32768": dict(n=32768, p=0.05, dtype="int32", dist="uniform", lo=1, hi=100, algo="gemm"),
+    "apsp_fw_n32768_f32": dict(n=32768, p=0.05, dtype="float32", dist="uniform01", lo=0, hi=1, algo="fw"),
+    "apsp_fw_n4096": dict(n=4096, p=0.5, dtype="int32", dist="uniform", lo=1, hi=1000, algo="fw"),
+}
+SMS_NOMINAL = 152
+LANES_PER_SM = 128
+MAX_SM_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="apsp_fw_n32768", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def gen_input(w):
+    dist = w["dist"]
+    if w["dtype"] == "int32":
+        return workloads.er_graph(w["n"], w["p"], "int32", lo=w["lo"], hi=w["hi"], seed=0)
+    if dist == "uniform01":
+        return workloads.er_graph(w["n"], w["p"], "float32", dist="uniform01", seed=0)
+    return workloads.er_graph(w["n"], w["p"], "float32", dist=dist, lo=w["lo"], hi=w["hi"], seed=0)
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU leg
+def cpu_sample(h, seconds: float, cores: int):
+    """Time the oracle's Eq. 1 loop over a prefix of the intermediate vertices of the same
+    matrix; return (Gop/s, cores, description)."""
+    import oracle
+    n = h.shape[0]
+    if h.dtype == np.int32:
+        d = np.minimum(h.astype(np.int64), workloads.INF_I32)
+    else:
+        d = h.astype(np.float64)
+    np.fill_diagonal(d, 0)
+    k, done, t_total = 0, 0, 0.0
+    step = 1
+    while t_total < seconds and k < n:
+        k1 = min(n, k + step)
+        t0 = time.perf_counter()
+        oracle.fw_steps(d, k, k1, threads=cores)
+        dt = time.perf_counter() - t0
+        t_total += dt
+        done += k1 - k
+        k = k1
+        if dt < seconds / 8:
+            step *= 2
+    ops = 2.0 * n * n * done
+    desc = (f"oracle k-i-j loop (Eq. 1, int64/fp64) over intermediate vertices 0..{done - 1} of the same "
+            f"n={n} matrix ({done}/{n} of the full closure), {t_total:.1f} s")
+    return ops / t_total / 1e9, desc
+
+
+def cores_available():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, w, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    cores = cores_available() if oracle.openmp_enabled() else 1
+    h = gen_input(w)
+    per_step = max(1.0, args.cpu_seconds / max(1, args.steps))
+    for _ in range(args.warmup):
+        cpu_sample(h, 0.2, cores)
+    vals, descs = [], []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, desc = cpu_sample(h, per_step, cores)
+        vals.append(v)
+        descs.append(desc)
+    wall = time.perf_counter() - t0
+    value = statistics.median(vals)
+    n = w["n"]
+    line = {
+        "impl": "reference", "metric": "(min,+) Gop/s (2n^3/s)", "value": round(value, 3), "unit": "Gop/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(2.0 * n ** 3 / (value * 1e9) * 1e3, 1), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "i64" if w["dtype"] == "int32" else "f64", "data": "synthetic",
+        "config": config_of(args, w, world),
+        "cpu_baseline": {"value": round(value, 3), "unit": "Gop/s", "cores": cores, "kind": "oracle",
+                         "sample": descs[-1]},
+        "e2e": {"value": round(value, 3), "unit": "Gop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": round(wall, 1),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_of(args, w, world):
+    c = {"workload": args.workload, "n": w["n"], "edge_p": w["p"], "weights": f"{w['dtype']} {w['dist']}"
+         f"[{w['lo']},{w['hi']}]", "algo": w["algo"], "graphs_per_step_per_gpu": 1,
+         "parallelism": f"replicas{world}", "l2": "inputs 4 GiB per step, larger than L2; no flush"}
+    if w["n"] < 32768:
+        c["l2"] = "inputs smaller than L2: L2 flushed between steps by a 256 MiB write"
+    if "param" in w:
+        c["param"] = w["param"]
+    return c
+
+
+# ----------------------------------------------------------------------------- GPU leg
+def run_ours(args, w, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    import paper_2310_03983_gb300 as apsp
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n = w["n"]
+    h = gen_input(w)
+    host = torch.from_numpy(h).pin_memory()
+    tdt = host.dtype
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+
+    def step_fn(buf, out=None):
+        if w["algo"] == "fw":
+            apsp.apsp_fw(buf)
+        elif w["algo"] == "rkleene":
+            apsp.apsp_rkleene(buf, cutoff=w.get("param", 256), ws=rk_ws)
+        else:
+            apsp.tropical_gemm(out, buf, buf, ws=gemm_ws)
+
+    rk_ws = None
+    if w["algo"] == "rkleene":
+        rk_ws = torch.empty(apsp.apsp_rkleene_workspace_bytes(n, n, tdt, w.get("param", 256)), dtype=torch.uint8,
+                            device=dev)
+    gemm_ws = torch.empty(256, dtype=torch.uint8, device=dev)
+    gemm_out = torch.empty((n, n), dtype=tdt, device=dev) if w["algo"] == "gemm" else None
+
+    # One resident copy per step (copies are far larger than L2).
+    mat_bytes = n * n * 4
+    free, _ = torch.cuda.mem_get_info(dev)
+    want = args.warmup + args.steps
+    pool = max(1, min(want, int(free * 0.7 // mat_bytes) - (1 if gemm_out is not None else 0)))
+    copies = [host.to(dev) for _ in range(pool)]
+    pristine = copies[0].clone() if pool < want else None
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev) if n < 32768 else None
+
+    def prepare(i):
+        if i < pool and pristine is None:
+            return copies[i]
+        buf = copies[i % pool]
+        buf.copy_(pristine)
+        return buf
+
+    torch.cuda.synchronize()
+    for i in range(args.warmup):
+        step_fn(prepare(i), gemm_out)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    time.sleep(0.3)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    apsp.apsp_trace_enable(True)
+    apsp.apsp_trace_read(-1)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for i in range(args.steps):
+        if flush is not None:
+            flush.zero_()
+        step_fn(prepare(args.warmup + i), gemm_out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    apsp.apsp_trace_enable(False)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    dom_mode = 0 if w["algo"] in ("gemm", "rkleene") else 2
+    k_ms, k_launches, k_pairs = apsp.apsp_trace_read(dom_mode)
+    all_ms, all_launches, _ = apsp.apsp_trace_read(-1) if False else (None, None, None)
+
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    ops_step = 2.0 * n ** 3
+    value = world * args.steps * ops_step / (ms_max * 1e-3) / 1e9
+
+    # End to end through the public API: pinned host matrix in, distances back to pinned host.
+    e2e_val = None
+    out_host = torch.empty((n, n), dtype=tdt).pin_memory()
+    if args.e2e_steps > 0:
+        if w["algo"] == "gemm":
+            e2e_ms = []
+            for _ in range(args.e2e_steps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                a = host.to(dev, non_blocking=True)
+                apsp.tropical_gemm(gemm_out, a, a, ws=gemm_ws)
+                out_host.copy_(gemm_out, non_blocking=True)
+                torch.cuda.synchronize()
+                e2e_ms.append((time.perf_counter() - t0) * 1e3)
+                del a
+        else:
+            e2e_ms = []
+            for _ in range(args.e2e_steps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                apsp.solve(host, algo=w["algo"], param=w.get("param", 0), out=out_host)
+                e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        te = torch.tensor([statistics.median(e2e_ms)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e_val = world * ops_step / (float(te.item()) * 1e-3) / 1e9
+
+    # Peak: one (min,+) pair per lane per clock (packed pair add + 3-input min = one issued
+    # instruction per pair), 128 lanes per SM.
+    peak_max = 2.0 * sms * LANES_PER_SM * MAX_SM_MHZ * 1e6 / 1e12
+    achieved = 2.0 * k_pairs / (k_ms * 1e-3) / 1e12 if k_ms > 0 else None
+    sm_mhz = clocks.get("sm_mhz")
+    nb = -(-n // 128)
+    launches_per_step = {"fw": 1 + 3 * nb, "gemm": 2, "rkleene": None}[w["algo"]]
+    line = {
+        "metric": "(min,+) Gop/s (2n^3/s)", "value": round(value, 2), "unit": "Gop/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "i32" if w["dtype"] == "int32" else "f32",
+        "arith": ("fp32 packed add + 3-input min on int32 bit patterns (exact: every distance < 2^24)"
+                  if w["dtype"] == "int32" else "fp32 packed add + 3-input min"),
+        "data": "synthetic", "config": config_of(args, w, world),
+        "roofline": {"bound": "alu", "kernel": {0: "tgemm_kernel (product)", 2: "tgemm_kernel (FW phase 3)"}[dom_mode],
+                     "achieved": round(achieved, 2) if achieved else None, "peak": round(peak_max, 2),
+                     "unit": "Tops/s", "frac": round(achieved / peak_max, 4) if achieved else None,
+                     "frac_at_observed_clock": (round(achieved / (peak_max * sm_mhz / MAX_SM_MHZ), 4)
+                                                if achieved and sm_mhz else None),
+                     "peak_basis": f"{sms} SMs x {LANES_PER_SM} lanes x 1 pair/lane/clk x {MAX_SM_MHZ:.0f} MHz x 2 ops",
+                     "launches": k_launches, "avg_launch_ms": round(k_ms / max(1, k_launches), 4),
+                     "traffic": None},
+        "clocks": clocks,
+        "e2e": {"value": round(e2e_val, 2) if e2e_val else None, "unit": "Gop/s",
+                "h2d_bytes_per_step": mat_bytes, "d2h_bytes_per_step": mat_bytes},
+        "gpu_launches": launches_per_step * args.steps if launches_per_step else None,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        cores = cores_available() if oracle.openmp_enabled() else 1
+        v, desc = cpu_sample(h, args.cpu_seconds, cores)
+        line["cpu_baseline"] = {"value": round(v, 3), "unit": "Gop/s", "cores": cores, "kind": "oracle",
+                                "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    w = WORKLOADS[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, w, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    rc = run_ours(args, w, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -93,10 +93,13 @@ int apsp_normalise(void *d, int64_t n, int64_t ld, int dtype, const void *inf, v
  * or B (APSP_ERR_ARG).  K = 0 gives C = inf (or leaves C unchanged when accumulating);
  * M = 0 or N = 0 is a no-op.  When every base is 16-byte aligned and every leading
  * dimension a multiple of 4, the TMA-fed engine runs; otherwise a plain-load kernel.
- * Needs no workspace. */
+ * int32: when the largest finite entries of A and B sum below 2^24 the product runs in
+ * exact fp32 arithmetic on the int32 bit patterns, else in int32; results are identical.
+ * The workspace (tropical_gemm_workspace_bytes) holds those two maxima. */
+size_t tropical_gemm_workspace_bytes(int64_t M, int64_t N, int64_t K, int dtype);
 int tropical_gemm(void *C, const void *A, const void *B, int64_t M, int64_t N, int64_t K,
                   int64_t lda, int64_t ldb, int64_t ldc, int dtype, const void *inf,
-                  int accumulate, void *stream);
+                  int accumulate, void *ws, size_t ws_bytes, void *stream);
 
 /* ---- a3-a5: blocked Floyd-Warshall (Eq. 1 organised over b x b tiles) -----------------
  * Closes d (n x n, leading dimension ld) in place: after the call d[i][j] is the shortest
@@ -105,8 +108,10 @@ int tropical_gemm(void *C, const void *A, const void *B, int64_t M, int64_t N, i
  * by a (min,+) product with the closed tile; phase 3 updates every other tile by
  * D[i][j] = min(D[i][j], D[i][kb] (x) D[kb][j]).
  * tile: block size b; 0 selects the default (128).  Supported: 128.
- * d must be 16-byte aligned.  The workspace is empty when ld is a multiple of 4; otherwise
- * it holds an aligned copy of the matrix (n x round_up(n, 4) elements). */
+ * d must be 16-byte aligned.  The workspace holds 256 bytes of bound words (int32 matrices
+ * whose (n - 1) * largest finite weight < 2^24 run in exact fp32 arithmetic on their bit
+ * patterns; others in int32) and, when ld is not a multiple of 4, an aligned copy of the
+ * matrix (n x round_up(n, 4) elements). */
 size_t apsp_fw_workspace_bytes(int64_t n, int64_t ld, int dtype, int tile);
 int apsp_fw(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int tile, void *ws,
             size_t ws_bytes, void *stream);
@@ -117,12 +122,23 @@ int apsp_fw(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int tile
  *   B = B (x) D;  C = D (x) C;  A = min(A, B (x) C).
  * Blocks of size <= cutoff are closed by blocked Floyd-Warshall.  The split point is a
  * multiple of 128.  cutoff: 0 selects the default (256); it must be >= 128.
- * d must be 16-byte aligned.  The workspace holds a copy of the block being overwritten
- * (h x round_up(h, 4) elements, h = ceil(n/2) rounded up to a multiple of 128, when
- * n > cutoff) plus, when ld is not a multiple of 4, an aligned copy of the matrix. */
+ * d must be 16-byte aligned.  The workspace holds the 256 bytes of bound words (as for
+ * apsp_fw), a copy of the block being overwritten (h x round_up(h, 4) elements,
+ * h = ceil(n/2) rounded up to a multiple of 128, when n > cutoff) and, when ld is not a
+ * multiple of 4, an aligned copy of the matrix. */
 size_t apsp_rkleene_workspace_bytes(int64_t n, int64_t ld, int dtype, int cutoff);
 int apsp_rkleene(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int cutoff,
                  void *ws, size_t ws_bytes, void *stream);
+
+/* ---- measurement: launch tracing ------------------------------------------------------
+ * apsp_trace_enable(1) makes every launch of the tropical GEMM engine (the standalone
+ * product and blocked-FW phases 2 and 3) record a CUDA event before and after itself on its
+ * stream.  apsp_trace_read(mode, ...) waits for those events, returns the summed elapsed
+ * time (ms), the number of launches and their algorithmic (min,+) pairs for engine mode
+ * `mode` (0 = product, 1 = FW panels, 2 = FW remaining tiles; -1 = all), then discards
+ * every record.  Host-global; not for use inside CUDA-graph capture. */
+int apsp_trace_enable(int on);
+int apsp_trace_read(int mode, double *total_ms, int64_t *launches, double *pairs);
 
 /* ---- measurement: CUDA-core (min,+) rate probe -----------------------------------------
  * Launches `blocks` x `threads` threads, each running `iters` rounds of a register-only
@@ -130,6 +146,7 @@ int apsp_rkleene(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int
  *   0: int32 fused add-min (__viaddmin_s32)      1: int32 add then 2-input min
  *   2: int32 two adds then 3-input min            3: fp32 add then 2-input min
  *   4: fp32 two adds then 3-input min             5: fp32 packed pair add then 3-input min
+ *   6: as 5 on subnormal operands (int32 bit patterns below 2^24 read as fp32)
  * Writes a checksum per thread to sink (device, blocks*threads int32) so nothing is dead
  * code.  Time it with events on `stream`; pairs performed = blocks*threads*iters*64. */
 int apsp_probe_minplus(int variant, int blocks, int threads, int iters, void *sink,

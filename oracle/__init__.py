@@ -7,7 +7,8 @@ nothing but the seeded inputs of ``workloads.py``.
 
 What is here, each citing the passage it follows:
   * ``fw``            -- Eq. 1 (Sec. 2) as the textbook k-i-j triple loop, in C (apsp_oracle.c),
-                         int64 for int32 inputs and fp64 for float32 inputs.
+                         int64 for int32 inputs and fp64 for float32 inputs; ``fw_steps`` runs
+                         the same loop over a range of intermediate vertices.
   * ``minplus``       -- Eq. 2 (Sec. 3), the (min,+) product, as a triple loop in C.
   * ``dijkstra_rows`` -- single-source distances from chosen sources by array Dijkstra: an
                          independent algorithm for the same definition, used to check large
@@ -59,13 +60,15 @@ def _bind(lib):
     f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
     I64, INT = ctypes.c_int64, ctypes.c_int
     lib.oracle_fw_i64.argtypes = [i64p, I64, I64, INT]
+    lib.oracle_fw_i64_steps.argtypes = [i64p, I64, I64, I64, I64, INT]
+    lib.oracle_fw_f64_steps.argtypes = [f64p, I64, I64, I64, INT]
     lib.oracle_fw_f64.argtypes = [f64p, I64, INT]
     lib.oracle_minplus_i64.argtypes = [i64p, i64p, i64p, I64, I64, I64, I64, INT]
     lib.oracle_minplus_f64.argtypes = [f64p, f64p, f64p, I64, I64, I64, INT]
     lib.oracle_dijkstra_rows_i64.argtypes = [i64p, I64, I64, i64p, I64, i64p, INT]
     lib.oracle_dijkstra_rows_f64.argtypes = [f64p, I64, i64p, I64, f64p, INT]
     lib.oracle_openmp_enabled.restype = INT
-    for f in ("oracle_fw_i64", "oracle_fw_f64", "oracle_minplus_i64", "oracle_minplus_f64",
+    for f in ("oracle_fw_i64", "oracle_fw_f64", "oracle_fw_i64_steps", "oracle_fw_f64_steps", "oracle_minplus_i64", "oracle_minplus_f64",
               "oracle_dijkstra_rows_i64", "oracle_dijkstra_rows_f64"):
         getattr(lib, f).restype = None
     return lib
@@ -106,6 +109,21 @@ def fw(h: np.ndarray, inf: int = INF_I32, threads: int | None = None, lib=None) 
         return d.astype(np.int32) if h.dtype == np.int32 else d
     d = np.ascontiguousarray(h, dtype=np.float64).copy()
     lib.oracle_fw_f64(d, n, _threads(threads))
+    return d
+
+
+def fw_steps(d: np.ndarray, k0: int, k1: int, inf: int = INF_I32, threads: int | None = None, lib=None):
+    """Run the Eq. 1 loop for intermediate vertices k in [k0, k1) in place on a prepared
+    matrix (int64 with threshold inf, or float64 with +inf; zero diagonal)."""
+    lib = lib or load()
+    n = d.shape[0]
+    assert d.flags.c_contiguous and d.shape == (n, n)
+    if d.dtype == np.int64:
+        lib.oracle_fw_i64_steps(d, n, int(inf), int(k0), int(k1), _threads(threads))
+    elif d.dtype == np.float64:
+        lib.oracle_fw_f64_steps(d, n, int(k0), int(k1), _threads(threads))
+    else:
+        raise TypeError("fw_steps needs an int64 or float64 matrix")
     return d
 
 

@@ -63,24 +63,19 @@ int oracle_openmp_enabled(void) {
 #endif
 }
 
-/* Eq. 1 over int64 with an "unreachable" threshold inf. In place on d (n x n). */
-void oracle_fw_i64(int64_t *d, int64_t n, int64_t inf, int threads) {
+/* The k-i-j loop of Eq. 1 for intermediate vertices k in [k0, k1), int64 with threshold inf.
+ * oracle_fw_i64 runs it for every k; the benchmark's CPU baseline times a prefix of it. */
+void oracle_fw_i64_steps(int64_t *d, int64_t n, int64_t inf, int64_t k0, int64_t k1, int threads) {
   set_threads(threads);
-  for (int64_t i = 0; i < n; ++i) {
-    for (int64_t j = 0; j < n; ++j)
-      if (d[i * n + j] >= inf) d[i * n + j] = inf;
-#if ORACLE_PLANT != 1 /* plant 1: forget that a vertex reaches itself at cost 0 */
-    d[i * n + i] = 0;
-#endif
-  }
 #if ORACLE_PLANT == 2 /* plant 2: intermediate vertex innermost (i-j-k): not Floyd-Warshall */
+  (void)k0; (void)k1;
   for (int64_t i = 0; i < n; ++i)
     for (int64_t j = 0; j < n; ++j)
       for (int64_t k = 0; k < n; ++k)
         if (d[i * n + k] < inf && d[k * n + j] < inf && d[i * n + k] + d[k * n + j] < d[i * n + j])
           d[i * n + j] = d[i * n + k] + d[k * n + j];
 #else
-  for (int64_t k = 0; k < n; ++k) {
+  for (int64_t k = k0; k < k1; ++k) {
     const int64_t *rowk = d + k * n;
 #pragma omp parallel for schedule(static) if (threads > 1)
     for (int64_t i = 0; i < n; ++i) {
@@ -100,15 +95,26 @@ void oracle_fw_i64(int64_t *d, int64_t n, int64_t inf, int threads) {
     }
   }
 #endif
+}
+
+/* Eq. 1 over int64 with an "unreachable" threshold inf. In place on d (n x n). */
+void oracle_fw_i64(int64_t *d, int64_t n, int64_t inf, int threads) {
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t j = 0; j < n; ++j)
+      if (d[i * n + j] >= inf) d[i * n + j] = inf;
+#if ORACLE_PLANT != 1 /* plant 1: forget that a vertex reaches itself at cost 0 */
+    d[i * n + i] = 0;
+#endif
+  }
+  oracle_fw_i64_steps(d, n, inf, 0, n, threads);
   for (int64_t i = 0; i < n * n; ++i)
     if (d[i] >= inf) d[i] = inf;
 }
 
-/* Eq. 1 over fp64 with +infinity as "unreachable". In place on d (n x n). */
-void oracle_fw_f64(double *d, int64_t n, int threads) {
+/* The k-i-j loop of Eq. 1 over fp64 for k in [k0, k1); +infinity = unreachable. */
+void oracle_fw_f64_steps(double *d, int64_t n, int64_t k0, int64_t k1, int threads) {
   set_threads(threads);
-  for (int64_t i = 0; i < n; ++i) d[i * n + i] = 0.0;
-  for (int64_t k = 0; k < n; ++k) {
+  for (int64_t k = k0; k < k1; ++k) {
     const double *rowk = d + k * n;
 #pragma omp parallel for schedule(static) if (threads > 1)
     for (int64_t i = 0; i < n; ++i) {
@@ -121,6 +127,12 @@ void oracle_fw_f64(double *d, int64_t n, int threads) {
       }
     }
   }
+}
+
+/* Eq. 1 over fp64 with +infinity as "unreachable". In place on d (n x n). */
+void oracle_fw_f64(double *d, int64_t n, int threads) {
+  for (int64_t i = 0; i < n; ++i) d[i * n + i] = 0.0;
+  oracle_fw_f64_steps(d, n, 0, n, threads);
 }
 
 /* Eq. 2: Z = X (x) Y, or Z = min(Z, X (x) Y) when accumulate != 0.

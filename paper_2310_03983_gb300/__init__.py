@@ -44,12 +44,16 @@ def _load():
         "apsp_status_str": ([i32], ctypes.c_char_p),
         "apsp_device_status": ([vp, ctypes.POINTER(i32)], i32),
         "apsp_normalise": ([vp, i64, i64, i32, vp, vp], i32),
-        "tropical_gemm": ([vp, vp, vp, i64, i64, i64, i64, i64, i64, i32, vp, i32, vp], i32),
+        "tropical_gemm_workspace_bytes": ([i64, i64, i64, i32], sz),
+        "tropical_gemm": ([vp, vp, vp, i64, i64, i64, i64, i64, i64, i32, vp, i32, vp, sz, vp], i32),
         "apsp_fw_workspace_bytes": ([i64, i64, i32, i32], sz),
         "apsp_fw": ([vp, i64, i64, i32, vp, i32, vp, sz, vp], i32),
         "apsp_rkleene_workspace_bytes": ([i64, i64, i32, i32], sz),
         "apsp_rkleene": ([vp, i64, i64, i32, vp, i32, vp, sz, vp], i32),
         "apsp_probe_minplus": ([i32, i32, i32, i32, vp, vp], i32),
+        "apsp_trace_enable": ([i32], i32),
+        "apsp_trace_read": ([i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
+                             ctypes.POINTER(ctypes.c_double)], i32),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -58,9 +62,10 @@ def _load():
 
 
 _lib = _load()
-EXPORTS = ("apsp_version", "apsp_status_str", "apsp_device_status", "apsp_normalise", "tropical_gemm",
+EXPORTS = ("apsp_version", "apsp_status_str", "apsp_device_status", "apsp_normalise",
+           "tropical_gemm_workspace_bytes", "tropical_gemm",
            "apsp_fw_workspace_bytes", "apsp_fw", "apsp_rkleene_workspace_bytes", "apsp_rkleene",
-           "apsp_probe_minplus")
+           "apsp_probe_minplus", "apsp_trace_enable", "apsp_trace_read")
 
 
 def lib():
@@ -118,7 +123,7 @@ def apsp_normalise(d: torch.Tensor, inf=None, stream=None):
 
 
 def tropical_gemm(C: torch.Tensor, A: torch.Tensor, B: torch.Tensor, accumulate: bool = False, inf=None,
-                  stream=None):
+                  ws: torch.Tensor | None = None, stream=None):
     """C = A (x) B, or C = min(C, A (x) B) when accumulate (Eq. 2)."""
     M, K = A.shape
     K2, N = B.shape
@@ -131,7 +136,8 @@ def tropical_gemm(C: torch.Tensor, A: torch.Tensor, B: torch.Tensor, accumulate:
     pa, lda = _mat(A, "A")
     pb, ldb = _mat(B, "B")
     ip, _keep = _inf_arg(inf, code)
-    _check(_lib.tropical_gemm(pc, pa, pb, M, N, K, lda, ldb, ldc, code, ip, int(bool(accumulate)),
+    wp, wb = (None, 0) if ws is None else (ws.data_ptr(), ws.numel() * ws.element_size())
+    _check(_lib.tropical_gemm(pc, pa, pb, M, N, K, lda, ldb, ldc, code, ip, int(bool(accumulate)), wp, wb,
                               _stream(stream)), "tropical_gemm")
     return C
 
@@ -172,7 +178,18 @@ def apsp_rkleene(d: torch.Tensor, inf=None, cutoff: int = 0, ws: torch.Tensor | 
 
 def apsp_probe_minplus(variant: int, blocks: int, threads: int, iters: int, sink: torch.Tensor, stream=None):
     _check(_lib.apsp_probe_minplus(variant, blocks, threads, iters, sink.data_ptr(), _stream(stream)),
-           "apsp_probe_minplus")
+           "apsp_probe_minplus", "apsp_trace_enable", "apsp_trace_read")
+
+
+def apsp_trace_enable(on: bool = True):
+    _check(_lib.apsp_trace_enable(int(bool(on))), "apsp_trace_enable")
+
+
+def apsp_trace_read(mode: int = -1):
+    """(total_ms, launches, pairs) of traced engine launches of `mode` since the last read."""
+    ms, n, pairs = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+    _check(_lib.apsp_trace_read(mode, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(pairs)), "apsp_trace_read")
+    return ms.value, n.value, pairs.value
 
 
 ALGOS = {"fw": apsp_fw, "rkleene": apsp_rkleene}

@@ -1,5 +1,6 @@
 """Build libapsp.so in-tree: every .cu under csrc/ for sm_103a, compiled in parallel, linked
-with nvcc.  Usage: python -m paper_2310_03983_gb300.build [--force] [-DNAME=VALUE ...]"""
+with nvcc.  Usage: python paper_2310_03983_gb300/build.py [--force] [-v] [-DNAME=VALUE ...]
+(run as a file: importing the package would load the library it is about to build)."""
 from __future__ import annotations
 
 import os

@@ -5,11 +5,19 @@
 
 namespace apsp {
 
+// Device bound words of a closure (see TileProblem::wmax): w[0] = largest finite weight,
+// mult = n - 1 of the whole graph.  w == nullptr for float32.
+struct Bound {
+  const int *w;
+  int64_t mult;
+};
+
 // Blocked Floyd-Warshall on an aligned, normalised block (fw.cu).
-int fw_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, cudaStream_t s);
+int fw_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bound b, cudaStream_t s);
 
 // R-Kleene on an aligned, normalised block, scratch of rkleene_scratch_bytes (rkleene.cu).
-int rkleene_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, int cutoff, void *scratch, cudaStream_t s);
+int rkleene_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, int cutoff, Bound b, void *scratch,
+                    cudaStream_t s);
 size_t rkleene_scratch_bytes(int64_t n, int cutoff);
 
 // algo 0 = FW, 1 = R-Kleene; param = tile (FW) or cutoff (R-Kleene).
@@ -19,6 +27,6 @@ size_t closure_workspace_bytes(int algo, int64_t n, int64_t ld, int param);
 
 // (min,+) product of aligned operands through the TMA engine (rkleene.cu).
 int gemm_aligned(void *C, int64_t ldc, const void *A, int64_t lda, const void *B, int64_t ldb, int64_t M, int64_t N,
-                 int64_t K, int dtype, bool acc, int inf_i, cudaStream_t s);
+                 int64_t K, int dtype, bool acc, int inf_i, Bound b, cudaStream_t s);
 
 }  // namespace apsp

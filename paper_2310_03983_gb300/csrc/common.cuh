@@ -57,6 +57,20 @@ template <> struct Ops<float> {
   }
 };
 
+// Packed pair add (PTX add.rn.f32x2, sm_100+): {a.x + b.x, a.y + b.y} in one instruction.
+// Subnormals are kept (no .ftz), which the exact small-integer path relies on.
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %5};\n\t"
+      "add.rn.f32x2 rd, ra, rb;\n\t"
+      "mov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+
 // ---------------------------------------------------------------------------------------
 // mbarrier / TMA wrappers (PTX ISA: mbarrier.*, cp.async.bulk.tensor.*)
 // ---------------------------------------------------------------------------------------

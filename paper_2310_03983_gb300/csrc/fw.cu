@@ -71,7 +71,7 @@ int launch_fw_diag(void *d, int64_t ld, int64_t n, int64_t kb, int dtype, cudaSt
 }
 
 // Closes the n x n block at d (16-byte aligned, ld % 4 == 0, already normalised) in place.
-int fw_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, cudaStream_t s) {
+int fw_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bound b, cudaStream_t s) {
   if (n == 0) return APSP_OK;
   CUtensorMap mA, mB, mC;
   int r;
@@ -84,6 +84,8 @@ int fw_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, cudaStream_
   p.ldc = ld;
   p.inf_i = inf_i;
   p.status = status_word();
+  p.wmax = b.w;
+  p.wmult = b.mult;
   for (int64_t kb = 0; kb < nb; ++kb) {
     if ((r = launch_fw_diag(d, ld, n, kb, dtype, s))) return r;
     if (nb == 1) break;
@@ -122,17 +124,21 @@ int closure_entry(int algo, void *d, int64_t n, int64_t ld, int dtype, const voi
   }
   int r = APSP_OK;
   uint8_t *wsp = reinterpret_cast<uint8_t *>(ws);
+  int *words = reinterpret_cast<int *>(wsp);  // [0]: largest finite weight, [1]: 0
+  wsp += kFlagBytes;
+  if (cudaMemsetAsync(words, 0, 16, s) != cudaSuccess) r = APSP_ERR_CUDA;
+  const Bound bound = {dtype == APSP_I32 ? words : nullptr, n - 1};
   void *work = d;
   int64_t ldw = ld;
   if (ld % 4 != 0) {  // repack into an aligned copy at the front of the workspace
     ldw = round_up(n, 4);
     work = wsp;
     wsp += round_up(n * ldw * 4, 256);
-    r = launch_copy2d(work, ldw, d, ld, n, n, s);
+    if (!r) r = launch_copy2d(work, ldw, d, ld, n, n, s);
   }
-  if (!r) r = launch_normalise(work, n, ldw, dtype, inf_i, inf_f, s);
-  if (!r) r = algo == 0 ? fw_closure(work, n, ldw, dtype, inf_i, s)
-                        : rkleene_closure(work, n, ldw, dtype, inf_i, param ? param : 256, wsp, s);
+  if (!r) r = launch_normalise(work, n, ldw, dtype, inf_i, inf_f, dtype == APSP_I32 ? words : nullptr, s);
+  if (!r) r = algo == 0 ? fw_closure(work, n, ldw, dtype, inf_i, bound, s)
+                        : rkleene_closure(work, n, ldw, dtype, inf_i, param ? param : 256, bound, wsp, s);
   if (!r && work != d) r = launch_copy2d(d, ld, work, ldw, n, n, s);
   if (own) cudaFreeAsync(own, s);
   return r;
@@ -140,7 +146,7 @@ int closure_entry(int algo, void *d, int64_t n, int64_t ld, int dtype, const voi
 
 size_t closure_workspace_bytes(int algo, int64_t n, int64_t ld, int param) {
   if (n <= 0) return 0;
-  size_t b = 0;
+  size_t b = kFlagBytes;
   if (ld % 4 != 0) b += (size_t)round_up(n * round_up(n, 4) * 4, 256);
   if (algo == 1) b += rkleene_scratch_bytes(n, param ? param : 256);
   return b;

@@ -24,9 +24,14 @@ template <> struct Norm<float> {
   }
 };
 
+template <typename T> __device__ __forceinline__ int finite_max(T v, T inf, int m) { return m; }
+template <> __device__ __forceinline__ int finite_max<int>(int v, int inf, int m) { return v < inf ? max(m, v) : m; }
+
 template <typename T>
-__global__ void __launch_bounds__(256) normalise_kernel(T *d, int64_t n, int64_t ld, T inf, bool vec, unsigned int *st) {
+__global__ void __launch_bounds__(256) normalise_kernel(T *d, int64_t n, int64_t ld, T inf, bool vec, unsigned int *st,
+                                                        int *wmax) {
   bool bad = false;
+  int m = 0;
   for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
     T *row = d + i * ld;
     int64_t j0 = 0;
@@ -37,25 +42,56 @@ __global__ void __launch_bounds__(256) normalise_kernel(T *d, int64_t n, int64_t
         float4 raw = *reinterpret_cast<float4 *>(p);
         T *e = reinterpret_cast<T *>(&raw);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) e[q] = (4 * v + q == i) ? T(0) : Norm<T>::fix(e[q], inf, bad);
+        for (int q = 0; q < 4; ++q) {
+          e[q] = (4 * v + q == i) ? T(0) : Norm<T>::fix(e[q], inf, bad);
+          m = finite_max<T>(e[q], inf, m);
+        }
         *reinterpret_cast<float4 *>(p) = raw;
       }
       j0 = nv << 2;
     }
-    for (int64_t j = j0 + threadIdx.x; j < n; j += blockDim.x) row[j] = (j == i) ? T(0) : Norm<T>::fix(row[j], inf, bad);
+    for (int64_t j = j0 + threadIdx.x; j < n; j += blockDim.x) {
+      row[j] = (j == i) ? T(0) : Norm<T>::fix(row[j], inf, bad);
+      m = finite_max<T>(row[j], inf, m);
+    }
+  }
+  if (wmax) {
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(wmax, m);
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) flag_status(st, APSP_ERR_DOMAIN);
 }
 
-int launch_normalise(void *d, int64_t n, int64_t ld, int dtype, int inf_i, float inf_f, cudaStream_t s) {
+__global__ void __launch_bounds__(256) scan_max_kernel(const int *x, int64_t rows, int64_t cols, int64_t ld, int inf,
+                                                       int *out) {
+  int m = 0;
+  for (int64_t i = blockIdx.x; i < rows; i += gridDim.x)
+    for (int64_t j = threadIdx.x; j < cols; j += blockDim.x) {
+      const int v = x[i * ld + j];
+      if (v < inf) m = max(m, v);
+    }
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(out, m);
+}
+
+int launch_scan_max(const void *x, int64_t rows, int64_t cols, int64_t ld, int inf, int *out, cudaStream_t s) {
+  if (rows == 0 || cols == 0) return APSP_OK;
+  const int64_t cap = (int64_t)sm_count() * 8;
+  scan_max_kernel<<<(int)(rows < cap ? rows : cap), 256, 0, s>>>(reinterpret_cast<const int *>(x), rows, cols, ld,
+                                                                 inf, out);
+  APSP_LAUNCH_CHECK();
+  return APSP_OK;
+}
+
+int launch_normalise(void *d, int64_t n, int64_t ld, int dtype, int inf_i, float inf_f, int *wmax, cudaStream_t s) {
   if (n == 0) return APSP_OK;
   const bool vec = (reinterpret_cast<uintptr_t>(d) % 16 == 0) && (ld % 4 == 0);
   const int64_t cap = (int64_t)sm_count() * 8;
   const int grid = (int)(n < cap ? n : cap);
   if (dtype == APSP_I32)
-    normalise_kernel<int><<<grid, 256, 0, s>>>(reinterpret_cast<int *>(d), n, ld, inf_i, vec, status_word());
+    normalise_kernel<int><<<grid, 256, 0, s>>>(reinterpret_cast<int *>(d), n, ld, inf_i, vec, status_word(), wmax);
   else
-    normalise_kernel<float><<<grid, 256, 0, s>>>(reinterpret_cast<float *>(d), n, ld, inf_f, vec, status_word());
+    normalise_kernel<float><<<grid, 256, 0, s>>>(reinterpret_cast<float *>(d), n, ld, inf_f, vec, status_word(), nullptr);
   APSP_LAUNCH_CHECK();
   return APSP_OK;
 }
@@ -68,5 +104,5 @@ extern "C" int apsp_normalise(void *d, int64_t n, int64_t ld, int dtype, const v
   int inf_i = 0;
   float inf_f = 0.f;
   if (dtype == APSP_I32 ? resolve_inf_i32(inf, &inf_i) : resolve_inf_f32(inf, &inf_f)) return APSP_ERR_ARG;
-  return launch_normalise(d, n, ld, dtype, inf_i, inf_f, reinterpret_cast<cudaStream_t>(stream));
+  return launch_normalise(d, n, ld, dtype, inf_i, inf_f, nullptr, reinterpret_cast<cudaStream_t>(stream));
 }

@@ -22,7 +22,7 @@ size_t rkleene_scratch_bytes(int64_t n, int cutoff) {
 }
 
 int gemm_aligned(void *C, int64_t ldc, const void *A, int64_t lda, const void *B, int64_t ldb, int64_t M, int64_t N,
-                 int64_t K, int dtype, bool acc, int inf_i, cudaStream_t s) {
+                 int64_t K, int dtype, bool acc, int inf_i, Bound b, cudaStream_t s) {
   if (M == 0 || N == 0) return APSP_OK;
   CUtensorMap mA, mB, mC;
   int r;
@@ -38,37 +38,41 @@ int gemm_aligned(void *C, int64_t ldc, const void *A, int64_t lda, const void *B
   p.ldc = ldc;
   p.inf_i = inf_i;
   p.status = status_word();
+  p.wmax = b.w;
+  p.wmult = b.mult;
   return launch_tgemm(kModeGemm, acc, dtype, mA, mB, mC, p, s);
 }
 
-static int rk(uint8_t *d, int64_t m, int64_t ld, int dtype, int inf_i, int cutoff, uint8_t *W, cudaStream_t s) {
-  if (m <= cutoff) return fw_closure(d, m, ld, dtype, inf_i, s);
+static int rk(uint8_t *d, int64_t m, int64_t ld, int dtype, int inf_i, int cutoff, Bound bd, uint8_t *W,
+              cudaStream_t s) {
+  if (m <= cutoff) return fw_closure(d, m, ld, dtype, inf_i, bd, s);
   const int64_t h = split_of(m), r2 = m - h;
   const int64_t es = 4;
   uint8_t *A = d, *B = d + h * es, *C = d + h * ld * es, *D = d + (h * ld + h) * es;
   int r;
   // First half closed; paths through it update B, C, D.
-  if ((r = rk(A, h, ld, dtype, inf_i, cutoff, W, s))) return r;
+  if ((r = rk(A, h, ld, dtype, inf_i, cutoff, bd, W, s))) return r;
   int64_t ldw = round_up(r2, 4);
   if ((r = launch_copy2d(W, ldw, B, ld, h, r2, s))) return r;                                     // W = B
-  if ((r = gemm_aligned(B, ld, A, ld, W, ldw, h, r2, h, dtype, false, inf_i, s))) return r;      // B = A (x) B
+  if ((r = gemm_aligned(B, ld, A, ld, W, ldw, h, r2, h, dtype, false, inf_i, bd, s))) return r;      // B = A (x) B
   ldw = round_up(h, 4);
   if ((r = launch_copy2d(W, ldw, C, ld, r2, h, s))) return r;                                     // W = C
-  if ((r = gemm_aligned(C, ld, W, ldw, A, ld, r2, h, h, dtype, false, inf_i, s))) return r;      // C = C (x) A
-  if ((r = gemm_aligned(D, ld, C, ld, B, ld, r2, r2, h, dtype, true, inf_i, s))) return r;       // D = min(D, C (x) B)
+  if ((r = gemm_aligned(C, ld, W, ldw, A, ld, r2, h, h, dtype, false, inf_i, bd, s))) return r;      // C = C (x) A
+  if ((r = gemm_aligned(D, ld, C, ld, B, ld, r2, r2, h, dtype, true, inf_i, bd, s))) return r;       // D = min(D, C (x) B)
   // Second half closed; paths through it update B, C, A.
-  if ((r = rk(D, r2, ld, dtype, inf_i, cutoff, W, s))) return r;
+  if ((r = rk(D, r2, ld, dtype, inf_i, cutoff, bd, W, s))) return r;
   ldw = round_up(r2, 4);
   if ((r = launch_copy2d(W, ldw, B, ld, h, r2, s))) return r;                                     // W = B
-  if ((r = gemm_aligned(B, ld, W, ldw, D, ld, h, r2, r2, dtype, false, inf_i, s))) return r;     // B = B (x) D
+  if ((r = gemm_aligned(B, ld, W, ldw, D, ld, h, r2, r2, dtype, false, inf_i, bd, s))) return r;     // B = B (x) D
   ldw = round_up(h, 4);
   if ((r = launch_copy2d(W, ldw, C, ld, r2, h, s))) return r;                                     // W = C
-  if ((r = gemm_aligned(C, ld, D, ld, W, ldw, r2, h, r2, dtype, false, inf_i, s))) return r;     // C = D (x) C
-  return gemm_aligned(A, ld, B, ld, C, ld, h, h, r2, dtype, true, inf_i, s);                     // A = min(A, B (x) C)
+  if ((r = gemm_aligned(C, ld, D, ld, W, ldw, r2, h, r2, dtype, false, inf_i, bd, s))) return r;     // C = D (x) C
+  return gemm_aligned(A, ld, B, ld, C, ld, h, h, r2, dtype, true, inf_i, bd, s);                     // A = min(A, B (x) C)
 }
 
-int rkleene_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, int cutoff, void *scratch, cudaStream_t s) {
-  return rk(reinterpret_cast<uint8_t *>(d), n, ld, dtype, inf_i, cutoff, reinterpret_cast<uint8_t *>(scratch), s);
+int rkleene_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, int cutoff, Bound b, void *scratch,
+                    cudaStream_t s) {
+  return rk(reinterpret_cast<uint8_t *>(d), n, ld, dtype, inf_i, cutoff, b, reinterpret_cast<uint8_t *>(scratch), s);
 }
 
 }  // namespace apsp

@@ -3,6 +3,7 @@
 #include <math.h>
 #include <mutex>
 #include <string.h>
+#include <vector>
 
 #include "common.cuh"
 
@@ -81,7 +82,64 @@ int resolve_inf_f32(const void *inf, float *out) {
   return 0;
 }
 
+// ------------------------------------ tracing ------------------------------------------
+struct TraceRec {
+  cudaEvent_t e0, e1;
+  int mode;
+  double pairs;
+};
+static std::mutex g_trace_mu;
+static std::vector<TraceRec> g_trace;
+static bool g_trace_on = false;
+
+bool trace_on() { return g_trace_on; }
+
+void trace_begin(cudaStream_t s, void **ev0) {
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) == cudaSuccess) cudaEventRecord(e, s);
+  *ev0 = e;
+}
+
+void trace_end(cudaStream_t s, void *ev0, int mode, double pairs) {
+  cudaEvent_t e1 = nullptr;
+  if (!ev0 || cudaEventCreate(&e1) != cudaSuccess) return;
+  cudaEventRecord(e1, s);
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  g_trace.push_back({reinterpret_cast<cudaEvent_t>(ev0), e1, mode, pairs});
+}
+
 }  // namespace apsp
+
+extern "C" int apsp_trace_enable(int on) {
+  apsp::g_trace_on = on != 0;
+  return APSP_OK;
+}
+
+extern "C" int apsp_trace_read(int mode, double *total_ms, int64_t *launches, double *pairs) {
+  using namespace apsp;
+  if (!total_ms || !launches || !pairs) return APSP_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  double ms = 0, pr = 0;
+  int64_t cnt = 0;
+  int rc = APSP_OK;
+  for (auto &t : g_trace) {
+    if (cudaEventSynchronize(t.e1) != cudaSuccess) rc = APSP_ERR_CUDA;
+    float e = 0.f;
+    if (t.mode == mode || mode < 0) {
+      if (cudaEventElapsedTime(&e, t.e0, t.e1) != cudaSuccess) rc = APSP_ERR_CUDA;
+      ms += e;
+      pr += t.pairs;
+      ++cnt;
+    }
+    cudaEventDestroy(t.e0);
+    cudaEventDestroy(t.e1);
+  }
+  g_trace.clear();
+  *total_ms = ms;
+  *launches = cnt;
+  *pairs = pr;
+  return rc;
+}
 
 extern "C" int apsp_version(void) { return APSP_VERSION; }
 

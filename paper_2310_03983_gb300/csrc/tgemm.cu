@@ -88,94 +88,209 @@ __device__ __forceinline__ TileCoords tile_coords(const TileProblem &p, int64_t 
   return tc;
 }
 
-// Two (min,+) pairs into one accumulator: c = min(c, a0 + b0, a1 + b1).
-template <typename T> struct Pair2;
-template <> struct Pair2<int> {
-  static __device__ __forceinline__ int f(int c, int a0, int b0, int a1, int b1) {
-#if APSP_I32_SEQ == 0
-    return __viaddmin_s32(a1, b1, __viaddmin_s32(a0, b0, c));
-#else
-    return __vimin3_s32(c, a0 + b0, a1 + b1);
-#endif
-  }
-};
-template <> struct Pair2<float> {
-  static __device__ __forceinline__ float f(float c, float a0, float b0, float a1, float b1) {
-    return Ops<float>::min3(c, __fadd_rn(a0, b0), __fadd_rn(a1, b1));
-  }
-};
-
-template <typename T> struct Bits;
-template <> struct Bits<int> {
-  static __device__ __forceinline__ int from(int v) { return v; }
-  static __device__ __forceinline__ int to(int v) { return v; }
-};
-template <> struct Bits<float> {
-  static __device__ __forceinline__ float from(int v) { return __int_as_float(v); }
-  static __device__ __forceinline__ int to(float v) { return __float_as_int(v); }
-};
-
-// One full 32-deep k-slab: acc[i][j] = min over k of A[r_i][k] + B[k][c_j].
-template <typename T>
-__device__ __forceinline__ void slab_full(const T *As, const T *Bs, int tm, int tn, T (&acc)[8][8]) {
+// ---------------------------------------------------------------------------------------
+// Consumer arithmetic.  Both variants compute acc[i][j] = min(acc[i][j], A[r_i][k] + B[k][c_j])
+// over a 32-deep k-slab held in shared memory; they differ only in the instruction sequence.
+//
+// ArithF32: fp32 arithmetic.  Two consecutive k are handled at once: one packed pair add
+//   (add.rn.f32x2) forms {A[i][k] + B[k][j], A[i][k+1] + B[k+1][j]} and one 3-input min folds
+//   both into the accumulator -- one issued instruction per (min,+) pair, the best rate the
+//   probes measure on this chip.  It also serves int32 matrices whose every shortest distance
+//   is below 2^24: an int32 bit pattern v < 2^24 read as fp32 is the number v * 2^-149, sums
+//   below 2^24 * 2^-149 are exact, and rounding is monotone, so a rounded (>= 2^24) candidate
+//   can never undercut an exact one -- the min is bit-exact and so is its bit pattern.
+// ArithI32: the int32 fallback for larger weights: two fused add-min DPX operations
+//   (__viaddmin_s32) per accumulator and k-pair.
+// ---------------------------------------------------------------------------------------
+struct ArithF32 {
+  typedef float T;
+  static __device__ __forceinline__ T from(int v) { return __int_as_float(v); }
+  static __device__ __forceinline__ int to(T v) { return __float_as_int(v); }
+  static __device__ __forceinline__ T mn(T a, T b) { return fminf(a, b); }
+  static __device__ __forceinline__ void slab_full(const int *As, const int *Bs, int tm, int tn, T (&acc)[8][8]) {
 #pragma unroll
-  for (int q = 0; q < kBK / 4; ++q) {
-    T a[8][4];
+    for (int q = 0; q < kBK / 4; ++q) {
+      float2 a[8][2];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int4 v = lds128(As + (tm + 16 * i) * kBK + 4 * q);
-      a[i][0] = Bits<T>::from(v.x); a[i][1] = Bits<T>::from(v.y);
-      a[i][2] = Bits<T>::from(v.z); a[i][3] = Bits<T>::from(v.w);
+      for (int i = 0; i < 8; ++i) {
+        const int4 v = lds128(As + (tm + 16 * i) * kBK + 4 * q);
+        a[i][0] = make_float2(__int_as_float(v.x), __int_as_float(v.y));
+        a[i][1] = make_float2(__int_as_float(v.z), __int_as_float(v.w));
+      }
+#pragma unroll
+      for (int kp = 0; kp < 2; ++kp) {
+        const int *r0 = Bs + (4 * q + 2 * kp) * kBN + 4 * tn;
+        const int4 u0 = lds128(r0), u1 = lds128(r0 + 64), w0 = lds128(r0 + kBN), w1 = lds128(r0 + kBN + 64);
+        float2 b[8];
+        b[0] = make_float2(__int_as_float(u0.x), __int_as_float(w0.x));
+        b[1] = make_float2(__int_as_float(u0.y), __int_as_float(w0.y));
+        b[2] = make_float2(__int_as_float(u0.z), __int_as_float(w0.z));
+        b[3] = make_float2(__int_as_float(u0.w), __int_as_float(w0.w));
+        b[4] = make_float2(__int_as_float(u1.x), __int_as_float(w1.x));
+        b[5] = make_float2(__int_as_float(u1.y), __int_as_float(w1.y));
+        b[6] = make_float2(__int_as_float(u1.z), __int_as_float(w1.z));
+        b[7] = make_float2(__int_as_float(u1.w), __int_as_float(w1.w));
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float2 t = fadd2(a[i][kp], b[j]);
+            acc[i][j] = Ops<float>::min3(acc[i][j], t.x, t.y);
+          }
+      }
     }
+  }
+  static __device__ __forceinline__ void slab_part(const int *As, const int *Bs, int tm, int tn, int kc,
+                                                   T (&acc)[8][8]) {
+    for (int k = 0; k < kc; ++k) {
+      T a[8], b[8];
 #pragma unroll
-    for (int kk = 0; kk < 4; kk += 2) {
-      T b0[8], b1[8];
-      const T *r0 = Bs + (4 * q + kk) * kBN + 4 * tn;
-      const T *r1 = r0 + kBN;
-      int4 v;
-      v = lds128(r0);      b0[0] = Bits<T>::from(v.x); b0[1] = Bits<T>::from(v.y); b0[2] = Bits<T>::from(v.z); b0[3] = Bits<T>::from(v.w);
-      v = lds128(r0 + 64); b0[4] = Bits<T>::from(v.x); b0[5] = Bits<T>::from(v.y); b0[6] = Bits<T>::from(v.z); b0[7] = Bits<T>::from(v.w);
-      v = lds128(r1);      b1[0] = Bits<T>::from(v.x); b1[1] = Bits<T>::from(v.y); b1[2] = Bits<T>::from(v.z); b1[3] = Bits<T>::from(v.w);
-      v = lds128(r1 + 64); b1[4] = Bits<T>::from(v.x); b1[5] = Bits<T>::from(v.y); b1[6] = Bits<T>::from(v.z); b1[7] = Bits<T>::from(v.w);
+      for (int i = 0; i < 8; ++i) a[i] = __int_as_float(As[(tm + 16 * i) * kBK + k]);
+      const int *r = Bs + k * kBN + 4 * tn;
+      const int4 u0 = lds128(r), u1 = lds128(r + 64);
+      b[0] = from(u0.x); b[1] = from(u0.y); b[2] = from(u0.z); b[3] = from(u0.w);
+      b[4] = from(u1.x); b[5] = from(u1.y); b[6] = from(u1.z); b[7] = from(u1.w);
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = Pair2<T>::f(acc[i][j], a[i][kk], b0[j], a[i][kk + 1], b1[j]);
+        for (int j = 0; j < 8; ++j) acc[i][j] = fminf(acc[i][j], __fadd_rn(a[i], b[j]));
+    }
+  }
+};
+
+struct ArithI32 {
+  typedef int T;
+  static __device__ __forceinline__ T from(int v) { return v; }
+  static __device__ __forceinline__ int to(T v) { return v; }
+  static __device__ __forceinline__ T mn(T a, T b) { return min(a, b); }
+  static __device__ __forceinline__ void slab_full(const int *As, const int *Bs, int tm, int tn, T (&acc)[8][8]) {
+#pragma unroll
+    for (int q = 0; q < kBK / 4; ++q) {
+      int4 a[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) a[i] = lds128(As + (tm + 16 * i) * kBK + 4 * q);
+#pragma unroll
+      for (int kp = 0; kp < 2; ++kp) {
+        const int *r0 = Bs + (4 * q + 2 * kp) * kBN + 4 * tn;
+        const int4 u0 = lds128(r0), u1 = lds128(r0 + 64), w0 = lds128(r0 + kBN), w1 = lds128(r0 + kBN + 64);
+        const int b0[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+        const int b1[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int a0 = kp ? a[i].z : a[i].x, a1 = kp ? a[i].w : a[i].y;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = __viaddmin_s32(a1, b1[j], __viaddmin_s32(a0, b0[j], acc[i][j]));
+        }
+      }
+    }
+  }
+  static __device__ __forceinline__ void slab_part(const int *As, const int *Bs, int tm, int tn, int kc,
+                                                   T (&acc)[8][8]) {
+    for (int k = 0; k < kc; ++k) {
+      int a[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) a[i] = As[(tm + 16 * i) * kBK + k];
+      const int *r = Bs + k * kBN + 4 * tn;
+      const int4 u0 = lds128(r), u1 = lds128(r + 64);
+      const int b[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = __viaddmin_s32(a[i], b[j], acc[i][j]);
+    }
+  }
+};
+
+// True when int32 operands may take the exact fp32 path: every finite sum stays below 2^24.
+__device__ __forceinline__ bool small_int_bound(const TileProblem &p) {
+  if (!p.wmax) return false;
+  const int64_t w0 = p.wmax[0], w1 = p.wmax[1];
+  return w0 >= 0 && w1 >= 0 && w0 * p.wmult + w1 < (int64_t(1) << 24);
+}
+
+struct Smem {
+  const int *sA, *sB, *sC;
+  uint64_t *full, *empty, *cfull, *cempty;
+};
+
+// Consumer warps: walk the same tile sequence as the producer, fold every k-slab into the
+// 8 x 8 register tile, then (optionally) min with the prefetched C tile and store.
+template <typename AR, int MODE, bool ACC>
+__device__ __forceinline__ void consume(const TileProblem &p, const Smem &sm, int warp, int lane, int init_bits) {
+  typedef typename AR::T T;
+  const int tm = (warp & 3) * 4 + (lane >> 3);
+  const int tn = (warp >> 2) * 8 + (lane & 7);
+  int *C = reinterpret_cast<int *>(p.C);
+  int stage = 0;
+  uint32_t phase = 0, cphase = 0;
+  const T init = AR::from(init_bits);
+  for (int64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
+    const TileCoords tc = tile_coords<MODE>(p, t);
+    const int nk = (tc.k_len + kBK - 1) / kBK;
+    T acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = init;
+    for (int kt = 0; kt < nk; ++kt) {
+      if (!mbar_wait(&sm.full[stage], phase, p.status)) return;
+      const int *As = sm.sA + stage * (kBM * kBK);
+      const int *Bs = sm.sB + stage * (kBK * kBN);
+      const int kc = tc.k_len - kt * kBK;
+      if (kc >= kBK) AR::slab_full(As, Bs, tm, tn, acc);
+      else AR::slab_part(As, Bs, tm, tn, kc, acc);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sm.empty[stage]);
+      if (++stage == kStages) { stage = 0; phase ^= 1; }
+    }
+    if (ACC) {
+      if (!mbar_wait(sm.cfull, cphase, p.status)) return;
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int4 v = lds128(sm.sC + (tm + 16 * i) * kBN + 4 * tn + 64 * h);
+          acc[i][4 * h + 0] = AR::mn(acc[i][4 * h + 0], AR::from(v.x));
+          acc[i][4 * h + 1] = AR::mn(acc[i][4 * h + 1], AR::from(v.y));
+          acc[i][4 * h + 2] = AR::mn(acc[i][4 * h + 2], AR::from(v.z));
+          acc[i][4 * h + 3] = AR::mn(acc[i][4 * h + 3], AR::from(v.w));
+        }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(sm.cempty);
+      cphase ^= 1;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int rl = tm + 16 * i;
+      if (rl >= tc.m_valid) continue;
+      int *crow = C + (int64_t)(tc.c_row + rl) * p.ldc + tc.c_col;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int cl = 4 * tn + 64 * h;
+        if (cl + 3 < tc.n_valid) {
+          *reinterpret_cast<int4 *>(crow + cl) = make_int4(AR::to(acc[i][4 * h]), AR::to(acc[i][4 * h + 1]),
+                                                           AR::to(acc[i][4 * h + 2]), AR::to(acc[i][4 * h + 3]));
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (cl + q < tc.n_valid) crow[cl + q] = AR::to(acc[i][4 * h + q]);
+        }
+      }
     }
   }
 }
 
-// The ragged last slab of a tile (kc < 32 valid k), one k at a time.
-template <typename T>
-__device__ __forceinline__ void slab_part(const T *As, const T *Bs, int tm, int tn, int kc, T (&acc)[8][8]) {
-  for (int k = 0; k < kc; ++k) {
-    T a[8], b[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) a[i] = As[(tm + 16 * i) * kBK + k];
-    const T *r = Bs + k * kBN + 4 * tn;
-    int4 v;
-    v = lds128(r);      b[0] = Bits<T>::from(v.x); b[1] = Bits<T>::from(v.y); b[2] = Bits<T>::from(v.z); b[3] = Bits<T>::from(v.w);
-    v = lds128(r + 64); b[4] = Bits<T>::from(v.x); b[5] = Bits<T>::from(v.y); b[6] = Bits<T>::from(v.z); b[7] = Bits<T>::from(v.w);
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-      for (int j = 0; j < 8; ++j) acc[i][j] = Ops<T>::mn(acc[i][j], Ops<T>::add(a[i], b[j]));
-  }
-}
-
-template <typename T> __device__ __forceinline__ T acc_init(const TileProblem &p);
-template <> __device__ __forceinline__ int acc_init<int>(const TileProblem &p) { return p.inf_i; }
-template <> __device__ __forceinline__ float acc_init<float>(const TileProblem &p) { return __int_as_float(0x7f800000); }
-
-template <typename T, int MODE, bool ACC>
+// S: storage type (int or float).  Float matrices always take ArithF32; int matrices take
+// ArithF32 when small_int_bound holds for this launch, else ArithI32 (uniform per launch).
+template <typename S, int MODE, bool ACC>
 __global__ void __launch_bounds__(kThreads, 1)
     tgemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
                  const __grid_constant__ CUtensorMap mC, const TileProblem p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  T *sA = reinterpret_cast<T *>(smem);
-  T *sB = reinterpret_cast<T *>(smem + kStages * kAStageBytes);
-  T *sC = reinterpret_cast<T *>(smem + kStages * (kAStageBytes + kBStageBytes));
+  int *sA = reinterpret_cast<int *>(smem);
+  int *sB = reinterpret_cast<int *>(smem + kStages * kAStageBytes);
+  int *sC = reinterpret_cast<int *>(smem + kStages * (kAStageBytes + kBStageBytes));
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * (kAStageBytes + kBStageBytes) + kCBytes);
   uint64_t *full = bars, *empty = bars + kStages, *cfull = bars + 2 * kStages, *cempty = cfull + 1;
 
@@ -230,70 +345,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     return;
   }
 
-  // --------------------------------- consumers -------------------------------------
-  const int tm = (warp & 3) * 4 + (lane >> 3);
-  const int tn = (warp >> 2) * 8 + (lane & 7);
-  T *C = reinterpret_cast<T *>(p.C);
-  int stage = 0;
-  uint32_t phase = 0, cphase = 0;
-  for (int64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
-    const TileCoords tc = tile_coords<MODE>(p, t);
-    const int nk = (tc.k_len + kBK - 1) / kBK;
-    T acc[8][8];
-    const T init = acc_init<T>(p);
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-      for (int j = 0; j < 8; ++j) acc[i][j] = init;
-    bool ok = true;
-    for (int kt = 0; kt < nk; ++kt) {
-      if (!mbar_wait(&full[stage], phase, p.status)) { ok = false; break; }
-      const T *As = sA + stage * (kBM * kBK);
-      const T *Bs = sB + stage * (kBK * kBN);
-      const int kc = tc.k_len - kt * kBK;
-      if (kc >= kBK) slab_full<T>(As, Bs, tm, tn, acc);
-      else slab_part<T>(As, Bs, tm, tn, kc, acc);
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[stage]);
-      if (++stage == kStages) { stage = 0; phase ^= 1; }
-    }
-    if (!ok) return;
-    if (ACC) {
-      if (!mbar_wait(cfull, cphase, p.status)) return;
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int4 v = lds128(sC + (tm + 16 * i) * kBN + 4 * tn + 64 * h);
-          acc[i][4 * h + 0] = Ops<T>::mn(acc[i][4 * h + 0], Bits<T>::from(v.x));
-          acc[i][4 * h + 1] = Ops<T>::mn(acc[i][4 * h + 1], Bits<T>::from(v.y));
-          acc[i][4 * h + 2] = Ops<T>::mn(acc[i][4 * h + 2], Bits<T>::from(v.z));
-          acc[i][4 * h + 3] = Ops<T>::mn(acc[i][4 * h + 3], Bits<T>::from(v.w));
-        }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(cempty);
-      cphase ^= 1;
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int rl = tm + 16 * i;
-      if (rl >= tc.m_valid) continue;
-      T *crow = C + (int64_t)(tc.c_row + rl) * p.ldc + tc.c_col;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int cl = 4 * tn + 64 * h;
-        if (cl + 3 < tc.n_valid) {
-          int4 v = make_int4(Bits<T>::to(acc[i][4 * h]), Bits<T>::to(acc[i][4 * h + 1]),
-                             Bits<T>::to(acc[i][4 * h + 2]), Bits<T>::to(acc[i][4 * h + 3]));
-          *reinterpret_cast<int4 *>(crow + cl) = v;
-        } else {
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            if (cl + q < tc.n_valid) crow[cl + q] = acc[i][4 * h + q];
-        }
-      }
-    }
+  const Smem sm = {sA, sB, sC, full, empty, cfull, cempty};
+  if (sizeof(S) == 4 && S(0.5) != S(0)) {  // float storage
+    consume<ArithF32, MODE, ACC>(p, sm, warp, lane, 0x7f800000);
+  } else if (small_int_bound(p)) {
+    consume<ArithF32, MODE, ACC>(p, sm, warp, lane, p.inf_i);
+  } else {
+    consume<ArithI32, MODE, ACC>(p, sm, warp, lane, p.inf_i);
   }
+}
+
+// (min,+) pairs one launch performs by definition (Eq. 2: one add and one min per (i, j, k)).
+template <int MODE> static double algorithmic_pairs(const TileProblem &p) {
+  if (MODE == kModeGemm) return (double)p.M * (double)p.N * (double)p.K;
+  const double bk = (double)(p.n - p.kb * kBM < kBM ? p.n - p.kb * kBM : kBM);
+  const double rest = (double)p.n - bk;
+  return MODE == kModeFwPanels ? 2.0 * bk * bk * rest : rest * rest * bk;
 }
 
 template <typename T, int MODE, bool ACC>
@@ -303,8 +370,12 @@ static int launch_one(const CUtensorMap &mA, const CUtensorMap &mB, const CUtens
   APSP_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes + 1024));
   const int64_t sms = sm_count();
   const int grid = (int)(p.ntiles < sms ? p.ntiles : sms);
+  void *ev = nullptr;
+  const bool tr = trace_on();
+  if (tr) trace_begin(s, &ev);
   k<<<grid, kThreads, kSmemBytes + 1024, s>>>(mA, mB, mC, p);
   APSP_LAUNCH_CHECK();
+  if (tr) trace_end(s, ev, MODE, algorithmic_pairs<MODE>(p));
   return APSP_OK;
 }
 
@@ -426,13 +497,20 @@ int launch_copy2d(void *dst, int64_t ldd, const void *src, int64_t lds, int64_t 
 }  // namespace apsp
 
 // ------------------------------------ C ABI -------------------------------------------
+extern "C" size_t tropical_gemm_workspace_bytes(int64_t M, int64_t N, int64_t K, int dtype) {
+  (void)M; (void)N; (void)K; (void)dtype;
+  return apsp::kFlagBytes;
+}
+
 extern "C" int tropical_gemm(void *C, const void *A, const void *B, int64_t M, int64_t N, int64_t K, int64_t lda,
-                             int64_t ldb, int64_t ldc, int dtype, const void *inf, int accumulate, void *stream) {
+                             int64_t ldb, int64_t ldc, int dtype, const void *inf, int accumulate, void *ws,
+                             size_t ws_bytes, void *stream) {
   using namespace apsp;
   if (!dtype_ok(dtype) || M < 0 || N < 0 || K < 0) return APSP_ERR_ARG;
   if (M == 0 || N == 0) return APSP_OK;
   if (!C || (K > 0 && (!A || !B)) || ldc < N || (K > 0 && (lda < K || ldb < N))) return APSP_ERR_ARG;
   if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX) return APSP_ERR_ARG;
+  if (ws && (ws_bytes < kFlagBytes || reinterpret_cast<uintptr_t>(ws) % 256 != 0)) return APSP_ERR_ARG;
   // C must not overlap A or B (byte ranges of the strided extents).
   auto span = [](const void *p, int64_t rows, int64_t cols, int64_t ld) {
     return std::make_pair((uintptr_t)p, (uintptr_t)p + (uintptr_t)(((rows - 1) * ld + cols) * 4));
@@ -456,6 +534,21 @@ extern "C" int tropical_gemm(void *C, const void *A, const void *B, int64_t M, i
     return r;
   if ((r = make_operand_maps(K > 0 ? B : C, K > 0 ? K : 1, N, K > 0 ? ldb : ldc, dtype, nullptr, &mB, nullptr))) return r;
   if ((r = make_operand_maps(C, M, N, ldc, dtype, nullptr, nullptr, &mC))) return r;
+  void *own = nullptr;
+  int *words = nullptr;
+  if (dtype == APSP_I32) {  // largest finite entries of A and B decide the exact fp32 path
+    if (!ws) {
+      if (cudaMallocAsync(&own, kFlagBytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return APSP_ERR_NOMEM;
+      }
+      ws = own;
+    }
+    words = reinterpret_cast<int *>(ws);
+    if (cudaMemsetAsync(words, 0, 16, s) != cudaSuccess) r = APSP_ERR_CUDA;
+    if (!r && K > 0) r = launch_scan_max(A, M, K, lda, inf_i, words, s);
+    if (!r && K > 0) r = launch_scan_max(B, K, N, ldb, inf_i, words + 1, s);
+  }
   TileProblem p = {};
   p.M = M; p.N = N; p.K = K;
   p.tiles_m = cdiv(M, kBM);
@@ -466,5 +559,9 @@ extern "C" int tropical_gemm(void *C, const void *A, const void *B, int64_t M, i
   p.inf_i = inf_i;
   p.inf_f = inf_f;
   p.status = status_word();
-  return launch_tgemm(kModeGemm, accumulate != 0, dtype, mA, mB, mC, p, s);
+  p.wmax = words;
+  p.wmult = 1;
+  if (!r) r = launch_tgemm(kModeGemm, accumulate != 0, dtype, mA, mB, mC, p, s);
+  if (own) cudaFreeAsync(own, s);
+  return r;
 }

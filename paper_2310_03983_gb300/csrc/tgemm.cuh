@@ -33,6 +33,11 @@ struct TileProblem {
   int inf_i;
   float inf_f;
   unsigned int *status;
+  // Bound words for int32 storage (device, may be null): the exact fp32 path is taken when
+  // wmax[0] * wmult + wmax[1] < 2^24 (closures: max finite weight times n-1; products: the
+  // largest finite entries of A and B).
+  const int *wmax;
+  int64_t wmult;
 };
 
 // Launch one tile pass.  acc: fold into the existing C (min) instead of overwriting it.
@@ -52,7 +57,20 @@ int make_operand_maps(const void *base, int64_t rows, int64_t cols, int64_t ld, 
 // Strided 2-D copy (rows x cols elements of 4 bytes), used for operand copies.
 int launch_copy2d(void *dst, int64_t ldd, const void *src, int64_t lds, int64_t rows, int64_t cols, cudaStream_t s);
 
-// a1 launcher (normalise.cu)
-int launch_normalise(void *d, int64_t n, int64_t ld, int dtype, int inf_i, float inf_f, cudaStream_t s);
+// a1 launcher (normalise.cu).  For int32, atomically maxes the largest finite entry into
+// *wmax (device word, zeroed by the caller) when wmax is not null.
+int launch_normalise(void *d, int64_t n, int64_t ld, int dtype, int inf_i, float inf_f, int *wmax, cudaStream_t s);
+
+// Largest entry < inf of a rows x cols int32 matrix, atomically maxed into *out (normalise.cu).
+int launch_scan_max(const void *x, int64_t rows, int64_t cols, int64_t ld, int inf, int *out, cudaStream_t s);
+
+// Launch tracing (runtime.cu): when enabled, every tropical-GEMM-engine launch is bracketed
+// by two CUDA events on its stream and tagged with its mode and algorithmic pair count.
+bool trace_on();
+void trace_begin(cudaStream_t s, void **ev0);
+void trace_end(cudaStream_t s, void *ev0, int mode, double pairs);
+
+// Bytes of the per-call bound words at the front of every workspace.
+constexpr size_t kFlagBytes = 256;
 
 }  // namespace apsp

@@ -128,6 +128,19 @@ def test_tropical_gemm_strided_and_unaligned(apsp, dtype):
     assert_dist_equal(C.cpu().numpy(), want, "unaligned")
 
 
+@pytest.mark.parametrize("hi", [1000, 2**23 - 1, 2**23, 2**24, 10**8])
+def test_tropical_gemm_int_paths(apsp, hi):
+    """Entries up to `hi`: below 2^23 + 2^23 the exact fp32 path runs, above it the int32
+    path; both must give the oracle's values, including sums right at the 2^24 boundary."""
+    rng = np.random.default_rng(hi % 1000)
+    M, N, K = 200, 160, 140
+    a = np.where(rng.random((M, K)) < 0.8, rng.integers(hi // 2, hi, (M, K), endpoint=True), INF).astype(np.int32)
+    b = np.where(rng.random((K, N)) < 0.8, rng.integers(hi // 2, hi, (K, N), endpoint=True), INF).astype(np.int32)
+    C = torch.empty((M, N), dtype=torch.int32, device="cuda")
+    apsp.tropical_gemm(C, torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda())
+    assert_dist_equal(C.cpu().numpy(), oracle.minplus(a, b), f"hi={hi}")
+
+
 def test_tropical_gemm_identity_and_k0(apsp):
     n = 200
     eye = np.full((n, n), INF, np.int32)
@@ -232,6 +245,27 @@ def test_saturation_near_inf(apsp):
         d = torch.from_numpy(h).cuda()
         fn(d)
         assert_dist_equal(d.cpu().numpy(), want, fn.__name__)
+
+
+@pytest.mark.parametrize("hi", [100, 65000, 66000, 10**6])
+def test_closure_int_paths(apsp, hi):
+    """n = 258 with weights up to `hi`: (n - 1) * hi crosses 2^24 between 65000 and 66000, so
+    both the exact fp32 path and the int32 path are exercised on long shortest paths."""
+    n = 258
+    rng = np.random.default_rng(hi)
+    h = np.full((n, n), INF, np.int32)
+    np.fill_diagonal(h, 0)
+    perm = rng.permutation(n)
+    for a, b in zip(perm[:-1], perm[1:]):  # a Hamiltonian path of heavy edges: long distances
+        h[a, b] = rng.integers(hi - 50, hi, endpoint=True)
+    extra = rng.random((n, n)) < 0.01
+    h[extra] = rng.integers(hi // 2, hi, size=int(extra.sum()), endpoint=True)
+    np.fill_diagonal(h, 0)
+    want = oracle.fw(h)
+    for fn, kw in ((apsp.apsp_fw, {}), (apsp.apsp_rkleene, {"cutoff": 128})):
+        d = torch.from_numpy(h).cuda()
+        fn(d, **kw)
+        assert_dist_equal(d.cpu().numpy(), want, f"{fn.__name__} hi={hi}")
 
 
 def test_empty_matrix(apsp):
