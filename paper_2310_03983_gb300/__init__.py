@@ -178,7 +178,7 @@ def apsp_rkleene(d: torch.Tensor, inf=None, cutoff: int = 0, ws: torch.Tensor | 
 
 def apsp_probe_minplus(variant: int, blocks: int, threads: int, iters: int, sink: torch.Tensor, stream=None):
     _check(_lib.apsp_probe_minplus(variant, blocks, threads, iters, sink.data_ptr(), _stream(stream)),
-           "apsp_probe_minplus", "apsp_trace_enable", "apsp_trace_read")
+           "apsp_probe_minplus")
 
 
 def apsp_trace_enable(on: bool = True):

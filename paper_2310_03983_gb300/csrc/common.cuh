@@ -57,6 +57,10 @@ template <> struct Ops<float> {
   }
 };
 
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
 // Packed pair add (PTX add.rn.f32x2, sm_100+): {a.x + b.x, a.y + b.y} in one instruction.
 // Subnormals are kept (no .ftz), which the exact small-integer path relies on.
 __device__ __forceinline__ float2 fadd2(float2 a, float2 b) {
@@ -71,13 +75,36 @@ __device__ __forceinline__ float2 fadd2(float2 a, float2 b) {
   return d;
 }
 
+// The same packed add on operands already held as 64-bit register pairs, and the helpers
+// that build / split such pairs.  Building each pair once and reusing it keeps the packing
+// moves out of the inner loop.
+__device__ __forceinline__ uint64_t pack2(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ uint64_t fadd2_64(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ float lo_of(uint64_t v) {
+  float f, g;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(f), "=f"(g) : "l"(v));
+  return f;
+}
+__device__ __forceinline__ float hi_of(uint64_t v) {
+  float f, g;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(f), "=f"(g) : "l"(v));
+  return g;
+}
+__device__ __forceinline__ void lds128_2x64(const void *p, uint64_t &a, uint64_t &b) {
+  asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(smem_u32(p)));
+}
+
 // ---------------------------------------------------------------------------------------
 // mbarrier / TMA wrappers (PTX ISA: mbarrier.*, cp.async.bulk.tensor.*)
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }

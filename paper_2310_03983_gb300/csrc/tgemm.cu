@@ -108,34 +108,32 @@ struct ArithF32 {
   static __device__ __forceinline__ int to(T v) { return __float_as_int(v); }
   static __device__ __forceinline__ T mn(T a, T b) { return fminf(a, b); }
   static __device__ __forceinline__ void slab_full(const int *As, const int *Bs, int tm, int tn, T (&acc)[8][8]) {
-#pragma unroll
+#pragma unroll 1
     for (int q = 0; q < kBK / 4; ++q) {
-      float2 a[8][2];
+      // a[i][0] = {A[r_i][4q], A[r_i][4q+1]}, a[i][1] = {A[r_i][4q+2], A[r_i][4q+3]}
+      uint64_t a[8][2];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int4 v = lds128(As + (tm + 16 * i) * kBK + 4 * q);
-        a[i][0] = make_float2(__int_as_float(v.x), __int_as_float(v.y));
-        a[i][1] = make_float2(__int_as_float(v.z), __int_as_float(v.w));
-      }
+      for (int i = 0; i < 8; ++i) lds128_2x64(As + (tm + 16 * i) * kBK + 4 * q, a[i][0], a[i][1]);
 #pragma unroll
       for (int kp = 0; kp < 2; ++kp) {
         const int *r0 = Bs + (4 * q + 2 * kp) * kBN + 4 * tn;
         const int4 u0 = lds128(r0), u1 = lds128(r0 + 64), w0 = lds128(r0 + kBN), w1 = lds128(r0 + kBN + 64);
-        float2 b[8];
-        b[0] = make_float2(__int_as_float(u0.x), __int_as_float(w0.x));
-        b[1] = make_float2(__int_as_float(u0.y), __int_as_float(w0.y));
-        b[2] = make_float2(__int_as_float(u0.z), __int_as_float(w0.z));
-        b[3] = make_float2(__int_as_float(u0.w), __int_as_float(w0.w));
-        b[4] = make_float2(__int_as_float(u1.x), __int_as_float(w1.x));
-        b[5] = make_float2(__int_as_float(u1.y), __int_as_float(w1.y));
-        b[6] = make_float2(__int_as_float(u1.z), __int_as_float(w1.z));
-        b[7] = make_float2(__int_as_float(u1.w), __int_as_float(w1.w));
+        // b[j] = {B[k][c_j], B[k+1][c_j]}: built once, reused by all eight rows
+        uint64_t b[8];
+        b[0] = pack2(__int_as_float(u0.x), __int_as_float(w0.x));
+        b[1] = pack2(__int_as_float(u0.y), __int_as_float(w0.y));
+        b[2] = pack2(__int_as_float(u0.z), __int_as_float(w0.z));
+        b[3] = pack2(__int_as_float(u0.w), __int_as_float(w0.w));
+        b[4] = pack2(__int_as_float(u1.x), __int_as_float(w1.x));
+        b[5] = pack2(__int_as_float(u1.y), __int_as_float(w1.y));
+        b[6] = pack2(__int_as_float(u1.z), __int_as_float(w1.z));
+        b[7] = pack2(__int_as_float(u1.w), __int_as_float(w1.w));
 #pragma unroll
         for (int i = 0; i < 8; ++i)
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
-            const float2 t = fadd2(a[i][kp], b[j]);
-            acc[i][j] = Ops<float>::min3(acc[i][j], t.x, t.y);
+            const uint64_t t = fadd2_64(a[i][kp], b[j]);
+            acc[i][j] = Ops<float>::min3(acc[i][j], lo_of(t), hi_of(t));
           }
       }
     }
@@ -164,7 +162,7 @@ struct ArithI32 {
   static __device__ __forceinline__ int to(T v) { return v; }
   static __device__ __forceinline__ T mn(T a, T b) { return min(a, b); }
   static __device__ __forceinline__ void slab_full(const int *As, const int *Bs, int tm, int tn, T (&acc)[8][8]) {
-#pragma unroll
+#pragma unroll 1
     for (int q = 0; q < kBK / 4; ++q) {
       int4 a[8];
 #pragma unroll
