@@ -195,9 +195,11 @@ int sm_count();
 unsigned int *status_word();
 
 // Encode a 2-D row-major tensor map: `rows` x `cols` elements (4 bytes each), leading
-// dimension ld elements, box `box_rows` x `box_cols`, no swizzle, zero OOB fill.
+// dimension ld elements, box `box_rows` x `box_cols`, zero OOB fill.  swizzle128: the box's
+// rows are 128 bytes and land in shared memory with their 16-byte chunks XOR-permuted by
+// (row mod 8) (requires a 1024-byte aligned destination).
 int make_tmap_2d(CUtensorMap *out, const void *base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
-                 int box_cols, int dtype);
+                 int box_cols, int dtype, bool swizzle128 = false);
 
 // Resolve the int32 sentinel (NULL -> APSP_INF_I32) or float sentinel (NULL -> +inf).
 int resolve_inf_i32(const void *inf, int *out);

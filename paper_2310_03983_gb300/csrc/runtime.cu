@@ -53,7 +53,7 @@ static EncodeTiledFn get_encode() {
 }
 
 int make_tmap_2d(CUtensorMap *out, const void *base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
-                 int box_cols, int dtype) {
+                 int box_cols, int dtype, bool swizzle128) {
   EncodeTiledFn enc = get_encode();
   if (!enc) return APSP_ERR_CUDA;
   if (reinterpret_cast<uintptr_t>(base) % 16 != 0 || (ld * 4) % 16 != 0) return APSP_ERR_ARG;
@@ -64,7 +64,8 @@ int make_tmap_2d(CUtensorMap *out, const void *base, int64_t rows, int64_t cols,
   cuuint32_t estr[2] = {1, 1};
   CUtensorMapDataType t = dtype == APSP_I32 ? CU_TENSOR_MAP_DATA_TYPE_INT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   CUresult r = enc(out, t, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                   swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? APSP_OK : APSP_ERR_CUDA;
 }
 

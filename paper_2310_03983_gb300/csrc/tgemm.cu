@@ -26,9 +26,17 @@
 
 namespace apsp {
 
-#ifndef APSP_I32_SEQ
-#define APSP_I32_SEQ 0  // 0: two fused add-mins; 1: two adds then one 3-input min
+// fp32 instruction sequence of the slab loop (all exact-equivalent; chosen by measurement):
+//   0: packed pair add over k-pairs + 3-input min;  1: two scalar adds + 3-input min;
+//   2: packed pair add over column pairs (duplicated A operand) + 3-input min.
+#ifndef APSP_F32_SEQ
+#define APSP_F32_SEQ 2
 #endif
+
+// Offset (in elements) of the 16-byte chunk kq (k = 4 kq .. 4 kq + 3) of row r of an A slab.
+// The slab is TMA-loaded with 128-byte swizzle: chunk kq of row r sits at chunk kq ^ (r & 7),
+// so the four rows a warp reads at once fall in four different bank groups.
+__device__ __forceinline__ int a_off(int r, int kq) { return r * kBK + ((kq ^ (r & 7)) << 2); }
 
 struct TileCoords {
   int a_row, a_col, b_row, b_col, c_row, c_col;
@@ -110,10 +118,11 @@ struct ArithF32 {
   static __device__ __forceinline__ void slab_full(const int *As, const int *Bs, int tm, int tn, T (&acc)[8][8]) {
 #pragma unroll 1
     for (int q = 0; q < kBK / 4; ++q) {
+#if APSP_F32_SEQ == 0
       // a[i][0] = {A[r_i][4q], A[r_i][4q+1]}, a[i][1] = {A[r_i][4q+2], A[r_i][4q+3]}
       uint64_t a[8][2];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) lds128_2x64(As + (tm + 16 * i) * kBK + 4 * q, a[i][0], a[i][1]);
+      for (int i = 0; i < 8; ++i) lds128_2x64(As + a_off(tm + 16 * i, q), a[i][0], a[i][1]);
 #pragma unroll
       for (int kp = 0; kp < 2; ++kp) {
         const int *r0 = Bs + (4 * q + 2 * kp) * kBN + 4 * tn;
@@ -136,6 +145,59 @@ struct ArithF32 {
             acc[i][j] = Ops<float>::min3(acc[i][j], lo_of(t), hi_of(t));
           }
       }
+#elif APSP_F32_SEQ == 1
+      // two scalar adds feeding one 3-input min
+      float4 a[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int4 v = lds128(As + a_off(tm + 16 * i, q));
+        a[i] = make_float4(__int_as_float(v.x), __int_as_float(v.y), __int_as_float(v.z), __int_as_float(v.w));
+      }
+#pragma unroll
+      for (int kp = 0; kp < 2; ++kp) {
+        const int *r0 = Bs + (4 * q + 2 * kp) * kBN + 4 * tn;
+        const int4 u0 = lds128(r0), u1 = lds128(r0 + 64), w0 = lds128(r0 + kBN), w1 = lds128(r0 + kBN + 64);
+        const float b0[8] = {__int_as_float(u0.x), __int_as_float(u0.y), __int_as_float(u0.z), __int_as_float(u0.w),
+                             __int_as_float(u1.x), __int_as_float(u1.y), __int_as_float(u1.z), __int_as_float(u1.w)};
+        const float b1[8] = {__int_as_float(w0.x), __int_as_float(w0.y), __int_as_float(w0.z), __int_as_float(w0.w),
+                             __int_as_float(w1.x), __int_as_float(w1.y), __int_as_float(w1.z), __int_as_float(w1.w)};
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float a0 = kp ? a[i].z : a[i].x, a1 = kp ? a[i].w : a[i].y;
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            acc[i][j] = Ops<float>::min3(acc[i][j], __fadd_rn(a0, b0[j]), __fadd_rn(a1, b1[j]));
+        }
+      }
+#else
+      // packed adds along j: {A[i][k], A[i][k]} + {B[k][c_j], B[k][c_j+1]}
+      float4 a[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int4 v = lds128(As + a_off(tm + 16 * i, q));
+        a[i] = make_float4(__int_as_float(v.x), __int_as_float(v.y), __int_as_float(v.z), __int_as_float(v.w));
+      }
+#pragma unroll
+      for (int kp = 0; kp < 2; ++kp) {
+        const int *r0 = Bs + (4 * q + 2 * kp) * kBN + 4 * tn;
+        uint64_t b0[4], b1[4];
+        lds128_2x64(r0, b0[0], b0[1]);
+        lds128_2x64(r0 + 64, b0[2], b0[3]);
+        lds128_2x64(r0 + kBN, b1[0], b1[1]);
+        lds128_2x64(r0 + kBN + 64, b1[2], b1[3]);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float a0 = kp ? a[i].z : a[i].x, a1 = kp ? a[i].w : a[i].y;
+          const uint64_t aa0 = pack2(a0, a0), aa1 = pack2(a1, a1);
+#pragma unroll
+          for (int jp = 0; jp < 4; ++jp) {
+            const uint64_t t0 = fadd2_64(aa0, b0[jp]), t1 = fadd2_64(aa1, b1[jp]);
+            acc[i][2 * jp] = Ops<float>::min3(acc[i][2 * jp], lo_of(t0), lo_of(t1));
+            acc[i][2 * jp + 1] = Ops<float>::min3(acc[i][2 * jp + 1], hi_of(t0), hi_of(t1));
+          }
+        }
+      }
+#endif
     }
   }
   static __device__ __forceinline__ void slab_part(const int *As, const int *Bs, int tm, int tn, int kc,
@@ -143,7 +205,7 @@ struct ArithF32 {
     for (int k = 0; k < kc; ++k) {
       T a[8], b[8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) a[i] = __int_as_float(As[(tm + 16 * i) * kBK + k]);
+      for (int i = 0; i < 8; ++i) a[i] = __int_as_float(As[a_off(tm + 16 * i, k >> 2) + (k & 3)]);
       const int *r = Bs + k * kBN + 4 * tn;
       const int4 u0 = lds128(r), u1 = lds128(r + 64);
       b[0] = from(u0.x); b[1] = from(u0.y); b[2] = from(u0.z); b[3] = from(u0.w);
@@ -166,7 +228,7 @@ struct ArithI32 {
     for (int q = 0; q < kBK / 4; ++q) {
       int4 a[8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) a[i] = lds128(As + (tm + 16 * i) * kBK + 4 * q);
+      for (int i = 0; i < 8; ++i) a[i] = lds128(As + a_off(tm + 16 * i, q));
 #pragma unroll
       for (int kp = 0; kp < 2; ++kp) {
         const int *r0 = Bs + (4 * q + 2 * kp) * kBN + 4 * tn;
@@ -187,7 +249,7 @@ struct ArithI32 {
     for (int k = 0; k < kc; ++k) {
       int a[8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) a[i] = As[(tm + 16 * i) * kBK + k];
+      for (int i = 0; i < 8; ++i) a[i] = As[a_off(tm + 16 * i, k >> 2) + (k & 3)];
       const int *r = Bs + k * kBN + 4 * tn;
       const int4 u0 = lds128(r), u1 = lds128(r + 64);
       const int b[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
@@ -304,9 +366,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   __syncthreads();
 
-  if (warp == kConsumerWarps) {
+  if (warp >= kConsumerWarps) {
     // ------------------------------- producer --------------------------------------
-    if (lane == 0) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kProducerRegs));
+    if (warp == kConsumerWarps && lane == 0) {
       tma_prefetch_desc(&mA);
       tma_prefetch_desc(&mB);
       if (ACC) tma_prefetch_desc(&mC);
@@ -343,6 +406,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     return;
   }
 
+  asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kConsumerRegs));
   const Smem sm = {sA, sB, sC, full, empty, cfull, cempty};
   if (sizeof(S) == 4 && S(0.5) != S(0)) {  // float storage
     consume<ArithF32, MODE, ACC>(p, sm, warp, lane, 0x7f800000);
@@ -365,6 +429,14 @@ template <typename T, int MODE, bool ACC>
 static int launch_one(const CUtensorMap &mA, const CUtensorMap &mB, const CUtensorMap &mC, const TileProblem &p,
                       cudaStream_t s) {
   auto k = tgemm_kernel<T, MODE, ACC>;
+  static int checked = 0;  // 1: register split verified for this instantiation
+  if (!checked) {
+    cudaFuncAttributes fa;
+    APSP_CUDA_TRY(cudaFuncGetAttributes(&fa, k));
+    // setmaxnreg.inc would wait forever if the split asked for more than the launch holds.
+    if (fa.numRegs < kLaunchRegs || fa.maxThreadsPerBlock < kThreads) return APSP_ERR_UNSUPPORTED;
+    checked = 1;
+  }
   APSP_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes + 1024));
   const int64_t sms = sm_count();
   const int grid = (int)(p.ntiles < sms ? p.ntiles : sms);
@@ -398,7 +470,7 @@ int launch_tgemm(int mode, bool acc, int dtype, const CUtensorMap &mA, const CUt
 int make_operand_maps(const void *base, int64_t rows, int64_t cols, int64_t ld, int dtype, CUtensorMap *mA,
                       CUtensorMap *mB, CUtensorMap *mC) {
   int r;
-  if (mA && (r = make_tmap_2d(mA, base, rows, cols, ld, kBM, kBK, dtype))) return r;
+  if (mA && (r = make_tmap_2d(mA, base, rows, cols, ld, kBM, kBK, dtype, true))) return r;
   if (mB && (r = make_tmap_2d(mB, base, rows, cols, ld, kBK, kBN, dtype))) return r;
   if (mC && (r = make_tmap_2d(mC, base, rows, cols, ld, kBM, kBN, dtype))) return r;
   return APSP_OK;

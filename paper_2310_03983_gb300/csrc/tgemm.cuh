@@ -9,7 +9,12 @@ namespace apsp {
 // CTA tile and pipeline shape.
 constexpr int kBM = 128, kBN = 128, kBK = 32, kStages = 4;
 constexpr int kConsumerWarps = 8;
-constexpr int kThreads = (kConsumerWarps + 1) * 32;  // 8 consumer warps + 1 TMA producer warp
+constexpr int kThreads = (kConsumerWarps + 4) * 32;  // 2 consumer warpgroups + 1 producer warpgroup
+// Register split (setmaxnreg): the launch gives every thread kLaunchRegs; the producer
+// warpgroup gives back down to kProducerRegs so the consumers can grow to kConsumerRegs.
+// 128 * kProducerRegs + 256 * kConsumerRegs must not exceed 384 * kLaunchRegs.
+constexpr int kLaunchRegs = 168, kProducerRegs = 40, kConsumerRegs = 232;
+static_assert(128 * kProducerRegs + 256 * kConsumerRegs <= kThreads * kLaunchRegs, "register split");
 constexpr int kAStageBytes = kBM * kBK * 4;         // A tile [128 m][32 k]
 constexpr int kBStageBytes = kBK * kBN * 4;         // B tile [32 k][128 n]
 constexpr int kCBytes = kBM * kBN * 4;              // C tile [128 m][128 n]
