@@ -32,6 +32,11 @@ namespace apsp {
 #ifndef APSP_F32_SEQ
 #define APSP_F32_SEQ 2
 #endif
+// Unroll factor of the loop over the eight 4-deep k-quads of a slab.
+#ifndef APSP_Q_UNROLL
+#define APSP_Q_UNROLL 2
+#endif
+constexpr int kQUnroll = APSP_Q_UNROLL;
 
 // Offset (in elements) of the 16-byte chunk kq (k = 4 kq .. 4 kq + 3) of row r of an A slab.
 // The slab is TMA-loaded with 128-byte swizzle: chunk kq of row r sits at chunk kq ^ (r & 7),
@@ -116,7 +121,7 @@ struct ArithF32 {
   static __device__ __forceinline__ int to(T v) { return __float_as_int(v); }
   static __device__ __forceinline__ T mn(T a, T b) { return fminf(a, b); }
   static __device__ __forceinline__ void slab_full(const int *As, const int *Bs, int tm, int tn, T (&acc)[8][8]) {
-#pragma unroll 1
+#pragma unroll kQUnroll
     for (int q = 0; q < kBK / 4; ++q) {
 #if APSP_F32_SEQ == 0
       // a[i][0] = {A[r_i][4q], A[r_i][4q+1]}, a[i][1] = {A[r_i][4q+2], A[r_i][4q+3]}
