@@ -130,6 +130,22 @@ size_t apsp_rkleene_workspace_bytes(int64_t n, int64_t ld, int dtype, int cutoff
 int apsp_rkleene(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int cutoff,
                  void *ws, size_t ws_bytes, void *stream);
 
+/* ---- a7: batched closure of many independent graphs in one persistent launch ----------
+ * Closes `count` graphs in place.  Graph g is an ns[g] x ns[g] matrix stored row-major at
+ * element offset offsets[g] of `pool` with leading dimension lds[g]; it is closed exactly as
+ * apsp_fw would close it (a1 normalisation, then blocked Floyd-Warshall), so results are
+ * identical to closing each graph alone.  `order` (device, optional) lists the graph indices
+ * in processing order -- largest first balances the persistent CTAs best; NULL = 0..count-1.
+ * offsets, ns, lds and order are DEVICE arrays of `count` entries.  pool must be 16-byte
+ * aligned; every lds[g] and offsets[g] must be a multiple of 4 and lds[g] >= ns[g]: a graph
+ * that breaks this, or an order entry outside [0, count), is skipped and sets APSP_ERR_ARG
+ * in the device status word (the rest of the batch is still closed).  ns[g] <= 0 is skipped.
+ * The workspace holds the work-queue counter (apsp_batched_workspace_bytes). */
+size_t apsp_batched_workspace_bytes(int64_t count);
+int apsp_batched(void *pool, const int64_t *offsets, const int32_t *ns, const int32_t *lds,
+                 const int32_t *order, int64_t count, int dtype, const void *inf, void *ws,
+                 size_t ws_bytes, void *stream);
+
 /* ---- measurement: launch tracing ------------------------------------------------------
  * apsp_trace_enable(1) makes every launch of the tropical GEMM engine (the standalone
  * product and blocked-FW phases 2 and 3) record a CUDA event before and after itself on its

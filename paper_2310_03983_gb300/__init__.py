@@ -51,6 +51,8 @@ def _load():
         "apsp_rkleene_workspace_bytes": ([i64, i64, i32, i32], sz),
         "apsp_rkleene": ([vp, i64, i64, i32, vp, i32, vp, sz, vp], i32),
         "apsp_probe_minplus": ([i32, i32, i32, i32, vp, vp], i32),
+        "apsp_batched_workspace_bytes": ([i64], sz),
+        "apsp_batched": ([vp, vp, vp, vp, vp, i64, i32, vp, vp, sz, vp], i32),
         "apsp_trace_enable": ([i32], i32),
         "apsp_trace_read": ([i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                              ctypes.POINTER(ctypes.c_double)], i32),
@@ -65,7 +67,8 @@ _lib = _load()
 EXPORTS = ("apsp_version", "apsp_status_str", "apsp_device_status", "apsp_normalise",
            "tropical_gemm_workspace_bytes", "tropical_gemm",
            "apsp_fw_workspace_bytes", "apsp_fw", "apsp_rkleene_workspace_bytes", "apsp_rkleene",
-           "apsp_probe_minplus", "apsp_trace_enable", "apsp_trace_read")
+           "apsp_probe_minplus", "apsp_trace_enable", "apsp_trace_read", "apsp_batched_workspace_bytes",
+           "apsp_batched")
 
 
 def lib():
@@ -190,6 +193,59 @@ def apsp_trace_read(mode: int = -1):
     ms, n, pairs = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
     _check(_lib.apsp_trace_read(mode, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(pairs)), "apsp_trace_read")
     return ms.value, n.value, pairs.value
+
+
+class Batch:
+    """A batch of graphs packed into one device pool, in the layout apsp_batched expects:
+    graph g at element offset offsets[g], leading dimension round_up(n_g, 4)."""
+
+    def __init__(self, mats, device=None, pin=True):
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        mats = [np.asarray(m) for m in mats]
+        if not mats:
+            raise ValueError("empty batch")
+        dt = mats[0].dtype
+        if any(m.dtype != dt for m in mats) or dt not in (np.int32, np.float32):
+            raise TypeError("all graphs must share one dtype, int32 or float32")
+        self.ns = np.array([m.shape[0] for m in mats], np.int32)
+        self.lds = ((self.ns + 3) // 4 * 4).astype(np.int32)
+        sizes = self.ns.astype(np.int64) * self.lds
+        self.offsets = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(np.int64)
+        total = int(sizes.sum())
+        host = np.zeros(max(total, 4), dtype=dt)
+        for m, o, n, ld in zip(mats, self.offsets, self.ns, self.lds):
+            host[o:o + n * ld].reshape(n, ld)[:, :n] = m
+        self.host = torch.from_numpy(host)
+        if pin:
+            self.host = self.host.pin_memory()
+        self.dtype = self.host.dtype
+        self.pool = self.host.to(dev, non_blocking=True)
+        self.d_offsets = torch.from_numpy(self.offsets).to(dev)
+        self.d_ns = torch.from_numpy(self.ns).to(dev)
+        self.d_lds = torch.from_numpy(self.lds).to(dev)
+        self.order = np.argsort(-self.ns, kind="stable").astype(np.int32)  # largest first
+        self.d_order = torch.from_numpy(self.order).to(dev)
+        self.ws = torch.empty(_lib.apsp_batched_workspace_bytes(len(mats)), dtype=torch.uint8, device=dev)
+
+    def __len__(self):
+        return len(self.ns)
+
+    def graph(self, g, src=None):
+        """Graph g of a pool (the device pool by default) as an n x n view."""
+        src = self.pool if src is None else src
+        o, n, ld = int(self.offsets[g]), int(self.ns[g]), int(self.lds[g])
+        return src[o:o + n * ld].view(n, ld)[:, :n]
+
+
+def apsp_batched(batch: Batch, inf=None, stream=None, pool=None):
+    """Close every graph of `batch` (its device pool, or `pool`) in one persistent launch."""
+    code = _dtype_code(batch.pool)
+    ip, _keep = _inf_arg(inf, code)
+    p = batch.pool if pool is None else pool
+    _check(_lib.apsp_batched(p.data_ptr(), batch.d_offsets.data_ptr(), batch.d_ns.data_ptr(),
+                             batch.d_lds.data_ptr(), batch.d_order.data_ptr(), len(batch), code, ip,
+                             batch.ws.data_ptr(), batch.ws.numel(), _stream(stream)), "apsp_batched")
+    return batch
 
 
 ALGOS = {"fw": apsp_fw, "rkleene": apsp_rkleene}

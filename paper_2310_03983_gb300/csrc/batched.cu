@@ -1,0 +1,376 @@
+// batched.cu -- a7: close many independent graphs of uneven size in ONE persistent launch.
+//
+// The paper's experiment solves a thousand random graphs of 4..1000 vertices one by one
+// (Sec. 3.4, Sec. 4).  Launched one at a time, small closures are dominated by launch latency
+// and a medium graph's phase-3 grid covers only a fraction of the 152 SMs.  Here one CTA per
+// SM pulls graphs from an atomic work queue (the caller orders it largest first, so the
+// largest jobs start earliest -- longest-processing-time list scheduling) and closes each
+// graph alone, with the same blocked Floyd-Warshall schedule as apsp_fw:
+//   a1  normalise the graph in place and find its largest finite weight;
+//   for each 128-vertex diagonal block kb:
+//     phase 1  Eq. 1 on the diagonal tile, resident in shared memory;
+//     phase 2  row/column panel tiles = (min,+) products with the closed tile;
+//     phase 3  every other tile D[i][j] = min(D[i][j], D[i][kb] (x) D[kb][j]).
+// Phases 2-3 run the register-tiled slab arithmetic of the GEMM engine (slab.cuh), fed by a
+// three-stage cp.async pipeline (each graph has its own shape, so no per-graph TMA
+// descriptors are needed).  int32 graphs whose (n - 1) * largest finite weight < 2^24 use
+// the exact fp32 instruction sequence; others the int32 one.  One CTA per graph needs no
+// inter-CTA synchronisation: there is no spin-wait anywhere in this kernel.
+#include "slab.cuh"
+#include "tgemm.cuh"
+
+namespace apsp {
+
+constexpr int kBThreads = 256;
+constexpr int kBStages = 3;
+constexpr int kBSlabInts = kSlabM * kSlabK;  // 4096 ints per A or B slab
+constexpr int kBTileInts = kSlabM * kSlabN;  // 16384 ints per 128 x 128 tile
+constexpr int kBSmemBytes = (2 * kBStages * kBSlabInts + kBTileInts) * 4 + 256;
+
+struct BatchArgs {
+  int *pool;
+  const int64_t *offsets;
+  const int32_t *ns, *lds, *order;
+  int64_t count;
+  int inf_i;
+  float inf_f;
+  int *queue;
+  unsigned int *status;
+};
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(smem)), "l"(gmem),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <typename S> struct Store;
+template <> struct Store<int> {
+  static constexpr bool is_float = false;
+  static __device__ __forceinline__ int fix(int v, const BatchArgs &a, bool &bad) {
+    bad |= v < 0;
+    return v >= a.inf_i ? a.inf_i : v;
+  }
+  static __device__ __forceinline__ int finite_max(int v, const BatchArgs &a, int m) { return v < a.inf_i ? max(m, v) : m; }
+  static __device__ __forceinline__ int add(int x, int y) { return x + y; }
+};
+template <> struct Store<float> {
+  static constexpr bool is_float = true;
+  static __device__ __forceinline__ int fix(int bits, const BatchArgs &a, bool &bad) {
+    const float v = __int_as_float(bits);
+    bad |= !(v >= 0.0f);
+    return v >= a.inf_f ? 0x7f800000 : bits;
+  }
+  static __device__ __forceinline__ int finite_max(int, const BatchArgs &, int m) { return m; }
+  static __device__ __forceinline__ int add(int x, int y) {
+    return __float_as_int(__fadd_rn(__int_as_float(x), __int_as_float(y)));
+  }
+};
+
+// a1 for one graph, whole CTA: returns the largest finite weight (int32; 0 for float32).
+template <typename S>
+__device__ int normalise_graph(int *D, int n, int ld, const BatchArgs &a, int *red) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  bool bad = false;
+  int m = 0;
+  for (int i = warp; i < n; i += kBThreads / 32) {
+    int *row = D + (int64_t)i * ld;
+    for (int j = lane; j < n; j += 32) {
+      const int v = (j == i) ? 0 : Store<S>::fix(row[j], a, bad);
+      row[j] = v;
+      m = Store<S>::finite_max(v, a, m);
+    }
+  }
+  m = __reduce_max_sync(0xffffffffu, m);
+  if (lane == 0) red[warp] = m;
+  if (__syncthreads_or(bad) && threadIdx.x == 0) flag_status(a.status, APSP_ERR_DOMAIN);
+  int r = 0;
+#pragma unroll
+  for (int w = 0; w < kBThreads / 32; ++w) r = max(r, red[w]);
+  __syncthreads();  // red[] is reused by the next graph
+  return r;
+}
+
+// Phase 1: Eq. 1 on the bk x bk diagonal tile at (kb0, kb0), held in shared memory T
+// (row stride 128).  At step k row k and column k do not change (d[k][k] = 0, weights >= 0),
+// and a thread writes only values that strictly decrease, so one barrier per k suffices.
+template <typename S>
+__device__ void close_diag(int *D, int n, int ld, int kb0, int *T) {
+  const int bk = min(kSlabM, n - kb0);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tm = (warp & 3) * 4 + (lane >> 3), tn = (warp >> 2) * 8 + (lane & 7);
+  for (int e = threadIdx.x; e < kSlabM * 32; e += kBThreads) {  // 16-byte chunks, row-major
+    const int r = e >> 5, c = (e & 31) * 4;
+    if (r < bk && c < bk) *reinterpret_cast<int4 *>(T + r * kSlabN + c) =
+        *reinterpret_cast<const int4 *>(D + (int64_t)(kb0 + r) * ld + kb0 + c);
+  }
+  __syncthreads();
+  for (int k = 0; k < bk; ++k) {
+    int rowk[8];
+    const int4 u0 = *reinterpret_cast<const int4 *>(T + k * kSlabN + 4 * tn);
+    const int4 u1 = *reinterpret_cast<const int4 *>(T + k * kSlabN + 4 * tn + 64);
+    rowk[0] = u0.x; rowk[1] = u0.y; rowk[2] = u0.z; rowk[3] = u0.w;
+    rowk[4] = u1.x; rowk[5] = u1.y; rowk[6] = u1.z; rowk[7] = u1.w;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = tm + 16 * i;
+      if (r >= bk) break;
+      const int dik = T[r * kSlabN + k];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        int *p = T + r * kSlabN + 4 * tn + 64 * h;
+        int4 v = *reinterpret_cast<int4 *>(p);
+        int *e = reinterpret_cast<int *>(&v);
+        bool ch = false;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int c = 4 * tn + 64 * h + q;
+          const int s = Store<S>::add(dik, rowk[4 * h + q]);
+          // both operands are non-negative, so comparing bit patterns as int orders floats too
+          if (c < bk && s < e[q]) { e[q] = s; ch = true; }
+        }
+        if (ch) *reinterpret_cast<int4 *>(p) = v;
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < kSlabM * 32; e += kBThreads) {
+    const int r = e >> 5, c = (e & 31) * 4;
+    if (r < bk && c < bk) {
+      if (c + 3 < bk) {
+        *reinterpret_cast<int4 *>(D + (int64_t)(kb0 + r) * ld + kb0 + c) = *reinterpret_cast<const int4 *>(T + r * kSlabN + c);
+      } else {
+        for (int q = 0; q < bk - c; ++q) D[(int64_t)(kb0 + r) * ld + kb0 + c + q] = T[r * kSlabN + c + q];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// One 128 x 128 output tile C(cr, cc) = [min(C,)] A(ar, ac .. +K) (x) B(br .. +K, bc), whole CTA.
+// Out-of-graph rows and columns are zero-filled in shared memory and never stored; the
+// ragged last k-slab is bounded by kc.
+template <typename AR, bool ACC>
+__device__ void tile_product(int *D, int n, int ld, int ar, int ac, int br, int bc, int cr, int cc, int K, int *sA,
+                             int *sB, int *sC, int init_bits) {
+  typedef typename AR::T T;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tm = (warp & 3) * 4 + (lane >> 3), tn = (warp >> 2) * 8 + (lane & 7);
+  const int m_valid = min(kSlabM, n - cr), n_valid = min(kSlabN, n - cc);
+  const int nk = (K + kSlabK - 1) / kSlabK;
+  auto load_slab = [&](int kt, int st) {
+    int *As = sA + st * kBSlabInts, *Bs = sB + st * kBSlabInts;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = tid + kBThreads * u;
+      const int r = e >> 3, kq = e & 7;
+      const int row = ar + r, col = ac + kt * kSlabK + 4 * kq;
+      const bool ok = row < n && col < n;
+      cp_async16(As + a_off(r, kq), ok ? D + (int64_t)row * ld + col : D, ok);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = tid + kBThreads * u;
+      const int r = e >> 5, c4 = e & 31;
+      const int row = br + kt * kSlabK + r, col = bc + 4 * c4;
+      const bool ok = row < n && col < n;
+      cp_async16(Bs + r * kSlabN + 4 * c4, ok ? D + (int64_t)row * ld + col : D, ok);
+    }
+  };
+  if (ACC) {
+#pragma unroll 4
+    for (int u = 0; u < 16; ++u) {
+      const int e = tid + kBThreads * u;
+      const int r = e >> 5, c4 = e & 31;
+      const bool ok = r < m_valid && 4 * c4 < n_valid;
+      cp_async16(sC + r * kSlabN + 4 * c4, ok ? D + (int64_t)(cr + r) * ld + cc + 4 * c4 : D, ok);
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < kBStages - 1; ++s) {
+    if (s < nk) load_slab(s, s);
+    cp_async_commit();
+  }
+  T acc[8][8];
+  const T init = AR::from(init_bits);
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = init;
+  for (int kt = 0; kt < nk; ++kt) {
+    cp_async_wait<kBStages - 2>();
+    __syncthreads();
+    if (kt + kBStages - 1 < nk) load_slab(kt + kBStages - 1, (kt + kBStages - 1) % kBStages);
+    cp_async_commit();
+    const int st = kt % kBStages;
+    const int kc = K - kt * kSlabK;
+    if (kc >= kSlabK) AR::slab_full(sA + st * kBSlabInts, sB + st * kBSlabInts, tm, tn, acc);
+    else AR::slab_part(sA + st * kBSlabInts, sB + st * kBSlabInts, tm, tn, kc, acc);
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int rl = tm + 16 * i;
+    if (rl >= m_valid) continue;
+    int *crow = D + (int64_t)(cr + rl) * ld + cc;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int cl = 4 * tn + 64 * h;
+      if (ACC) {
+        const int4 v = *reinterpret_cast<const int4 *>(sC + rl * kSlabN + cl);
+        acc[i][4 * h + 0] = AR::mn(acc[i][4 * h + 0], AR::from(v.x));
+        acc[i][4 * h + 1] = AR::mn(acc[i][4 * h + 1], AR::from(v.y));
+        acc[i][4 * h + 2] = AR::mn(acc[i][4 * h + 2], AR::from(v.z));
+        acc[i][4 * h + 3] = AR::mn(acc[i][4 * h + 3], AR::from(v.w));
+      }
+      if (cl + 3 < n_valid) {
+        *reinterpret_cast<int4 *>(crow + cl) = make_int4(AR::to(acc[i][4 * h]), AR::to(acc[i][4 * h + 1]),
+                                                         AR::to(acc[i][4 * h + 2]), AR::to(acc[i][4 * h + 3]));
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (cl + q < n_valid) crow[cl + q] = AR::to(acc[i][4 * h + q]);
+      }
+    }
+  }
+  __syncthreads();  // shared buffers are reused by the next tile
+}
+
+// Blocked Floyd-Warshall of one normalised graph by the whole CTA.
+template <typename AR, typename S>
+__device__ void close_blocked(int *D, int n, int ld, int init_bits, int *sA, int *sB, int *sT) {
+  const int nb = (n + kSlabM - 1) / kSlabM;
+  for (int kb = 0; kb < nb; ++kb) {
+    const int kb0 = kb * kSlabM, bk = min(kSlabM, n - kb0);
+    close_diag<S>(D, n, ld, kb0, sT);
+    if (nb == 1) break;
+    __threadfence();
+    __syncthreads();
+    for (int t = 0; t < 2 * (nb - 1); ++t) {
+      if (t < nb - 1) {
+        const int j = (t + (t >= kb)) * kSlabN;
+        tile_product<AR, false>(D, n, ld, kb0, kb0, kb0, j, kb0, j, bk, sA, sB, sT, init_bits);
+      } else {
+        int i = t - (nb - 1);
+        i = (i + (i >= kb)) * kSlabM;
+        tile_product<AR, false>(D, n, ld, i, kb0, kb0, kb0, i, kb0, bk, sA, sB, sT, init_bits);
+      }
+    }
+    __threadfence();
+    __syncthreads();
+    for (int t = 0; t < (nb - 1) * (nb - 1); ++t) {
+      int i = t / (nb - 1), j = t - i * (nb - 1);
+      i = (i + (i >= kb)) * kSlabM;
+      j = (j + (j >= kb)) * kSlabN;
+      tile_product<AR, true>(D, n, ld, i, kb0, kb0, j, i, j, bk, sA, sB, sT, init_bits);
+    }
+    __threadfence();
+    __syncthreads();
+  }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kBThreads, 1) batched_kernel(const BatchArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  int *sA = reinterpret_cast<int *>(smem);
+  int *sB = sA + kBStages * kBSlabInts;
+  int *sT = sB + kBStages * kBSlabInts;  // phase-1 tile and phase-3 C tile
+  __shared__ int s_idx;
+  __shared__ int red[kBThreads / 32];
+  for (;;) {
+    if (threadIdx.x == 0) s_idx = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int64_t idx = s_idx;
+    __syncthreads();
+    if (idx >= a.count) break;
+    const int g = a.order ? a.order[idx] : (int)idx;
+    if (g < 0 || g >= a.count) {
+      if (threadIdx.x == 0) flag_status(a.status, APSP_ERR_ARG);
+      continue;
+    }
+    const int n = a.ns[g], ld = a.lds[g];
+    const int64_t off = a.offsets[g];
+    if (n <= 0) continue;
+    if (ld < n || (ld & 3) || (off & 3) || off < 0) {
+      if (threadIdx.x == 0) flag_status(a.status, APSP_ERR_ARG);
+      continue;
+    }
+    int *D = a.pool + off;
+    const int wmax = normalise_graph<S>(D, n, ld, a, red);
+    __threadfence();
+    __syncthreads();
+    if (Store<S>::is_float) {
+      close_blocked<ArithF32, S>(D, n, ld, 0x7f800000, sA, sB, sT);
+    } else if (small_int_bound(wmax, n - 1, 0)) {
+      close_blocked<ArithF32, S>(D, n, ld, a.inf_i, sA, sB, sT);
+    } else {
+      close_blocked<ArithI32, S>(D, n, ld, a.inf_i, sA, sB, sT);
+    }
+    __threadfence();
+    __syncthreads();
+  }
+}
+
+}  // namespace apsp
+
+extern "C" size_t apsp_batched_workspace_bytes(int64_t count) {
+  (void)count;
+  return 256;
+}
+
+extern "C" int apsp_batched(void *pool, const int64_t *offsets, const int32_t *ns, const int32_t *lds,
+                            const int32_t *order, int64_t count, int dtype, const void *inf, void *ws, size_t ws_bytes,
+                            void *stream) {
+  using namespace apsp;
+  if (!dtype_ok(dtype) || count < 0 || count > INT32_MAX) return APSP_ERR_ARG;
+  if (count == 0) return APSP_OK;
+  if (!pool || !offsets || !ns || !lds || reinterpret_cast<uintptr_t>(pool) % 16 != 0) return APSP_ERR_ARG;
+  if (ws && (ws_bytes < 256 || reinterpret_cast<uintptr_t>(ws) % 256 != 0)) return APSP_ERR_ARG;
+  BatchArgs a = {};
+  if (dtype == APSP_I32 ? resolve_inf_i32(inf, &a.inf_i) : resolve_inf_f32(inf, &a.inf_f)) return APSP_ERR_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  void *own = nullptr;
+  if (!ws) {
+    if (cudaMallocAsync(&own, 256, s) != cudaSuccess) {
+      cudaGetLastError();
+      return APSP_ERR_NOMEM;
+    }
+    ws = own;
+  }
+  a.pool = reinterpret_cast<int *>(pool);
+  a.offsets = offsets;
+  a.ns = ns;
+  a.lds = lds;
+  a.order = order;
+  a.count = count;
+  a.queue = reinterpret_cast<int *>(ws);
+  a.status = status_word();
+  int r = APSP_OK;
+  if (cudaMemsetAsync(a.queue, 0, sizeof(int), s) != cudaSuccess) r = APSP_ERR_CUDA;
+  const int64_t sms = sm_count();
+  const int grid = (int)(count < sms ? count : sms);
+  if (!r) {
+    if (dtype == APSP_I32) {
+      if (cudaFuncSetAttribute(batched_kernel<int>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBSmemBytes) !=
+          cudaSuccess)
+        r = APSP_ERR_CUDA;
+      else
+        batched_kernel<int><<<grid, kBThreads, kBSmemBytes, s>>>(a);
+    } else {
+      if (cudaFuncSetAttribute(batched_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBSmemBytes) !=
+          cudaSuccess)
+        r = APSP_ERR_CUDA;
+      else
+        batched_kernel<float><<<grid, kBThreads, kBSmemBytes, s>>>(a);
+    }
+    if (!r && cudaGetLastError() != cudaSuccess) r = APSP_ERR_CUDA;
+  }
+  if (own) cudaFreeAsync(own, s);
+  return r;
+}
