@@ -74,7 +74,8 @@ int apsp_version(void);
 const char *apsp_status_str(int status);
 
 /* Synchronises `stream`, then reads and clears the current device's sticky data-status
- * word into *out (APSP_OK, or APSP_ERR_DOMAIN / APSP_ERR_TIMEOUT if a kernel flagged one).
+ * word into *out: APSP_OK, or the most severe code a kernel flagged since the last read
+ * (APSP_ERR_TIMEOUT, then APSP_ERR_ARG for a skipped batch entry, then APSP_ERR_DOMAIN).
  * Returns APSP_OK, or APSP_ERR_CUDA if the synchronisation failed. */
 int apsp_device_status(void *stream, int *out);
 

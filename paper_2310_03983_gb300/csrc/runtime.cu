@@ -163,6 +163,9 @@ extern "C" int apsp_device_status(void *stream, int *out) {
   unsigned int bits = 0, zero = 0;
   APSP_CUDA_TRY(cudaMemcpyFromSymbol(&bits, apsp::g_status, sizeof(bits)));
   APSP_CUDA_TRY(cudaMemcpyToSymbol(apsp::g_status, &zero, sizeof(zero)));
-  *out = (bits & (1u << APSP_ERR_TIMEOUT)) ? APSP_ERR_TIMEOUT : (bits & (1u << APSP_ERR_DOMAIN)) ? APSP_ERR_DOMAIN : APSP_OK;
+  *out = (bits & (1u << APSP_ERR_TIMEOUT)) ? APSP_ERR_TIMEOUT
+         : (bits & (1u << APSP_ERR_ARG))    ? APSP_ERR_ARG
+         : (bits & (1u << APSP_ERR_DOMAIN)) ? APSP_ERR_DOMAIN
+                                            : APSP_OK;
   return APSP_OK;
 }
