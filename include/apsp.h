@@ -131,6 +131,24 @@ size_t apsp_rkleene_workspace_bytes(int64_t n, int64_t ld, int dtype, int cutoff
 int apsp_rkleene(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int cutoff,
                  void *ws, size_t ws_bytes, void *stream);
 
+/* ---- R-Kleene with no device allocation ------------------------------------------------
+ * The paper has no counterpart to this entry point.  It is apsp_rkleene for callers that
+ * cannot call cudaMalloc -- code inside a framework or plugin host that owns all device
+ * memory through its own pool, request paths that forbid allocator calls, processes under a
+ * hard memory budget.  Its scratch is a fixed array inside libapsp.so (about 16 MiB per GPU
+ * that loads the library, held until exit), so the caller passes only the matrix:
+ *   - n must be <= APSP_NOALLOC_MAX_N and ld a multiple of 4; otherwise APSP_ERR_ARG and
+ *     nothing is launched (use apsp_rkleene with a workspace instead);
+ *   - it calls no cudaMalloc, cudaFree or allocating library routine;
+ *   - the first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ *     make that first call before any stream capture;
+ *   - every call shares the array: calls that overlap on the GPU race and must be serialised
+ *     by the caller.
+ * Results are identical to apsp_rkleene's. */
+#define APSP_NOALLOC_MAX_N 4096
+int apsp_rkleene_noalloc(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int cutoff,
+                         void *stream);
+
 /* ---- a7: batched closure of many independent graphs in one persistent launch ----------
  * Closes `count` graphs in place.  Graph g is an ns[g] x ns[g] matrix stored row-major at
  * element offset offsets[g] of `pool` with leading dimension lds[g]; it is closed exactly as
