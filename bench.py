@@ -48,6 +48,21 @@ WORKLOADS = {
 SMS_NOMINAL = 152
 LANES_PER_SM = 128
 MAX_SM_MHZ = 2070.0
+# DRAM traffic of one FW phase-3 launch per C element (dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture at n = 8192, block 50: 467.8 MB over 8064^2 C
+# elements), valid only for the kernel sources it was taken on (hash below).
+PHASE3_DRAM_BYTES_PER_C_ELEM = 7.197
+PHASE3_TRAFFIC_SRC_HASH = "e3436e5f396e7d0f"
+TGEMM_SOURCES = ("tgemm.cu", "tgemm.cuh", "slab.cuh", "common.cuh")
+
+
+def tgemm_src_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in TGEMM_SOURCES:
+        with open(os.path.join(ROOT, "paper_2310_03983_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def parse():
@@ -338,6 +353,11 @@ def run_ours(args, w, rank, world, local_rank):
     peak_max = 2.0 * sms * LANES_PER_SM * MAX_SM_MHZ * 1e6 / 1e12
     achieved = 2.0 * k_pairs / (k_ms * 1e-3) / 1e12 if k_ms > 0 else None
     sm_mhz = clocks.get("sm_mhz")
+    traffic = None
+    if dom_mode == 2 and tgemm_src_hash() == PHASE3_TRAFFIC_SRC_HASH:
+        traffic = {"bytes_per_launch": round(PHASE3_DRAM_BYTES_PER_C_ELEM * (n - 128) ** 2),
+                   "algorithmic_bytes_per_launch": 8 * (n - 128) ** 2,
+                   "source": "ncu dram bytes of one phase-3 launch at n=8192, scaled by (n-128)^2"}
     nb = -(-n // 128)
     launches_per_step = {"fw": 1 + 3 * nb, "gemm": 2, "rkleene": None}[w["algo"]]
     line = {
@@ -355,7 +375,7 @@ def run_ours(args, w, rank, world, local_rank):
                                                 if achieved and sm_mhz else None),
                      "peak_basis": f"{sms} SMs x {LANES_PER_SM} lanes x 1 pair/lane/clk x {MAX_SM_MHZ:.0f} MHz x 2 ops",
                      "launches": k_launches, "avg_launch_ms": round(k_ms / max(1, k_launches), 4),
-                     "traffic": None},
+                     "traffic": traffic},
         "clocks": clocks,
         "e2e": {"value": round(e2e_val, 2) if e2e_val else None, "unit": "Gop/s",
                 "h2d_bytes_per_step": mat_bytes, "d2h_bytes_per_step": mat_bytes},
