@@ -165,6 +165,31 @@ int apsp_batched(void *pool, const int64_t *offsets, const int32_t *ns, const in
                  const int32_t *order, int64_t count, int dtype, const void *inf, void *ws,
                  size_t ws_bytes, void *stream);
 
+/* ---- a8: the planner's cost-model network ---------------------------------------------
+ * A perceptron with two hidden layers of 64 ReLU units, fp32, that predicts the log run time
+ * of a closure configuration from a feature vector of in_dim (1..32) floats:
+ *   h1 = relu(x W1 + b1); h2 = relu(h1 W2 + b2); y = h2 . w3 + b3.
+ * params is one flat device array [W1 (in_dim x 64, row-major), b1 (64), W2 (64 x 64), b2 (64),
+ * w3 (64), b3 (1)] of apsp_mlp_param_count(in_dim) floats.  x is batch x in_dim row-major.
+ *  - apsp_mlp_forward: out[batch]; if acts is not NULL it receives h1 and h2 per sample
+ *    (batch x 2 x 64 floats), which apsp_mlp_backward needs.
+ *  - apsp_mlp_loss: mean squared error *loss (device, may be NULL) and dout = dL/dout.
+ *  - apsp_mlp_backward: grads (same layout as params) of the loss whose dout is given;
+ *    deterministic; workspace of apsp_mlp_backward_workspace_bytes(in_dim, batch).
+ *  - apsp_mlp_adam: one Adam step (bias-corrected; step counts from 1) over count floats.
+ * The paper has no learned component; this serves the planner only. */
+int64_t apsp_mlp_param_count(int in_dim);
+size_t apsp_mlp_backward_workspace_bytes(int in_dim, int batch);
+int apsp_mlp_forward(const float *params, int in_dim, const float *x, int batch, float *out,
+                     float *acts, void *stream);
+int apsp_mlp_loss(const float *out, const float *y, int batch, float *dout, float *loss,
+                  void *stream);
+int apsp_mlp_backward(const float *params, int in_dim, const float *x, const float *acts,
+                      const float *dout, int batch, float *grads, void *ws, size_t ws_bytes,
+                      void *stream);
+int apsp_mlp_adam(float *params, const float *grads, float *m, float *v, int64_t count, float lr,
+                  float beta1, float beta2, float eps, int step, void *stream);
+
 /* ---- measurement: launch tracing ------------------------------------------------------
  * apsp_trace_enable(1) makes every launch of the tropical GEMM engine (the standalone
  * product and blocked-FW phases 2 and 3) record a CUDA event before and after itself on its

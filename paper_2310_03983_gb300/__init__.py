@@ -53,6 +53,13 @@ def _load():
         "apsp_probe_minplus": ([i32, i32, i32, i32, vp, vp], i32),
         "apsp_batched_workspace_bytes": ([i64], sz),
         "apsp_batched": ([vp, vp, vp, vp, vp, i64, i32, vp, vp, sz, vp], i32),
+        "apsp_mlp_param_count": ([i32], i64),
+        "apsp_mlp_backward_workspace_bytes": ([i32, i32], sz),
+        "apsp_mlp_forward": ([vp, i32, vp, i32, vp, vp, vp], i32),
+        "apsp_mlp_loss": ([vp, vp, i32, vp, vp, vp], i32),
+        "apsp_mlp_backward": ([vp, i32, vp, vp, vp, i32, vp, vp, sz, vp], i32),
+        "apsp_mlp_adam": ([vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, i32,
+                           vp], i32),
         "apsp_trace_enable": ([i32], i32),
         "apsp_trace_read": ([i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                              ctypes.POINTER(ctypes.c_double)], i32),
@@ -68,7 +75,8 @@ EXPORTS = ("apsp_version", "apsp_status_str", "apsp_device_status", "apsp_normal
            "tropical_gemm_workspace_bytes", "tropical_gemm",
            "apsp_fw_workspace_bytes", "apsp_fw", "apsp_rkleene_workspace_bytes", "apsp_rkleene",
            "apsp_probe_minplus", "apsp_trace_enable", "apsp_trace_read", "apsp_batched_workspace_bytes",
-           "apsp_batched")
+           "apsp_batched", "apsp_mlp_param_count", "apsp_mlp_backward_workspace_bytes", "apsp_mlp_forward",
+           "apsp_mlp_loss", "apsp_mlp_backward", "apsp_mlp_adam")
 
 
 def lib():
@@ -246,6 +254,47 @@ def apsp_batched(batch: Batch, inf=None, stream=None, pool=None):
                              batch.d_lds.data_ptr(), batch.d_order.data_ptr(), len(batch), code, ip,
                              batch.ws.data_ptr(), batch.ws.numel(), _stream(stream)), "apsp_batched")
     return batch
+
+
+def _fptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError("expected a contiguous float32 CUDA tensor")
+    return t.data_ptr()
+
+
+def apsp_mlp_param_count(in_dim: int) -> int:
+    return int(_lib.apsp_mlp_param_count(in_dim))
+
+
+def apsp_mlp_forward(params, x, out, acts=None, stream=None):
+    batch, in_dim = x.shape
+    _check(_lib.apsp_mlp_forward(_fptr(params), in_dim, _fptr(x), batch, _fptr(out), _fptr(acts), _stream(stream)),
+           "apsp_mlp_forward")
+    return out
+
+
+def apsp_mlp_loss(out, y, dout, loss=None, stream=None):
+    _check(_lib.apsp_mlp_loss(_fptr(out), _fptr(y), out.numel(), _fptr(dout), _fptr(loss), _stream(stream)),
+           "apsp_mlp_loss")
+    return dout
+
+
+def apsp_mlp_backward(params, x, acts, dout, grads, ws=None, stream=None):
+    batch, in_dim = x.shape
+    need = _lib.apsp_mlp_backward_workspace_bytes(in_dim, batch)
+    if ws is None or ws.numel() * ws.element_size() < need:
+        raise ValueError(f"backward needs a workspace of {need} bytes")
+    _check(_lib.apsp_mlp_backward(_fptr(params), in_dim, _fptr(x), _fptr(acts), _fptr(dout), batch, _fptr(grads),
+                                  ws.data_ptr(), ws.numel() * ws.element_size(), _stream(stream)),
+           "apsp_mlp_backward")
+    return grads
+
+
+def apsp_mlp_adam(params, grads, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(_lib.apsp_mlp_adam(_fptr(params), _fptr(grads), _fptr(m), _fptr(v), params.numel(), lr, beta1, beta2, eps,
+                              step, _stream(stream)), "apsp_mlp_adam")
 
 
 ALGOS = {"fw": apsp_fw, "rkleene": apsp_rkleene}

@@ -1,0 +1,119 @@
+"""a8: the cost-model network kernels against the fp64 oracle, and the planner's regret and
+gain measured on this GPU."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def apsp():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_2310_03983_gb300 as m
+    return m
+
+
+def _t(a):
+    return torch.tensor(np.asarray(a), dtype=torch.float32, device="cuda")
+
+
+@pytest.mark.parametrize("in_dim,batch", [(7, 1), (7, 33), (3, 100), (32, 257)])
+def test_network_kernels_match_oracle(apsp, in_dim, batch):
+    rng = np.random.default_rng(in_dim * 1000 + batch)
+    p = omlp.init(in_dim, seed=batch).astype(np.float32).astype(np.float64)
+    x = rng.normal(size=(batch, in_dim)).astype(np.float32).astype(np.float64)
+    t = rng.normal(size=batch).astype(np.float32).astype(np.float64)
+    P, X, T = _t(p), _t(x), _t(t)
+    out = torch.empty(batch, dtype=torch.float32, device="cuda")
+    acts = torch.empty(batch * 128, dtype=torch.float32, device="cuda")
+    apsp.apsp_mlp_forward(P, X, out, acts)
+    y, h1, h2 = omlp.forward(p, x)
+    assert np.allclose(out.cpu().numpy(), y, rtol=1e-4, atol=1e-4)
+    a = acts.cpu().numpy().reshape(batch, 2, 64)
+    assert np.allclose(a[:, 0], h1, rtol=1e-4, atol=1e-4) and np.allclose(a[:, 1], h2, rtol=1e-4, atol=1e-4)
+    dout = torch.empty_like(out)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    apsp.apsp_mlp_loss(out, T, dout, loss)
+    assert np.isclose(loss.item(), omlp.loss(p, x, t), rtol=1e-4, atol=1e-5)
+    grads = torch.empty_like(P)
+    ws = torch.empty(apsp.lib().apsp_mlp_backward_workspace_bytes(in_dim, batch), dtype=torch.uint8, device="cuda")
+    apsp.apsp_mlp_backward(P, X, acts, dout, grads, ws)
+    g = grads.cpu().numpy()
+    want = omlp.grad(p, x, t)
+    scale = np.abs(want).max() + 1e-6
+    assert np.max(np.abs(g - want)) <= 1e-4 * scale + 1e-6
+    # deterministic: the same call twice gives identical bits
+    g2 = torch.empty_like(P)
+    apsp.apsp_mlp_backward(P, X, acts, dout, g2, ws)
+    assert torch.equal(grads, g2)
+
+
+def test_adam_step_matches_definition(apsp):
+    rng = np.random.default_rng(4)
+    n = 5000
+    p, g = rng.normal(size=n), rng.normal(size=n)
+    m, v = rng.normal(size=n) * 0.1, np.abs(rng.normal(size=n)) * 0.1
+    P, G, M, V = _t(p), _t(g), _t(m), _t(v)
+    lr, b1, b2, eps, step = 1e-2, 0.9, 0.999, 1e-8, 3
+    apsp.apsp_mlp_adam(P, G, M, V, lr, step, b1, b2, eps)
+    m2 = b1 * m + (1 - b1) * g
+    v2 = b2 * v + (1 - b2) * g * g
+    p2 = p - lr * (m2 / (1 - b1 ** step)) / (np.sqrt(v2 / (1 - b2 ** step)) + eps)
+    assert np.allclose(M.cpu().numpy(), m2, rtol=1e-5, atol=1e-6)
+    assert np.allclose(V.cpu().numpy(), v2, rtol=1e-5, atol=1e-6)
+    assert np.allclose(P.cpu().numpy(), p2, rtol=1e-5, atol=1e-5)
+
+
+def test_training_fits_a_known_function(apsp):
+    from paper_2310_03983_gb300 import planner
+    rng = np.random.default_rng(0)
+    rows = []
+    for n in np.unique(np.rint(np.exp(rng.uniform(np.log(64), np.log(8192), 200))).astype(int)):
+        for algo, param in planner.CANDIDATES:
+            ms = 1e-6 * n ** 3 * (1.0 if algo == "fw" else 1.3) + 0.05  # a smooth synthetic cost
+            rows.append({"n": int(n), "density": 0.1, "dtype": "int32", "algo": algo, "param": param, "ms": ms})
+    model = planner.CostModel(seed=1)
+    hist = model.fit(rows, epochs=2000, lr=3e-3)
+    assert hist[-1] < 0.05 * hist[0]
+    assert model.choose(4096, 0.1, "int32") == ("fw", 0)
+
+
+def test_planner_regret_and_gain_on_this_gpu(apsp, tmp_path):
+    """Autotune a sweep (the training log), fit the network, then on held-out graphs compare
+    the network's choice with the exhaustive best (regret) and with always-FW (gain)."""
+    from paper_2310_03983_gb300 import planner
+    log = str(tmp_path / "timings.jsonl")
+    tuner = planner.Autotuner(log_path=log, reps=3)
+    train_n = [96, 192, 320, 512, 768, 1100, 1536, 2048, 3072, 4096]
+    for i, n in enumerate(train_n):
+        for dt in ("int32", "float32"):
+            h = workloads.er_graph(n, 0.05 if i % 2 else 0.3, dt, seed=n,
+                                   **({"lo": 1, "hi": 100} if dt == "int32" else {"dist": "uniform01"}))
+            tuner.measure(h, tag="train")
+    rows = planner.load_rows(log)
+    assert len(rows) == len(tuner.rows) > 0
+    model = planner.CostModel(seed=0)
+    model.fit(rows, epochs=3000)
+    held_out = [128, 400, 900, 1800, 2600, 3500]
+    t_model = t_best = t_fw = 0.0
+    for n in held_out:
+        h = workloads.er_graph(n, 0.1, "int32", lo=1, hi=100, seed=7 * n)
+        meas = {(r["algo"], r["param"]): r["ms"] for r in tuner.measure(h, tag="held_out")}
+        choice = model.choose(n, planner.density_of(h), "int32")
+        t_model += meas[choice]
+        t_best += min(meas.values())
+        t_fw += meas[("fw", 0)]
+    regret = t_model / t_best - 1.0
+    gain = t_fw / t_model - 1.0
+    print(json.dumps({"regret": round(regret, 4), "gain_vs_always_fw": round(gain, 4),
+                      "t_model_ms": round(t_model, 3), "t_best_ms": round(t_best, 3), "t_fw_ms": round(t_fw, 3)}))
+    assert regret <= 0.25
+    assert t_model <= t_fw * 1.05
