@@ -245,6 +245,36 @@ class Batch:
         return src[o:o + n * ld].view(n, ld)[:, :n]
 
 
+class _OneGraph:
+    """Device descriptor arrays of a batch holding one graph (offset 0), cached by shape."""
+    _cache: dict = {}
+
+    @classmethod
+    def get(cls, n: int, ld: int, dev):
+        key = (n, ld, str(dev))
+        if key not in cls._cache:
+            cls._cache[key] = (torch.zeros(1, dtype=torch.int64, device=dev),
+                               torch.tensor([n], dtype=torch.int32, device=dev),
+                               torch.tensor([ld], dtype=torch.int32, device=dev),
+                               torch.empty(_lib.apsp_batched_workspace_bytes(1), dtype=torch.uint8, device=dev))
+        return cls._cache[key]
+
+
+def apsp_close_cta(d: torch.Tensor, inf=None, stream=None):
+    """Close one graph with a single CTA (apsp_batched on a batch of one): one launch, no
+    inter-CTA phases -- the cheapest plan for small graphs."""
+    n = d.shape[0]
+    p, ld = _mat(d, "d")
+    if d.shape[1] != n:
+        raise ValueError("d must be square")
+    off, ns, lds, ws = _OneGraph.get(n, ld, d.device)
+    code = _dtype_code(d)
+    ip, _keep = _inf_arg(inf, code)
+    _check(_lib.apsp_batched(p, off.data_ptr(), ns.data_ptr(), lds.data_ptr(), None, 1, code, ip, ws.data_ptr(),
+                             ws.numel(), _stream(stream)), "apsp_batched")
+    return d
+
+
 def apsp_batched(batch: Batch, inf=None, stream=None, pool=None):
     """Close every graph of `batch` (its device pool, or `pool`) in one persistent launch."""
     code = _dtype_code(batch.pool)

@@ -16,6 +16,7 @@
 // descriptors are needed).  int32 graphs whose (n - 1) * largest finite weight < 2^24 use
 // the exact fp32 instruction sequence; others the int32 one.  One CTA per graph needs no
 // inter-CTA synchronisation: there is no spin-wait anywhere in this kernel.
+#include "diag.cuh"
 #include "slab.cuh"
 #include "tgemm.cuh"
 
@@ -95,59 +96,18 @@ __device__ int normalise_graph(int *D, int n, int ld, const BatchArgs &a, int *r
   return r;
 }
 
-// Phase 1: Eq. 1 on the bk x bk diagonal tile at (kb0, kb0), held in shared memory T
-// (row stride 128).  At step k row k and column k do not change (d[k][k] = 0, weights >= 0),
-// and a thread writes only values that strictly decrease, so one barrier per k suffices.
+// Phase 1: Eq. 1 on the bk x bk diagonal tile at (kb0, kb0), closed in registers (diag.cuh);
+// int32 graphs relax in int32 (exact), float32 graphs in fp32.
 template <typename S>
-__device__ void close_diag(int *D, int n, int ld, int kb0, int *T) {
+__device__ void close_diag(int *D, int n, int ld, int kb0, int *buf) {
   const int bk = min(kSlabM, n - kb0);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tm = (warp & 3) * 4 + (lane >> 3), tn = (warp >> 2) * 8 + (lane & 7);
-  for (int e = threadIdx.x; e < kSlabM * 32; e += kBThreads) {  // 16-byte chunks, row-major
-    const int r = e >> 5, c = (e & 31) * 4;
-    if (r < bk && c < bk) *reinterpret_cast<int4 *>(T + r * kSlabN + c) =
-        *reinterpret_cast<const int4 *>(D + (int64_t)(kb0 + r) * ld + kb0 + c);
-  }
-  __syncthreads();
-  for (int k = 0; k < bk; ++k) {
-    int rowk[8];
-    const int4 u0 = *reinterpret_cast<const int4 *>(T + k * kSlabN + 4 * tn);
-    const int4 u1 = *reinterpret_cast<const int4 *>(T + k * kSlabN + 4 * tn + 64);
-    rowk[0] = u0.x; rowk[1] = u0.y; rowk[2] = u0.z; rowk[3] = u0.w;
-    rowk[4] = u1.x; rowk[5] = u1.y; rowk[6] = u1.z; rowk[7] = u1.w;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int r = tm + 16 * i;
-      if (r >= bk) break;
-      const int dik = T[r * kSlabN + k];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        int *p = T + r * kSlabN + 4 * tn + 64 * h;
-        int4 v = *reinterpret_cast<int4 *>(p);
-        int *e = reinterpret_cast<int *>(&v);
-        bool ch = false;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int c = 4 * tn + 64 * h + q;
-          const int s = Store<S>::add(dik, rowk[4 * h + q]);
-          // both operands are non-negative, so comparing bit patterns as int orders floats too
-          if (c < bk && s < e[q]) { e[q] = s; ch = true; }
-        }
-        if (ch) *reinterpret_cast<int4 *>(p) = v;
-      }
-    }
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < kSlabM * 32; e += kBThreads) {
-    const int r = e >> 5, c = (e & 31) * 4;
-    if (r < bk && c < bk) {
-      if (c + 3 < bk) {
-        *reinterpret_cast<int4 *>(D + (int64_t)(kb0 + r) * ld + kb0 + c) = *reinterpret_cast<const int4 *>(T + r * kSlabN + c);
-      } else {
-        for (int q = 0; q < bk - c; ++q) D[(int64_t)(kb0 + r) * ld + kb0 + c + q] = T[r * kSlabN + c + q];
-      }
-    }
-  }
+  int *T = D + (int64_t)kb0 * ld + kb0;
+  int r[8][8];
+  load_tile_regs(r, T, ld, bk, tm, tn);
+  close_tile_regs<Store<S>::is_float>(r, bk, tm, tn, buf);
+  store_tile_regs(r, T, ld, bk, tm, tn);
   __syncthreads();
 }
 

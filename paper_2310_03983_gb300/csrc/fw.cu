@@ -13,59 +13,31 @@
 #include <algorithm>
 
 #include "closure.cuh"
+#include "diag.cuh"
 
 namespace apsp {
 
-// Phase 1: Eq. 1 on the bk x bk diagonal tile held in shared memory.  At step k, row k and
-// column k do not change (d[k][k] = 0 and weights are non-negative), so every thread can
-// read them while others update the rest of the tile; one barrier per k orders the steps.
-// A thread only writes when the value strictly decreases, so row/column k are never written
-// during step k.
-template <typename T>
-__global__ void __launch_bounds__(1024) fw_diag_kernel(T *d, int64_t ld, int64_t n, int64_t kb) {
-  extern __shared__ uint8_t smem_raw[];
-  T(*S)[kBM] = reinterpret_cast<T(*)[kBM]>(smem_raw);
+// Phase 1: Eq. 1 on the bk x bk diagonal tile, closed in registers by one 256-thread CTA
+// (diag.cuh).  int32 tiles are relaxed in int32 (exact for any weights), float32 in fp32.
+template <bool FLOAT>
+__global__ void __launch_bounds__(256) fw_diag_kernel(int *d, int64_t ld, int64_t n, int64_t kb) {
+  __shared__ __align__(16) int buf[512];
   const int64_t kb0 = kb * kBM;
   const int bk = (int)std::min<int64_t>(kBM, n - kb0);
-  T *base = d + kb0 * ld + kb0;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int e = threadIdx.x; e < kBM * kBM; e += blockDim.x) {
-    const int r = e >> 7, c = e & (kBM - 1);
-    if (r < bk && c < bk) S[r][c] = base[(int64_t)r * ld + c];
-  }
-  __syncthreads();
-  for (int k = 0; k < bk; ++k) {
-#pragma unroll
-    for (int rr = 0; rr < 4; ++rr) {
-      const int i = ty + 32 * rr;
-      if (i >= bk) break;
-      const T dik = S[i][k];
-#pragma unroll
-      for (int cc = 0; cc < 4; ++cc) {
-        const int j = tx + 32 * cc;
-        if (j < bk) {
-          const T v = Ops<T>::add(dik, S[k][j]);
-          if (v < S[i][j]) S[i][j] = v;
-        }
-      }
-    }
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < kBM * kBM; e += blockDim.x) {
-    const int r = e >> 7, c = e & (kBM - 1);
-    if (r < bk && c < bk) base[(int64_t)r * ld + c] = S[r][c];
-  }
+  int *T = d + kb0 * ld + kb0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tm = (warp & 3) * 4 + (lane >> 3), tn = (warp >> 2) * 8 + (lane & 7);
+  int r[8][8];
+  load_tile_regs(r, T, ld, bk, tm, tn);
+  close_tile_regs<FLOAT>(r, bk, tm, tn, buf);
+  store_tile_regs(r, T, ld, bk, tm, tn);
 }
 
 int launch_fw_diag(void *d, int64_t ld, int64_t n, int64_t kb, int dtype, cudaStream_t s) {
-  const int smem = kBM * kBM * 4;
-  if (dtype == APSP_I32) {
-    APSP_CUDA_TRY(cudaFuncSetAttribute(fw_diag_kernel<int>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    fw_diag_kernel<int><<<1, 1024, smem, s>>>(reinterpret_cast<int *>(d), ld, n, kb);
-  } else {
-    APSP_CUDA_TRY(cudaFuncSetAttribute(fw_diag_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    fw_diag_kernel<float><<<1, 1024, smem, s>>>(reinterpret_cast<float *>(d), ld, n, kb);
-  }
+  if (dtype == APSP_I32)
+    fw_diag_kernel<false><<<1, 256, 0, s>>>(reinterpret_cast<int *>(d), ld, n, kb);
+  else
+    fw_diag_kernel<true><<<1, 256, 0, s>>>(reinterpret_cast<int *>(d), ld, n, kb);
   APSP_LAUNCH_CHECK();
   return APSP_OK;
 }

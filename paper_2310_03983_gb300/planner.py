@@ -1,7 +1,8 @@
 """a8: choosing how to close a graph -- exhaustive autotuning and a learned cost model.
 
-A closure can run as blocked Floyd-Warshall or as R-Kleene with a leaf cutoff (Sec. 3.2,
-Sec. 3.3); which is fastest depends on the size and type of the graph.  Two planners pick the
+A closure can run as blocked Floyd-Warshall (many launches over all SMs), as R-Kleene with a
+leaf cutoff (Sec. 3.3), or on a single CTA in one launch (the batched kernel on a batch of one);
+which is fastest depends on the size and type of the graph.  Two planners pick the
 configuration from the graph's features (vertex count, edge density, dtype):
 
 * ``Autotuner`` times every candidate on the GPU (median of a few runs) and keeps the fastest.
@@ -26,11 +27,12 @@ import time
 import numpy as np
 import torch
 
-from . import (apsp_fw, apsp_mlp_adam, apsp_mlp_backward, apsp_mlp_forward, apsp_mlp_loss, apsp_mlp_param_count,
+from . import (apsp_close_cta, apsp_fw, apsp_mlp_adam, apsp_mlp_backward, apsp_mlp_forward, apsp_mlp_loss, apsp_mlp_param_count,
                apsp_rkleene, apsp_rkleene_workspace_bytes, lib)
 
-CANDIDATES = (("fw", 0), ("rkleene", 128), ("rkleene", 256), ("rkleene", 512), ("rkleene", 1024))
-IN_DIM = 7
+CANDIDATES = (("fw", 0), ("rkleene", 128), ("rkleene", 256), ("rkleene", 512), ("rkleene", 1024), ("cta", 0))
+CTA_MAX_N = 1024  # beyond this one SM is far too slow to be worth timing
+IN_DIM = 8
 HIDDEN = 64
 
 
@@ -38,8 +40,15 @@ def features(n: int, density: float, dtype: str, algo: str, param: int) -> list[
     """Feature vector of a (graph, configuration) pair, each entry scaled to about [0, 1]."""
     rk = algo == "rkleene"
     return [math.log2(max(n, 1)) / 15.0, float(density), 1.0 if dtype == "float32" else 0.0,
-            0.0 if rk else 1.0, 1.0 if rk else 0.0, math.log2(param) / 11.0 if rk else 0.0,
+            1.0 if algo == "fw" else 0.0, 1.0 if rk else 0.0, 1.0 if algo == "cta" else 0.0,
+            math.log2(param) / 11.0 if rk else 0.0,
             (math.log2(max(n, 1)) - math.log2(param)) / 8.0 if rk and param else 0.0]
+
+
+def applicable(n: int):
+    """Candidates worth considering for an n-vertex graph."""
+    return [(a, p) for a, p in CANDIDATES
+            if not (a == "rkleene" and p >= n) and not (a == "cta" and n > CTA_MAX_N)]
 
 
 def density_of(h: np.ndarray, inf: int = 0x3FFFFFFF) -> float:
@@ -54,6 +63,8 @@ def density_of(h: np.ndarray, inf: int = 0x3FFFFFFF) -> float:
 def run_config(d: torch.Tensor, algo: str, param: int, ws: torch.Tensor | None = None):
     if algo == "fw":
         apsp_fw(d, ws=ws)
+    elif algo == "cta":
+        apsp_close_cta(d)
     else:
         apsp_rkleene(d, cutoff=param, ws=ws)
 
@@ -91,9 +102,7 @@ class Autotuner:
         dens = density_of(h)
         d0 = torch.from_numpy(h).cuda()
         rows = []
-        for algo, param in CANDIDATES:
-            if algo == "rkleene" and param >= n:
-                continue  # degenerates to blocked Floyd-Warshall
+        for algo, param in applicable(n):
             ms = time_config(d0, algo, param, self.reps)
             rows.append({"n": n, "density": round(dens, 6), "dtype": dtype, "algo": algo, "param": param,
                          "ms": round(ms, 5), "tag": tag, "gpu": torch.cuda.get_device_name()})
@@ -159,7 +168,7 @@ class CostModel:
 
     # -- inference -----------------------------------------------------------------------
     def predict_ms(self, n: int, density: float, dtype: str) -> dict:
-        cands = [(a, p) for a, p in CANDIDATES if not (a == "rkleene" and p >= n)]
+        cands = applicable(n)
         X = torch.tensor([features(n, density, dtype, a, p) for a, p in cands], dtype=torch.float32,
                          device=self.device)
         out = torch.empty(len(cands), dtype=torch.float32, device=self.device)

@@ -168,7 +168,16 @@ def _graph(n, p, dtype, seed):
     return workloads.er_graph(n, p, "float32", dist="lognormal", lo=0.0, hi=1.0, seed=seed)
 
 
-ALGOS = [("fw", 0), ("rkleene", 128), ("rkleene", 256)]
+ALGOS = [("fw", 0), ("rkleene", 128), ("rkleene", 256), ("cta", 0)]
+
+
+def _close(apsp, d, algo, param):
+    if algo == "fw":
+        apsp.apsp_fw(d)
+    elif algo == "cta":
+        apsp.apsp_close_cta(d)
+    else:
+        apsp.apsp_rkleene(d, cutoff=param)
 
 
 @pytest.mark.parametrize("dtype", [np.int32, np.float32])
@@ -178,7 +187,7 @@ def test_closure_parity_small(apsp, dtype, n):
     want = oracle.fw(h, threads=THREADS)
     for algo, param in ALGOS:
         d = torch.from_numpy(h).cuda()
-        (apsp.apsp_fw if algo == "fw" else apsp.apsp_rkleene)(d, **({} if algo == "fw" else {"cutoff": param}))
+        _close(apsp, d, algo, param)
         assert_dist_equal(d.cpu().numpy(), want, f"{algo}/{param} n={n}")
     assert apsp.apsp_device_status() == 0
 

@@ -77,13 +77,14 @@ def test_training_fits_a_known_function(apsp):
     rng = np.random.default_rng(0)
     rows = []
     for n in np.unique(np.rint(np.exp(rng.uniform(np.log(64), np.log(8192), 200))).astype(int)):
-        for algo, param in planner.CANDIDATES:
+        for algo, param in planner.applicable(int(n)):
             ms = 1e-6 * n ** 3 * (1.0 if algo == "fw" else 1.3) + 0.05  # a smooth synthetic cost
             rows.append({"n": int(n), "density": 0.1, "dtype": "int32", "algo": algo, "param": param, "ms": ms})
     model = planner.CostModel(seed=1)
     hist = model.fit(rows, epochs=2000, lr=3e-3)
     assert hist[-1] < 0.05 * hist[0]
     assert model.choose(4096, 0.1, "int32") == ("fw", 0)
+    assert model.choose(100, 0.1, "int32") == ("fw", 0)
 
 
 def test_planner_regret_and_gain_on_this_gpu(apsp, tmp_path):
@@ -92,7 +93,7 @@ def test_planner_regret_and_gain_on_this_gpu(apsp, tmp_path):
     from paper_2310_03983_gb300 import planner
     log = str(tmp_path / "timings.jsonl")
     tuner = planner.Autotuner(log_path=log, reps=3)
-    train_n = [96, 192, 320, 512, 768, 1100, 1536, 2048, 3072, 4096]
+    train_n = [48, 96, 160, 192, 320, 512, 640, 768, 1100, 1536, 2048, 3072, 4096]
     for i, n in enumerate(train_n):
         for dt in ("int32", "float32"):
             h = workloads.er_graph(n, 0.05 if i % 2 else 0.3, dt, seed=n,
@@ -102,7 +103,7 @@ def test_planner_regret_and_gain_on_this_gpu(apsp, tmp_path):
     assert len(rows) == len(tuner.rows) > 0
     model = planner.CostModel(seed=0)
     model.fit(rows, epochs=3000)
-    held_out = [128, 400, 900, 1800, 2600, 3500]
+    held_out = [64, 128, 256, 400, 900, 1800, 2600, 3500]
     t_model = t_best = t_fw = 0.0
     for n in held_out:
         h = workloads.er_graph(n, 0.1, "int32", lo=1, hi=100, seed=7 * n)
