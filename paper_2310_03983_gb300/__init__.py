@@ -267,6 +267,10 @@ def apsp_close_cta(d: torch.Tensor, inf=None, stream=None):
     p, ld = _mat(d, "d")
     if d.shape[1] != n:
         raise ValueError("d must be square")
+    if n <= 1:
+        ld = 4  # a single row: the leading dimension is never used to address memory
+    elif ld % 4 != 0:
+        return apsp_fw(d, inf=inf, stream=stream)  # the single-CTA kernel needs 16-byte rows
     off, ns, lds, ws = _OneGraph.get(n, ld, d.device)
     code = _dtype_code(d)
     ip, _keep = _inf_arg(inf, code)
