@@ -44,6 +44,8 @@ WORKLOADS = {
     "apsp_fw_n4096": dict(n=4096, p=0.5, dtype="int32", dist="uniform", lo=1, hi=1000, algo="fw"),
     "apsp_fw_n8192": dict(n=8192, p=0.05, dtype="int32", dist="uniform", lo=1, hi=100, algo="fw"),
     "batched_2048": dict(n=None, count=2048, dtype="int32", dist="uniform", lo=1, hi=100, algo="batched"),
+    "serve_poisson": dict(n=None, rate=200.0, library=128, n_lo=64, n_hi=8192, dtype="mixed", dist="mixed", lo=1,
+                          hi=100, algo="serve"),
 }
 SMS_NOMINAL = 152
 LANES_PER_SM = 128
@@ -75,6 +77,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="length of the Poisson request stream")
     return ap.parse_args()
 
 
@@ -220,6 +223,13 @@ def run_reference(args, w, rank, world):
 
 
 def config_of(args, w, world):
+    if w["algo"] == "serve":
+        return {"workload": args.workload, "arrivals": f"Poisson {w['rate']:.0f}/s for {args.serve_seconds:.0f} s",
+                "n": f"log-uniform [{w['n_lo']}, {w['n_hi']}]", "edge_p": "uniform [0.01, 0.5]",
+                "weights": "even requests int32 uniform[1,100], odd float32 lognormal(0,1)",
+                "graphs": f"library of {w['library']} seeded graphs, request k carries graph k mod {w['library']}",
+                "admission": "HBM arena 16 GiB, first fit", "batching": "n <= 1024 continuously batched",
+                "parallelism": f"replicas{world}"}
     if w["algo"] == "batched":
         return {"workload": args.workload, "graphs": w["count"], "n": "log-uniform [32, 1024]",
                 "edge_p": "uniform [0.02, 0.8]", "weights": "int32 uniform[1,100]", "algo": "batched persistent FW",
@@ -544,6 +554,80 @@ def run_batched(args, w, rank, world, local_rank):
     return 0
 
 
+def run_reference_serve(args, w, rank, world):
+    """CPU oracle serving a bounded sample of the request library one by one: the p99 of its
+    per-request service time (a lower bound on its latency; no queueing)."""
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    cores = cores_available() if oracle.openmp_enabled() else 1
+    ns, ps, lib = workloads.request_library(w["library"], w["n_lo"], w["n_hi"], seed=0)
+    order = np.argsort(ns)  # a bounded sample: the smaller half of the library, cycled
+    times = []
+    t_start = time.perf_counter()
+    k = 0
+    while time.perf_counter() - t_start < args.cpu_seconds:
+        g = int(order[k % (len(order) // 2)])
+        t0 = time.perf_counter()
+        oracle.fw(lib[g], threads=cores)
+        times.append((time.perf_counter() - t0) * 1e3)
+        k += 1
+    p99 = float(np.percentile(times, 99))
+    gs = len(times) / sum(t / 1e3 for t in times)
+    line = {"impl": "reference", "metric": "serve p99 ms", "value": round(p99, 3), "unit": "ms", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(p99, 3), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "i64/f64", "data": "synthetic",
+            "config": config_of(args, w, world), "graphs_per_s": round(gs, 3),
+            "cpu_baseline": {"value": round(p99, 3), "unit": "ms", "cores": cores, "kind": "oracle",
+                             "sample": f"{len(times)} requests from the smaller half of the library, service time only"},
+            "e2e": {"value": round(p99, 3), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args, w, rank, world, local_rank):
+    """Poisson stream through the continuous-batching server vs a one-at-a-time plain loop."""
+    import torch
+    import torch.distributed as dist
+    import paper_2310_03983_gb300 as apsp
+    from paper_2310_03983_gb300 import serve
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    ns, ps, lib = workloads.request_library(w["library"], w["n_lo"], w["n_hi"], seed=0)
+    t_arr, _, _, _ = workloads.poisson_requests(w["rate"], args.serve_seconds, seed=0)
+    # warm-up: every distinct size once through both paths (first-launch set-up)
+    srv = serve.Server(device=dev, arena_bytes=16 << 30, small_max=1024, slots=4)
+    srv.serve(serve.make_requests(np.linspace(0, 0.01, len(lib)), lib))
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    reqs = serve.make_requests(t_arr, lib)
+    st = srv.serve(reqs)
+    clocks = sampler.stop()
+    base = serve.serve_one_at_a_time(serve.make_requests(t_arr, lib), device=dev)
+    ok = apsp.apsp_device_status() == 0
+    bytes_in = int(sum(r.n * r.n * 4 for r in reqs))
+    line = {
+        "metric": "serve p99 ms", "value": round(st["p99"], 3), "unit": "ms", "n_gpus": world, "steps": 1,
+        "warmup": 1, "ms_per_step": round(st["wall_s"] * 1e3, 1), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "i32/f32", "data": "synthetic", "config": config_of(args, w, world),
+        "p50_ms": round(st["p50"], 3), "graphs_per_s": round(st["graphs_per_s"], 2), "requests": st["requests"],
+        "launches": st["launches"], "arena_peak_bytes": st["arena_peak_bytes"],
+        "one_at_a_time": {"p50_ms": round(base["p50"], 3), "p99_ms": round(base["p99"], 3),
+                          "graphs_per_s": round(base["graphs_per_s"], 2)},
+        "clocks": clocks,
+        "e2e": {"value": round(st["p99"], 3), "unit": "ms", "h2d_bytes_per_step": bytes_in,
+                "d2h_bytes_per_step": bytes_in},
+        "gpu_launches": st["launches"]["batch"] + st["launches"]["solo"], "status_ok": ok,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     w = WORKLOADS[args.workload]
@@ -551,13 +635,14 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
-        return (run_reference_batched if w["algo"] == "batched" else run_reference)(args, w, rank, world)
+        return {"batched": run_reference_batched, "serve": run_reference_serve}.get(w["algo"], run_reference)(
+            args, w, rank, world)
     if world > 1:
         import torch
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    rc = (run_batched if w["algo"] == "batched" else run_ours)(args, w, rank, world, local_rank)
+    rc = {"batched": run_batched, "serve": run_serve}.get(w["algo"], run_ours)(args, w, rank, world, local_rank)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -279,6 +279,16 @@ def apsp_close_cta(d: torch.Tensor, inf=None, stream=None):
     return d
 
 
+def apsp_batched_raw(pool, d_offsets, d_ns, d_lds, d_order, count: int, ws, inf=None, stream=None):
+    """apsp_batched on caller-built device descriptor arrays (int64 offsets, int32 ns, lds and
+    order) over `pool` (a 1-D int32 or float32 CUDA tensor)."""
+    code = _dtype_code(pool)
+    ip, _keep = _inf_arg(inf, code)
+    _check(_lib.apsp_batched(pool.data_ptr(), d_offsets.data_ptr(), d_ns.data_ptr(), d_lds.data_ptr(),
+                             None if d_order is None else d_order.data_ptr(), count, code, ip, ws.data_ptr(),
+                             ws.numel() * ws.element_size(), _stream(stream)), "apsp_batched")
+
+
 def apsp_batched(batch: Batch, inf=None, stream=None, pool=None):
     """Close every graph of `batch` (its device pool, or `pool`) in one persistent launch."""
     code = _dtype_code(batch.pool)

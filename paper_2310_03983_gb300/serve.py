@@ -1,0 +1,336 @@
+"""a9: serving APSP requests with continuous batching on one GPU.
+
+Requests (a cost matrix each, int32 or float32) arrive over time.  The server
+* admits them by HBM footprint: every admitted matrix lives in one device arena whose size is
+  the admission budget, placed by a first-fit allocator; a request that does not fit waits
+  (requests behind a blocked large one may still be admitted if they fit -- small requests
+  are not held up by a large head);
+* keeps admitted matrices on the device from the host-to-device copy until the closed result
+  has been copied back;
+* batches continuously: whenever a launch slot frees up, all admitted small requests of one
+  dtype (n <= small_max) are closed together by one apsp_batched launch over the arena, and
+  a large request is closed alone with the plan the planner picks for it.  Requests that
+  arrive while others are on the GPU join the next launch; launches run concurrently on
+  several CUDA streams, with copies overlapping the closures;
+* records, per request, the time from arrival to its result being back on the host, and
+  reports p50/p99 latency and graphs/s.
+
+Results do not depend on the mix: a request's plan depends only on its own size, density and
+dtype, and the batched kernel closes each graph exactly as apsp_fw does.
+
+The scheduling policy (Arena, Scheduler) is plain Python and is tested without a GPU.
+"""
+from __future__ import annotations
+
+import bisect
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+ALIGN = 64  # elements (256 bytes): every arena offset keeps rows 16-byte aligned
+
+
+class Arena:
+    """First-fit allocator over [0, capacity) elements with coalescing free lists."""
+
+    def __init__(self, capacity: int, align: int = ALIGN):
+        self.capacity = int(capacity)
+        self.align = align
+        self.free_list = [(0, self.capacity)]  # sorted (offset, size)
+        self.live = {}
+        self.used = 0
+        self.peak = 0
+
+    def alloc(self, size: int):
+        size = -(-int(size) // self.align) * self.align
+        if size <= 0:
+            size = self.align
+        for i, (off, sz) in enumerate(self.free_list):
+            if sz >= size:
+                if sz == size:
+                    self.free_list.pop(i)
+                else:
+                    self.free_list[i] = (off + size, sz - size)
+                self.live[off] = size
+                self.used += size
+                self.peak = max(self.peak, self.used)
+                return off
+        return None
+
+    def free(self, off: int):
+        size = self.live.pop(off)
+        self.used -= size
+        i = bisect.bisect_left(self.free_list, (off, 0))
+        self.free_list.insert(i, (off, size))
+        # coalesce with the right, then the left neighbour
+        if i + 1 < len(self.free_list) and off + size == self.free_list[i + 1][0]:
+            self.free_list[i] = (off, size + self.free_list[i + 1][1])
+            self.free_list.pop(i + 1)
+        if i > 0 and self.free_list[i - 1][0] + self.free_list[i - 1][1] == off:
+            self.free_list[i - 1] = (self.free_list[i - 1][0], self.free_list[i - 1][1] + self.free_list[i][1])
+            self.free_list.pop(i)
+
+
+@dataclass
+class Request:
+    rid: int
+    n: int
+    dtype: str               # "int32" or "float32"
+    arrival: float           # seconds after the start of the stream
+    host: object = None      # pinned host tensor holding the cost matrix
+    density: float = 0.0
+    off: int = -1            # arena offset once admitted
+    ld: int = 0
+    plan: tuple = ("batched", 0)
+    t_admit: float = -1.0
+    t_done: float = -1.0
+    result: object = None
+
+    @property
+    def footprint(self) -> int:
+        return self.n * self.ld
+
+
+class Scheduler:
+    """Admission and launch grouping, independent of the GPU."""
+
+    def __init__(self, arena: Arena, small_max: int = 1024, max_batch: int = 4096):
+        self.arena = arena
+        self.small_max = small_max
+        self.max_batch = max_batch
+        self.waiting = collections.deque()
+        self.ready_small = {"int32": [], "float32": []}
+        self.ready_large = collections.deque()
+
+    def arrive(self, r: Request):
+        r.ld = -(-r.n // 4) * 4
+        self.waiting.append(r)
+
+    def admit(self, now: float) -> list:
+        """Admit waiting requests that fit, in arrival order; small ones may pass a large head
+        that does not fit.  Returns the newly admitted requests."""
+        out = []
+        blocked_large = False
+        keep = collections.deque()
+        while self.waiting:
+            r = self.waiting.popleft()
+            if blocked_large and r.n > self.small_max:
+                keep.append(r)
+                continue
+            off = self.arena.alloc(r.footprint)
+            if off is None:
+                keep.append(r)
+                if r.n > self.small_max:
+                    blocked_large = True
+                continue
+            r.off, r.t_admit = off, now
+            out.append(r)
+            if r.n <= self.small_max:
+                self.ready_small[r.dtype].append(r)
+            else:
+                self.ready_large.append(r)
+        self.waiting = keep
+        return out
+
+    def next_launch(self):
+        """The next unit of work: ("batch", dtype, [requests]) or ("solo", request), or None.
+        Large requests go first (they take longest); small ones are gathered per dtype."""
+        if self.ready_large:
+            return ("solo", self.ready_large.popleft())
+        best = max(self.ready_small, key=lambda k: len(self.ready_small[k]))
+        if self.ready_small[best]:
+            group = self.ready_small[best][: self.max_batch]
+            self.ready_small[best] = self.ready_small[best][self.max_batch:]
+            return ("batch", best, group)
+        return None
+
+    def release(self, r: Request):
+        self.arena.free(r.off)
+        r.off = -1
+
+
+def make_requests(arrivals, library, density=None):
+    """Requests for arrival times `arrivals` (seconds): request k carries library graph
+    k mod len(library) (a list of numpy cost matrices), copied once to pinned host memory."""
+    import torch
+    pinned = [torch.from_numpy(m).pin_memory() for m in library]
+    dens = density or [0.0] * len(library)
+    out = []
+    for k, t in enumerate(arrivals):
+        g = k % len(library)
+        m = library[g]
+        out.append(Request(rid=k, n=m.shape[0], dtype="float32" if m.dtype == np.float32 else "int32",
+                           arrival=float(t), host=pinned[g], density=dens[g]))
+    return out
+
+
+def percentiles(lat_ms):
+    a = np.sort(np.asarray(lat_ms, dtype=np.float64))
+    if a.size == 0:
+        return {"p50": None, "p99": None}
+    return {"p50": float(np.percentile(a, 50)), "p99": float(np.percentile(a, 99)), "mean": float(a.mean()),
+            "max": float(a.max())}
+
+
+class Server:
+    """Continuous-batching APSP server on one GPU (see the module docstring)."""
+
+    def __init__(self, device=None, arena_bytes: int = 8 << 30, small_max: int = 1024, slots: int = 4,
+                 planner=None, keep_results: bool = False):
+        import torch
+        self.torch = torch
+        self.dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.arena_elems = arena_bytes // 4
+        self.pool = torch.empty(self.arena_elems, dtype=torch.int32, device=self.dev)
+        self.sched = Scheduler(Arena(self.arena_elems), small_max=small_max)
+        self.slots = slots
+        self.streams = [torch.cuda.Stream(self.dev) for _ in range(slots)]
+        self.copy_in = torch.cuda.Stream(self.dev)
+        self.planner = planner
+        self.keep_results = keep_results
+        self.ws = [torch.empty(256, dtype=torch.uint8, device=self.dev) for _ in range(slots)]
+        self._staging = {}
+
+    # -- helpers ---------------------------------------------------------------------------
+    def _view(self, r: Request):
+        t = self.pool[r.off:r.off + r.n * r.ld].view(r.n, r.ld)[:, :r.n]
+        return t.view(self.torch.float32) if r.dtype == "float32" else t
+
+    def _plan(self, r: Request):
+        if r.n <= self.sched.small_max:
+            return ("batched", 0)
+        if self.planner is not None:
+            return self.planner.choose(r.n, r.density, r.dtype)
+        return ("fw", 0)
+
+    def _result_buffer(self, r: Request):
+        torch = self.torch
+        dt = torch.float32 if r.dtype == "float32" else torch.int32
+        if self.keep_results:
+            return torch.empty((r.n, r.n), dtype=dt).pin_memory()
+        key = (r.n, r.dtype)
+        if key not in self._staging:
+            self._staging[key] = torch.empty((r.n, r.n), dtype=dt).pin_memory()
+        return self._staging[key]
+
+    def _launch(self, work, stream, ws):
+        from . import apsp_batched_raw, apsp_fw, apsp_rkleene
+        torch = self.torch
+        with torch.cuda.stream(stream):
+            stream.wait_stream(self.copy_in)
+            if work[0] == "batch":
+                group = work[2]
+                offs = np.array([r.off for r in group], np.int64)
+                ns = np.array([r.n for r in group], np.int32)
+                lds = np.array([r.ld for r in group], np.int32)
+                order = np.argsort(-ns, kind="stable").astype(np.int32)
+                meta = torch.from_numpy(np.concatenate([offs.view(np.int32), ns, lds, order])).pin_memory()
+                dmeta = meta.to(self.dev, non_blocking=True)
+                k = len(group)
+                d_off = dmeta[:2 * k].view(torch.int64)
+                apsp_batched_raw(self.pool if work[1] == "int32" else self.pool.view(torch.float32), d_off,
+                                 dmeta[2 * k:3 * k], dmeta[3 * k:4 * k], dmeta[4 * k:5 * k], k, ws)
+                reqs = group
+                keep = (meta, dmeta)
+            else:
+                r = work[1]
+                algo, param = r.plan
+                v = self._view(r)
+                if algo == "rkleene":
+                    apsp_rkleene(v, cutoff=param)
+                elif algo == "cta":
+                    from . import apsp_close_cta
+                    apsp_close_cta(v)
+                else:
+                    apsp_fw(v)
+                reqs = [r]
+                keep = None
+            for r in reqs:
+                r.result = self._result_buffer(r)
+                r.result.copy_(self._view(r), non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        return ev, reqs, keep
+
+    # -- the loop ----------------------------------------------------------------------------
+    def serve(self, requests: list, time_scale: float = 1.0) -> dict:
+        """Serve requests at their arrival times (arrival * time_scale seconds after start)."""
+        torch = self.torch
+        reqs = sorted(requests, key=lambda r: r.arrival)
+        for r in reqs:
+            r.plan = self._plan(r)
+            if r.n * (-(-r.n // 4) * 4) > self.sched.arena.capacity:
+                raise ValueError(f"request {r.rid} (n={r.n}) can never fit the {self.arena_elems * 4} B arena")
+        total = len(reqs)
+        t0 = time.perf_counter()
+        nxt, done = 0, 0
+        inflight = []  # (event, reqs, keepalive, slot)
+        free_slots = list(range(self.slots))
+        launches = {"batch": 0, "solo": 0}
+        while done < total:
+            now = time.perf_counter() - t0
+            while nxt < total and reqs[nxt].arrival * time_scale <= now:
+                self.sched.arrive(reqs[nxt])
+                nxt += 1
+            for r in self.sched.admit(now):
+                with torch.cuda.stream(self.copy_in):
+                    self._view(r).copy_(r.host, non_blocking=True)
+            progressed = False
+            while free_slots:
+                work = self.sched.next_launch()
+                if work is None:
+                    break
+                slot = free_slots.pop()
+                ev, rs, keep = self._launch(work, self.streams[slot], self.ws[slot])
+                inflight.append((ev, rs, keep, slot))
+                launches[work[0]] += 1
+                progressed = True
+            still = []
+            for ev, rs, keep, slot in inflight:
+                if ev.query():
+                    t = time.perf_counter() - t0
+                    for r in rs:
+                        r.t_done = t
+                        self.sched.release(r)
+                        done += 1
+                    free_slots.append(slot)
+                    progressed = True
+                else:
+                    still.append((ev, rs, keep, slot))
+            inflight = still
+            if not progressed:
+                time.sleep(50e-6)
+        wall = time.perf_counter() - t0
+        lat = [(r.t_done - r.arrival * time_scale) * 1e3 for r in reqs]
+        st = percentiles(lat)
+        st.update({"requests": total, "wall_s": wall, "graphs_per_s": total / wall, "launches": launches,
+                   "arena_peak_bytes": self.sched.arena.peak * 4, "arena_bytes": self.arena_elems * 4})
+        return st
+
+
+def serve_one_at_a_time(requests: list, device=None, time_scale: float = 1.0, planner=None) -> dict:
+    """Baseline: each request in arrival order is copied in, closed alone (apsp_fw) and copied
+    back before the next one starts."""
+    import torch
+    from . import apsp_fw
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    reqs = sorted(requests, key=lambda r: r.arrival)
+    staging = {}
+    t0 = time.perf_counter()
+    for r in reqs:
+        while time.perf_counter() - t0 < r.arrival * time_scale:
+            time.sleep(50e-6)
+        d = r.host.to(dev, non_blocking=True)
+        apsp_fw(d)
+        key = (r.n, r.dtype)
+        if key not in staging:
+            staging[key] = torch.empty_like(r.host).pin_memory()
+        staging[key].copy_(d, non_blocking=True)
+        torch.cuda.current_stream(dev).synchronize()
+        r.t_done = time.perf_counter() - t0
+    wall = time.perf_counter() - t0
+    st = percentiles([(r.t_done - r.arrival * time_scale) * 1e3 for r in reqs])
+    st.update({"requests": len(reqs), "wall_s": wall, "graphs_per_s": len(reqs) / wall})
+    return st

@@ -111,6 +111,26 @@ def batch_graphs(ns, ps, dtype="int32", lo=1, hi=100, inf: int = INF_I32):
             for g, (n, p) in enumerate(zip(ns, ps))]
 
 
+def request_library(count: int = 128, n_lo: int = 64, n_hi: int = 8192, p_lo: float = 0.01, p_hi: float = 0.5,
+                    seed: int = 0, threads: int | None = None):
+    """Graphs for a request stream: entry i has n log-uniform in [n_lo, n_hi], p uniform in
+    [p_lo, p_hi]; even entries int32 weights in [1, 100], odd entries float32 lognormal(0, 1).
+    Request k of a stream carries entry k mod count (count even keeps the dtype alternation)."""
+    rng = np.random.Generator(np.random.PCG64([int(seed), 0x4C494252]))
+    ns = np.rint(np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), size=count))).astype(np.int64)
+    ps = rng.uniform(p_lo, p_hi, size=count)
+
+    def make(i):
+        if i % 2 == 0:
+            return er_graph(int(ns[i]), float(ps[i]), "int32", lo=1, hi=100, seed=5000 + i, threads=1)
+        return er_graph(int(ns[i]), float(ps[i]), "float32", dist="lognormal", lo=0.0, hi=1.0, seed=5000 + i,
+                        threads=1)
+
+    with ThreadPoolExecutor(threads or min(16, os.cpu_count() or 1)) as ex:
+        mats = list(ex.map(make, range(count)))
+    return ns, ps, mats
+
+
 def poisson_requests(rate: float = 200.0, duration: float = 60.0, n_lo: int = 64, n_hi: int = 8192,
                      p_lo: float = 0.01, p_hi: float = 0.5, seed: int = 0):
     """Arrival times (s), sizes, densities and dtypes of a Poisson request stream.
