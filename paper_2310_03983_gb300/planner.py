@@ -197,6 +197,31 @@ class CostModel:
 
 
 DEFAULT_MODEL = os.path.join(os.path.dirname(os.path.abspath(__file__)), "cost_model.json")
+DEFAULT_LOG = os.path.join(os.path.dirname(os.path.abspath(__file__)), "timings_gb300.jsonl")
+
+
+def sweep_graphs(seed: int = 0):
+    """The autotuning sweep: sizes 32..8192 (log-spaced), both dtypes, sparse and dense."""
+    import workloads
+    sizes = sorted({int(round(2 ** e)) for e in np.arange(5.0, 13.01, 0.5)})
+    for i, n in enumerate(sizes):
+        for dt in ("int32", "float32"):
+            for p in (0.02, 0.4):
+                kw = {"lo": 1, "hi": 100} if dt == "int32" else {"dist": "lognormal", "lo": 0.0, "hi": 1.0}
+                yield workloads.er_graph(n, p, dt, seed=seed * 100000 + 10 * n + (p > 0.1), **kw)
+
+
+def main(log_path: str = DEFAULT_LOG, model_path: str = DEFAULT_MODEL, reps: int = 5):
+    """Record a timing log on this GPU with the exhaustive autotuner and fit the cost model."""
+    if os.path.exists(log_path):
+        os.remove(log_path)
+    tuner = Autotuner(log_path=log_path, reps=reps)
+    for h in sweep_graphs():
+        tuner.measure(h, tag="sweep")
+    model = CostModel(seed=0)
+    hist = model.fit(load_rows(log_path), epochs=4000)
+    model.save(model_path)
+    return hist
 
 
 def default_plan(n: int, density: float, dtype: str) -> tuple[str, int]:
