@@ -222,6 +222,21 @@ def run_reference(args, w, rank, world):
     return 0
 
 
+def aggregate(ms_local: float, work_local: float, device=None):
+    """Whole-job throughput across ranks: the time is the max over ranks (the job ends when the
+    slowest rank does), the work is summed.  Works with any torch.distributed backend; with no
+    process group it is the local figure.  Returns (ms_max, work_total)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return ms_local, work_local
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    w = torch.tensor([work_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(w.item())
+
+
 def config_of(args, w, world):
     if w["algo"] == "serve":
         return {"workload": args.workload, "arrivals": f"Poisson {w['rate']:.0f}/s for {args.serve_seconds:.0f} s",
@@ -324,12 +339,9 @@ def run_ours(args, w, rank, world, local_rank):
     k_ms, k_launches, k_pairs = apsp.apsp_trace_read(dom_mode)
     all_ms, all_launches, _ = apsp.apsp_trace_read(-1) if False else (None, None, None)
 
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
     ops_step = 2.0 * n ** 3
-    value = world * args.steps * ops_step / (ms_max * 1e-3) / 1e9
+    ms_max, ops_total = aggregate(ms, args.steps * ops_step, dev)
+    value = ops_total / (ms_max * 1e-3) / 1e9
 
     # End to end through the public API: pinned host matrix in, distances back to pinned host.
     e2e_val = None
@@ -478,11 +490,8 @@ def run_batched(args, w, rank, world, local_rank):
         dist.barrier()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * args.steps * len(batch) / (ms_max * 1e-3)
+    ms_max, graphs_total = aggregate(ms, args.steps * len(batch), dev)
+    value = graphs_total / (ms_max * 1e-3)
 
     # Dominant kernel alone (no restore copy), for the roofline.
     work.copy_(pristine)

@@ -227,3 +227,8 @@ def main(log_path: str = DEFAULT_LOG, model_path: str = DEFAULT_MODEL, reps: int
 def default_plan(n: int, density: float, dtype: str) -> tuple[str, int]:
     """The plan without a model: blocked Floyd-Warshall."""
     return ("fw", 0)
+
+
+def paper_rule(n: int) -> tuple[str, int]:
+    """The paper's guidance (Sec. 4): R-Kleene for graphs above 1000 vertices, FW below."""
+    return ("rkleene", 256) if n > 1000 else ("fw", 0)
