@@ -26,7 +26,7 @@ constexpr int kBThreads = 256;
 constexpr int kBStages = 3;
 constexpr int kBSlabInts = kSlabM * kSlabK;  // 4096 ints per A or B slab
 constexpr int kBTileInts = kSlabM * kSlabN;  // 16384 ints per 128 x 128 tile
-constexpr int kBSmemBytes = (2 * kBStages * kBSlabInts + kBTileInts + 2 * kBSlabInts) * 4 + 256;
+constexpr int kBSmemBytes = (2 * kBStages * kBSlabInts + kBTileInts) * 4 + 256;
 
 struct BatchArgs {
   int *pool;
@@ -116,7 +116,7 @@ __device__ void close_diag(int *D, int n, int ld, int kb0, int *buf) {
 // ragged last k-slab is bounded by kc.
 template <typename AR, bool ACC>
 __device__ void tile_product(int *D, int n, int ld, int ar, int ac, int br, int bc, int cr, int cc, int K, int *sA,
-                             int *sB, int *sC, int *sBT, int init_bits) {
+                             int *sB, int *sC, int init_bits) {
   typedef typename AR::T T;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tm = (warp & 3) * 4 + (lane >> 3), tn = (warp >> 2) * 8 + (lane & 7);
@@ -168,15 +168,8 @@ __device__ void tile_product(int *D, int n, int ld, int ar, int ac, int br, int 
     cp_async_commit();
     const int st = kt % kBStages;
     const int kc = K - kt * kSlabK;
-    if (AR::kTransposeB && kc >= kSlabK) {
-      int *bt = sBT + (kt & 1) * kBSlabInts;
-      AR::transpose_b(sB + st * kBSlabInts, bt);
-      AR::slab_full_bt(sA + st * kBSlabInts, bt, tm, tn, acc);
-    } else if (kc >= kSlabK) {
-      AR::slab_full(sA + st * kBSlabInts, sB + st * kBSlabInts, tm, tn, acc);
-    } else {
-      AR::slab_part(sA + st * kBSlabInts, sB + st * kBSlabInts, tm, tn, kc, acc);
-    }
+    if (kc >= kSlabK) AR::slab_full(sA + st * kBSlabInts, sB + st * kBSlabInts, tm, tn, acc);
+    else AR::slab_part(sA + st * kBSlabInts, sB + st * kBSlabInts, tm, tn, kc, acc);
   }
   cp_async_wait<0>();
   __syncthreads();
@@ -210,7 +203,7 @@ __device__ void tile_product(int *D, int n, int ld, int ar, int ac, int br, int 
 
 // Blocked Floyd-Warshall of one normalised graph by the whole CTA.
 template <typename AR, typename S>
-__device__ void close_blocked(int *D, int n, int ld, int init_bits, int *sA, int *sB, int *sT, int *sBT) {
+__device__ void close_blocked(int *D, int n, int ld, int init_bits, int *sA, int *sB, int *sT) {
   const int nb = (n + kSlabM - 1) / kSlabM;
   for (int kb = 0; kb < nb; ++kb) {
     const int kb0 = kb * kSlabM, bk = min(kSlabM, n - kb0);
@@ -221,11 +214,11 @@ __device__ void close_blocked(int *D, int n, int ld, int init_bits, int *sA, int
     for (int t = 0; t < 2 * (nb - 1); ++t) {
       if (t < nb - 1) {
         const int j = (t + (t >= kb)) * kSlabN;
-        tile_product<AR, false>(D, n, ld, kb0, kb0, kb0, j, kb0, j, bk, sA, sB, sT, sBT, init_bits);
+        tile_product<AR, false>(D, n, ld, kb0, kb0, kb0, j, kb0, j, bk, sA, sB, sT, init_bits);
       } else {
         int i = t - (nb - 1);
         i = (i + (i >= kb)) * kSlabM;
-        tile_product<AR, false>(D, n, ld, i, kb0, kb0, kb0, i, kb0, bk, sA, sB, sT, sBT, init_bits);
+        tile_product<AR, false>(D, n, ld, i, kb0, kb0, kb0, i, kb0, bk, sA, sB, sT, init_bits);
       }
     }
     __threadfence();
@@ -234,7 +227,7 @@ __device__ void close_blocked(int *D, int n, int ld, int init_bits, int *sA, int
       int i = t / (nb - 1), j = t - i * (nb - 1);
       i = (i + (i >= kb)) * kSlabM;
       j = (j + (j >= kb)) * kSlabN;
-      tile_product<AR, true>(D, n, ld, i, kb0, kb0, j, i, j, bk, sA, sB, sT, sBT, init_bits);
+      tile_product<AR, true>(D, n, ld, i, kb0, kb0, j, i, j, bk, sA, sB, sT, init_bits);
     }
     __threadfence();
     __syncthreads();
@@ -248,7 +241,6 @@ __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(const BatchArgs a
   int *sA = reinterpret_cast<int *>(smem);
   int *sB = sA + kBStages * kBSlabInts;
   int *sT = sB + kBStages * kBSlabInts;  // phase-1 scratch and phase-3 C tile
-  int *sBT = sT + kBTileInts;            // two transposed B slabs
   __shared__ int s_idx;
   __shared__ int red[kBThreads / 32];
   for (;;) {
@@ -274,11 +266,11 @@ __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(const BatchArgs a
     __threadfence();
     __syncthreads();
     if (Store<S>::is_float) {
-      close_blocked<ArithF32, S>(D, n, ld, 0x7f800000, sA, sB, sT, sBT);
+      close_blocked<ArithF32, S>(D, n, ld, 0x7f800000, sA, sB, sT);
     } else if (small_int_bound(wmax, n - 1, 0)) {
-      close_blocked<ArithF32, S>(D, n, ld, a.inf_i, sA, sB, sT, sBT);
+      close_blocked<ArithF32, S>(D, n, ld, a.inf_i, sA, sB, sT);
     } else {
-      close_blocked<ArithI32, S>(D, n, ld, a.inf_i, sA, sB, sT, sBT);
+      close_blocked<ArithI32, S>(D, n, ld, a.inf_i, sA, sB, sT);
     }
     __threadfence();
     __syncthreads();

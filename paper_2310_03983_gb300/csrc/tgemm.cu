@@ -87,7 +87,6 @@ __device__ __forceinline__ TileCoords tile_coords(const TileProblem &p, int64_t 
 
 struct Smem {
   const int *sA, *sB, *sC;
-  int *sBT;
   uint64_t *full, *empty, *cfull, *cempty;
 };
 
@@ -101,10 +100,6 @@ __device__ __forceinline__ void consume(const TileProblem &p, const Smem &sm, in
   int *C = reinterpret_cast<int *>(p.C);
   int stage = 0;
   uint32_t phase = 0, cphase = 0;
-  // Transposed-slab buffers alternate over a count that runs across tiles: a warp writes a
-  // buffer only after the barrier of the previous slab, which every warp reaches after it has
-  // finished reading that buffer two slabs earlier.
-  uint32_t bt_ctr = 0;
   const T init = AR::from(init_bits);
   for (int64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
     const TileCoords tc = tile_coords<MODE>(p, t);
@@ -119,15 +114,8 @@ __device__ __forceinline__ void consume(const TileProblem &p, const Smem &sm, in
       const int *As = sm.sA + stage * (kBM * kBK);
       const int *Bs = sm.sB + stage * (kBK * kBN);
       const int kc = tc.k_len - kt * kBK;
-      if (AR::kTransposeB && kc >= kBK) {
-        int *bt = sm.sBT + (bt_ctr++ & 1) * (kBK * kBN);
-        AR::transpose_b(Bs, bt);
-        AR::slab_full_bt(As, bt, tm, tn, acc);
-      } else if (kc >= kBK) {
-        AR::slab_full(As, Bs, tm, tn, acc);
-      } else {
-        AR::slab_part(As, Bs, tm, tn, kc, acc);
-      }
+      if (kc >= kBK) AR::slab_full(As, Bs, tm, tn, acc);
+      else AR::slab_part(As, Bs, tm, tn, kc, acc);
       __syncwarp();
       if (lane == 0) mbar_arrive(&sm.empty[stage]);
       if (++stage == kStages) { stage = 0; phase ^= 1; }
@@ -180,8 +168,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   int *sA = reinterpret_cast<int *>(smem);
   int *sB = reinterpret_cast<int *>(smem + kStages * kAStageBytes);
   int *sC = reinterpret_cast<int *>(smem + kStages * (kAStageBytes + kBStageBytes));
-  int *sBT = reinterpret_cast<int *>(smem + kStages * (kAStageBytes + kBStageBytes) + kCBytes);
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * (kAStageBytes + kBStageBytes) + kCBytes + kBTBytes);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * (kAStageBytes + kBStageBytes) + kCBytes);
   uint64_t *full = bars, *empty = bars + kStages, *cfull = bars + 2 * kStages, *cempty = cfull + 1;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -237,7 +224,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 
   asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kConsumerRegs));
-  const Smem sm = {sA, sB, sC, sBT, full, empty, cfull, cempty};
+  const Smem sm = {sA, sB, sC, full, empty, cfull, cempty};
   if (sizeof(S) == 4 && S(0.5) != S(0)) {  // float storage
     consume<ArithF32, MODE, ACC>(p, sm, warp, lane, 0x7f800000);
   } else if (p.wmax && small_int_bound(p.wmax[0], p.wmult, p.wmax[1])) {

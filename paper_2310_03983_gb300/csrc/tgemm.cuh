@@ -18,8 +18,7 @@ static_assert(128 * kProducerRegs + 256 * kConsumerRegs <= kThreads * kLaunchReg
 constexpr int kAStageBytes = kBM * kBK * 4;         // A tile [128 m][32 k]
 constexpr int kBStageBytes = kBK * kBN * 4;         // B tile [32 k][128 n]
 constexpr int kCBytes = kBM * kBN * 4;              // C tile [128 m][128 n]
-constexpr int kBTBytes = 2 * kBK * kBN * 4;            // two transposed B slabs (fp32 k-pair form)
-constexpr int kSmemBytes = kStages * (kAStageBytes + kBStageBytes) + kCBytes + kBTBytes + 256;
+constexpr int kSmemBytes = kStages * (kAStageBytes + kBStageBytes) + kCBytes + 256;
 
 // Which tiles a launch visits and where their operands live.
 enum TileMode : int {
