@@ -96,10 +96,13 @@ class Request:
 class Scheduler:
     """Admission and launch grouping, independent of the GPU."""
 
-    def __init__(self, arena: Arena, small_max: int = 1024, max_batch: int = 4096):
+    def __init__(self, arena: Arena, small_max: int = 1024, max_batch: int = 4096, big_n: int = 2048,
+                 big_slots: int = 1):
         self.arena = arena
         self.small_max = small_max
         self.max_batch = max_batch
+        self.big_n = big_n          # solo closures this large use the whole GPU ...
+        self.big_slots = big_slots  # ... so at most this many run at once (the rest wait in order)
         self.waiting = collections.deque()
         self.ready_small = {"int32": [], "float32": []}
         self.ready_large = collections.deque()
@@ -134,11 +137,17 @@ class Scheduler:
         self.waiting = keep
         return out
 
-    def next_launch(self):
+    def next_launch(self, big_inflight: int = 0):
         """The next unit of work: ("batch", dtype, [requests]) or ("solo", request), or None.
-        Large requests go first (they take longest); small ones are gathered per dtype."""
-        if self.ready_large:
-            return ("solo", self.ready_large.popleft())
+        Large requests go first (they take longest), in arrival order, except that a very large
+        one (n >= big_n) waits while big_slots of them are already running -- two such closures
+        sharing the GPU would both finish late -- and smaller work flows around it.  Small
+        requests are gathered per dtype."""
+        for idx, r in enumerate(self.ready_large):
+            if r.n >= self.big_n and big_inflight >= self.big_slots:
+                continue
+            del self.ready_large[idx]
+            return ("solo", r)
         best = max(self.ready_small, key=lambda k: len(self.ready_small[k]))
         if self.ready_small[best]:
             group = self.ready_small[best][: self.max_batch]
@@ -268,6 +277,7 @@ class Server:
         nxt, done = 0, 0
         inflight = []  # (event, reqs, keepalive, slot)
         free_slots = list(range(self.slots))
+        big = self.sched.big_n
         launches = {"batch": 0, "solo": 0}
         while done < total:
             now = time.perf_counter() - t0
@@ -279,7 +289,9 @@ class Server:
                     self._view(r).copy_(r.host, non_blocking=True)
             progressed = False
             while free_slots:
-                work = self.sched.next_launch()
+                big_inflight = sum(1 for _, rs, _, _ in inflight if len(rs) == 1 and rs[0].n >= big
+                                   and rs[0].plan[0] != "batched")
+                work = self.sched.next_launch(big_inflight)
                 if work is None:
                     break
                 slot = free_slots.pop()

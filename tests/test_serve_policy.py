@@ -73,6 +73,22 @@ def test_launch_grouping_by_dtype_and_large_first():
     assert s.arena.used == 0
 
 
+def test_very_large_requests_do_not_share_the_gpu():
+    s = Scheduler(Arena(1 << 30), small_max=100, big_n=2048, big_slots=1)
+    for i, n in enumerate([4096, 3000, 500, 50]):
+        s.arrive(_req(i, n))
+    s.admit(0.0)
+    w = s.next_launch(big_inflight=0)
+    assert w[0] == "solo" and w[1].n == 4096
+    w = s.next_launch(big_inflight=1)      # 3000 must wait: the mid-size one goes around it
+    assert w[0] == "solo" and w[1].n == 500
+    w = s.next_launch(big_inflight=1)
+    assert w[0] == "batch" and [r.n for r in w[2]] == [50]
+    assert s.next_launch(big_inflight=1) is None
+    w = s.next_launch(big_inflight=0)
+    assert w[0] == "solo" and w[1].n == 3000
+
+
 def test_percentiles():
     p = percentiles(list(range(1, 101)))
     assert abs(p["p50"] - 50.5) < 1e-9 and abs(p["p99"] - 99.01) < 1e-9
