@@ -12,8 +12,8 @@
 //     phase 2  row/column panel tiles = (min,+) products with the closed tile;
 //     phase 3  every other tile D[i][j] = min(D[i][j], D[i][kb] (x) D[kb][j]).
 // Phases 2-3 run the register-tiled slab arithmetic of the GEMM engine (slab.cuh), fed by a
-// three-stage cp.async pipeline (each graph has its own shape, so no per-graph TMA
-// descriptors are needed).  int32 graphs whose (n - 1) * largest finite weight < 2^24 use
+// four-stage cp.async pipeline that streams across tile boundaries (each graph has its own
+// shape, so no per-graph TMA descriptors are needed).  int32 graphs whose (n - 1) * largest finite weight < 2^24 use
 // the exact fp32 instruction sequence; others the int32 one.  One CTA per graph needs no
 // inter-CTA synchronisation: there is no spin-wait anywhere in this kernel.
 #include "diag.cuh"
@@ -23,10 +23,10 @@
 namespace apsp {
 
 constexpr int kBThreads = 256;
-constexpr int kBStages = 3;
+constexpr int kBStages = 4;
 constexpr int kBSlabInts = kSlabM * kSlabK;  // 4096 ints per A or B slab
 constexpr int kBTileInts = kSlabM * kSlabN;  // 16384 ints per 128 x 128 tile
-constexpr int kBSmemBytes = (2 * kBStages * kBSlabInts + kBTileInts) * 4 + 256;
+constexpr int kBSmemBytes = (2 * kBStages * kBSlabInts + kBTileInts + 512) * 4 + 256;
 
 struct BatchArgs {
   int *pool;
@@ -111,24 +111,61 @@ __device__ void close_diag(int *D, int n, int ld, int kb0, int *buf) {
   __syncthreads();
 }
 
-// One 128 x 128 output tile C(cr, cc) = [min(C,)] A(ar, ac .. +K) (x) B(br .. +K, bc), whole CTA.
-// Out-of-graph rows and columns are zero-filled in shared memory and never stored; the
-// ragged last k-slab is bounded by kc.
-template <typename AR, bool ACC>
-__device__ void tile_product(int *D, int n, int ld, int ar, int ac, int br, int bc, int cr, int cc, int K, int *sA,
-                             int *sB, int *sC, int init_bits) {
-  typedef typename AR::T T;
+// Operand origins of tile t of an FW phase (phase 2: row panel tiles then column panel
+// tiles; phase 3: every tile outside block row/column kb).  All tiles of a phase have K = bk.
+struct PhaseTile {
+  int ar, ac, br, bc, cr, cc;
+};
+__device__ __forceinline__ PhaseTile phase_tile(bool rest, int t, int nb, int kb) {
+  const int kb0 = kb * kSlabM;
+  PhaseTile p;
+  if (!rest) {
+    if (t < nb - 1) {  // row panel: D[kb][j] = D[kb][kb]* (x) D[kb][j]
+      const int j = (t + (t >= kb)) * kSlabN;
+      p = {kb0, kb0, kb0, j, kb0, j};
+    } else {           // column panel: D[i][kb] = D[i][kb] (x) D[kb][kb]*
+      int i = t - (nb - 1);
+      i = (i + (i >= kb)) * kSlabM;
+      p = {i, kb0, kb0, kb0, i, kb0};
+    }
+  } else {             // D[i][j] = min(D[i][j], D[i][kb] (x) D[kb][j])
+    int i = t / (nb - 1), j = t - i * (nb - 1);
+    i = (i + (i >= kb)) * kSlabM;
+    j = (j + (j >= kb)) * kSlabN;
+    p = {i, kb0, kb0, j, i, j};
+  }
+  return p;
+}
+
+// All tiles of one FW phase by the whole CTA, as one stream of 32-deep k-slabs: the cp.async
+// pipeline runs across tile boundaries, so the next tile's first slabs are already in flight
+// while a tile finishes.  Out-of-graph rows
+// and columns are zero-filled and never stored; the ragged last slab is bounded by kc.
+// For phase 3 a tile's old C block is copied into shared memory while its slabs are computed.
+// In-place safety: a phase-2 tile is both output and operand, but it is written only after
+// all its own slabs have been consumed, and no other tile of the phase reads it.
+// f32: the exact fp32 instruction sequence, else the int32 one; the accumulators are fp32
+// registers either way (for non-negative values, ordering their bits as int32 or as fp32 agrees,
+// so the final min with the old C is the same operation for both).
+template <bool ACC>
+__device__ void phase_tiles(int *D, int n, int ld, int kb, int nb, int ntiles, int *sA, int *sB, int *sC, bool f32,
+                            int init_bits) {
+  typedef ArithF32 AR;
+  typedef float T;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tm = (warp & 3) * 4 + (lane >> 3), tn = (warp >> 2) * 8 + (lane & 7);
-  const int m_valid = min(kSlabM, n - cr), n_valid = min(kSlabN, n - cc);
-  const int nk = (K + kSlabK - 1) / kSlabK;
-  auto load_slab = [&](int kt, int st) {
+  const int bk = min(kSlabM, n - kb * kSlabM);
+  const int nk = (bk + kSlabK - 1) / kSlabK;
+  const int total = ntiles * nk;
+  auto load_slab = [&](int g) {
+    const PhaseTile p = phase_tile(ACC, g / nk, nb, kb);
+    const int kt = g % nk, st = g % kBStages;
     int *As = sA + st * kBSlabInts, *Bs = sB + st * kBSlabInts;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int e = tid + kBThreads * u;
       const int r = e >> 3, kq = e & 7;
-      const int row = ar + r, col = ac + kt * kSlabK + 4 * kq;
+      const int row = p.ar + r, col = p.ac + kt * kSlabK + 4 * kq;
       const bool ok = row < n && col < n;
       cp_async16(As + a_off(r, kq), ok ? D + (int64_t)row * ld + col : D, ok);
     }
@@ -136,99 +173,99 @@ __device__ void tile_product(int *D, int n, int ld, int ar, int ac, int br, int 
     for (int u = 0; u < 4; ++u) {
       const int e = tid + kBThreads * u;
       const int r = e >> 5, c4 = e & 31;
-      const int row = br + kt * kSlabK + r, col = bc + 4 * c4;
+      const int row = p.br + kt * kSlabK + r, col = p.bc + 4 * c4;
       const bool ok = row < n && col < n;
       cp_async16(Bs + r * kSlabN + 4 * c4, ok ? D + (int64_t)row * ld + col : D, ok);
     }
   };
-  if (ACC) {
-#pragma unroll 4
-    for (int u = 0; u < 16; ++u) {
-      const int e = tid + kBThreads * u;
-      const int r = e >> 5, c4 = e & 31;
-      const bool ok = r < m_valid && 4 * c4 < n_valid;
-      cp_async16(sC + r * kSlabN + 4 * c4, ok ? D + (int64_t)(cr + r) * ld + cc + 4 * c4 : D, ok);
-    }
-  }
 #pragma unroll
   for (int s = 0; s < kBStages - 1; ++s) {
-    if (s < nk) load_slab(s, s);
+    if (s < total) load_slab(s);
     cp_async_commit();
   }
   T acc[8][8];
   const T init = AR::from(init_bits);
+  for (int g = 0; g < total; ++g) {
+    const int t = g / nk, kt = g - t * nk;
+    const PhaseTile p = phase_tile(ACC, t, nb, kb);
+    const int m_valid = min(kSlabM, n - p.cr), n_valid = min(kSlabN, n - p.cc);
+    if (kt == 0) {
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
+      for (int i = 0; i < 8; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = init;
-  for (int kt = 0; kt < nk; ++kt) {
+        for (int j = 0; j < 8; ++j) acc[i][j] = init;
+    }
     cp_async_wait<kBStages - 2>();
     __syncthreads();
-    if (kt + kBStages - 1 < nk) load_slab(kt + kBStages - 1, (kt + kBStages - 1) % kBStages);
-    cp_async_commit();
-    const int st = kt % kBStages;
-    const int kc = K - kt * kSlabK;
-    if (kc >= kSlabK) AR::slab_full(sA + st * kBSlabInts, sB + st * kBSlabInts, tm, tn, acc);
-    else AR::slab_part(sA + st * kBSlabInts, sB + st * kBSlabInts, tm, tn, kc, acc);
-  }
-  cp_async_wait<0>();
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int rl = tm + 16 * i;
-    if (rl >= m_valid) continue;
-    int *crow = D + (int64_t)(cr + rl) * ld + cc;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int cl = 4 * tn + 64 * h;
-      if (ACC) {
-        const int4 v = *reinterpret_cast<const int4 *>(sC + rl * kSlabN + cl);
-        acc[i][4 * h + 0] = AR::mn(acc[i][4 * h + 0], AR::from(v.x));
-        acc[i][4 * h + 1] = AR::mn(acc[i][4 * h + 1], AR::from(v.y));
-        acc[i][4 * h + 2] = AR::mn(acc[i][4 * h + 2], AR::from(v.z));
-        acc[i][4 * h + 3] = AR::mn(acc[i][4 * h + 3], AR::from(v.w));
+    if (ACC && kt == 0) {  // this tile's old C, in flight during its slabs
+#pragma unroll 4
+      for (int u = 0; u < 16; ++u) {
+        const int e = tid + kBThreads * u;
+        const int r = e >> 5, c4 = e & 31;
+        const bool ok = r < m_valid && 4 * c4 < n_valid;
+        cp_async16(sC + r * kSlabN + 4 * c4, ok ? D + (int64_t)(p.cr + r) * ld + p.cc + 4 * c4 : D, ok);
       }
-      if (cl + 3 < n_valid) {
-        *reinterpret_cast<int4 *>(crow + cl) = make_int4(AR::to(acc[i][4 * h]), AR::to(acc[i][4 * h + 1]),
-                                                         AR::to(acc[i][4 * h + 2]), AR::to(acc[i][4 * h + 3]));
-      } else {
+    }
+    if (g + kBStages - 1 < total) load_slab(g + kBStages - 1);
+    cp_async_commit();
+    const int st = g % kBStages;
+    const int kc = bk - kt * kSlabK;
+    const int *As = sA + st * kBSlabInts, *Bs = sB + st * kBSlabInts;
+    if (f32) {
+      if (kc >= kSlabK) ArithF32::slab_full(As, Bs, tm, tn, acc);
+      else ArithF32::slab_part(As, Bs, tm, tn, kc, acc);
+    } else {
+      if (kc >= kSlabK) ArithI32::slab_full(As, Bs, tm, tn, acc);
+      else ArithI32::slab_part(As, Bs, tm, tn, kc, acc);
+    }
+    if (kt != nk - 1) continue;
+    if (ACC) {  // the slabs issued since are a slab's compute old: waiting for them costs little
+      cp_async_wait<0>();
+      __syncthreads();
+    }
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (cl + q < n_valid) crow[cl + q] = AR::to(acc[i][4 * h + q]);
+    for (int i = 0; i < 8; ++i) {
+      const int rl = tm + 16 * i;
+      if (rl >= m_valid) continue;
+      int *crow = D + (int64_t)(p.cr + rl) * ld + p.cc;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int cl = 4 * tn + 64 * h;
+        if (ACC) {
+          const int4 v = *reinterpret_cast<const int4 *>(sC + rl * kSlabN + cl);
+          acc[i][4 * h + 0] = AR::mn(acc[i][4 * h + 0], AR::from(v.x));
+          acc[i][4 * h + 1] = AR::mn(acc[i][4 * h + 1], AR::from(v.y));
+          acc[i][4 * h + 2] = AR::mn(acc[i][4 * h + 2], AR::from(v.z));
+          acc[i][4 * h + 3] = AR::mn(acc[i][4 * h + 3], AR::from(v.w));
+        }
+        if (cl + 3 < n_valid) {
+          *reinterpret_cast<int4 *>(crow + cl) = make_int4(AR::to(acc[i][4 * h]), AR::to(acc[i][4 * h + 1]),
+                                                           AR::to(acc[i][4 * h + 2]), AR::to(acc[i][4 * h + 3]));
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (cl + q < n_valid) crow[cl + q] = AR::to(acc[i][4 * h + q]);
+        }
       }
     }
   }
-  __syncthreads();  // shared buffers are reused by the next tile
+  cp_async_wait<0>();
+  __syncthreads();  // shared buffers are reused by the next phase
 }
 
 // Blocked Floyd-Warshall of one normalised graph by the whole CTA.
-template <typename AR, typename S>
-__device__ void close_blocked(int *D, int n, int ld, int init_bits, int *sA, int *sB, int *sT) {
+template <typename S>
+__device__ void close_blocked(int *D, int n, int ld, bool f32, int init_bits, int *sA, int *sB, int *sC, int *sT) {
   const int nb = (n + kSlabM - 1) / kSlabM;
   for (int kb = 0; kb < nb; ++kb) {
-    const int kb0 = kb * kSlabM, bk = min(kSlabM, n - kb0);
-    close_diag<S>(D, n, ld, kb0, sT);
+    close_diag<S>(D, n, ld, kb * kSlabM, sT);
     if (nb == 1) break;
     __threadfence();
     __syncthreads();
-    for (int t = 0; t < 2 * (nb - 1); ++t) {
-      if (t < nb - 1) {
-        const int j = (t + (t >= kb)) * kSlabN;
-        tile_product<AR, false>(D, n, ld, kb0, kb0, kb0, j, kb0, j, bk, sA, sB, sT, init_bits);
-      } else {
-        int i = t - (nb - 1);
-        i = (i + (i >= kb)) * kSlabM;
-        tile_product<AR, false>(D, n, ld, i, kb0, kb0, kb0, i, kb0, bk, sA, sB, sT, init_bits);
-      }
-    }
+    phase_tiles<false>(D, n, ld, kb, nb, 2 * (nb - 1), sA, sB, sC, f32, init_bits);
     __threadfence();
     __syncthreads();
-    for (int t = 0; t < (nb - 1) * (nb - 1); ++t) {
-      int i = t / (nb - 1), j = t - i * (nb - 1);
-      i = (i + (i >= kb)) * kSlabM;
-      j = (j + (j >= kb)) * kSlabN;
-      tile_product<AR, true>(D, n, ld, i, kb0, kb0, j, i, j, bk, sA, sB, sT, init_bits);
-    }
+    phase_tiles<true>(D, n, ld, kb, nb, (nb - 1) * (nb - 1), sA, sB, sC, f32, init_bits);
     __threadfence();
     __syncthreads();
   }
@@ -240,7 +277,8 @@ __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(const BatchArgs a
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   int *sA = reinterpret_cast<int *>(smem);
   int *sB = sA + kBStages * kBSlabInts;
-  int *sT = sB + kBStages * kBSlabInts;  // phase-1 scratch and phase-3 C tile
+  int *sC = sB + kBStages * kBSlabInts;  // a phase-3 tile's old C block
+  int *sT = sC + kBTileInts;             // phase-1 row/column exchange buffer
   __shared__ int s_idx;
   __shared__ int red[kBThreads / 32];
   for (;;) {
@@ -265,13 +303,8 @@ __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(const BatchArgs a
     const int wmax = normalise_graph<S>(D, n, ld, a, red);
     __threadfence();
     __syncthreads();
-    if (Store<S>::is_float) {
-      close_blocked<ArithF32, S>(D, n, ld, 0x7f800000, sA, sB, sT);
-    } else if (small_int_bound(wmax, n - 1, 0)) {
-      close_blocked<ArithF32, S>(D, n, ld, a.inf_i, sA, sB, sT);
-    } else {
-      close_blocked<ArithI32, S>(D, n, ld, a.inf_i, sA, sB, sT);
-    }
+    const bool f32 = Store<S>::is_float || small_int_bound(wmax, n - 1, 0);
+    close_blocked<S>(D, n, ld, f32, Store<S>::is_float ? 0x7f800000 : a.inf_i, sA, sB, sC, sT);
     __threadfence();
     __syncthreads();
   }

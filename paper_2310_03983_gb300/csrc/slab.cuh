@@ -99,12 +99,20 @@ struct ArithF32 {
   }
 };
 
+// Accumulator registers may be typed int or float; the int32 sequence only reinterprets their
+// bits (free), which lets one accumulator array serve both instruction sequences.
+__device__ __forceinline__ int acc_bits(int v) { return v; }
+__device__ __forceinline__ int acc_bits(float v) { return __float_as_int(v); }
+__device__ __forceinline__ void set_acc(int &d, int v) { d = v; }
+__device__ __forceinline__ void set_acc(float &d, int v) { d = __int_as_float(v); }
+
 struct ArithI32 {
   typedef int T;
   static __device__ __forceinline__ T from(int v) { return v; }
   static __device__ __forceinline__ int to(T v) { return v; }
   static __device__ __forceinline__ T mn(T a, T b) { return min(a, b); }
-  static __device__ __forceinline__ void slab_full(const int *As, const int *Bs, int tm, int tn, T (&acc)[8][8]) {
+  template <typename A>
+  static __device__ __forceinline__ void slab_full(const int *As, const int *Bs, int tm, int tn, A (&acc)[8][8]) {
 #pragma unroll 1
     for (int q = 0; q < kSlabK / 4; ++q) {
       int4 a[8];
@@ -120,13 +128,15 @@ struct ArithI32 {
         for (int i = 0; i < 8; ++i) {
           const int a0 = kp ? a[i].z : a[i].x, a1 = kp ? a[i].w : a[i].y;
 #pragma unroll
-          for (int j = 0; j < 8; ++j) acc[i][j] = __viaddmin_s32(a1, b1[j], __viaddmin_s32(a0, b0[j], acc[i][j]));
+          for (int j = 0; j < 8; ++j)
+            set_acc(acc[i][j], __viaddmin_s32(a1, b1[j], __viaddmin_s32(a0, b0[j], acc_bits(acc[i][j]))));
         }
       }
     }
   }
+  template <typename A>
   static __device__ __forceinline__ void slab_part(const int *As, const int *Bs, int tm, int tn, int kc,
-                                                   T (&acc)[8][8]) {
+                                                   A (&acc)[8][8]) {
     for (int k = 0; k < kc; ++k) {
       int a[8];
 #pragma unroll
@@ -137,7 +147,7 @@ struct ArithI32 {
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = __viaddmin_s32(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < 8; ++j) set_acc(acc[i][j], __viaddmin_s32(a[i], b[j], acc_bits(acc[i][j])));
     }
   }
 };
