@@ -44,6 +44,7 @@ WORKLOADS = {
     "apsp_fw_n4096": dict(n=4096, p=0.5, dtype="int32", dist="uniform", lo=1, hi=1000, algo="fw"),
     "apsp_fw_n8192": dict(n=8192, p=0.05, dtype="int32", dist="uniform", lo=1, hi=100, algo="fw"),
     "batched_2048": dict(n=None, count=2048, dtype="int32", dist="uniform", lo=1, hi=100, algo="batched"),
+    "batched_256": dict(n=None, count=256, dtype="int32", dist="uniform", lo=1, hi=100, algo="batched"),
     "serve_poisson": dict(n=None, rate=200.0, library=128, n_lo=64, n_hi=8192, dtype="mixed", dist="mixed", lo=1,
                           hi=100, algo="serve"),
 }
