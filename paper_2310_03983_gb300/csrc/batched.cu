@@ -16,9 +16,13 @@
 // shape, so no per-graph TMA descriptors are needed).  int32 graphs whose (n - 1) * largest finite weight < 2^24 use
 // the exact fp32 instruction sequence; others the int32 one.  One CTA per graph needs no
 // inter-CTA synchronisation: there is no spin-wait anywhere in this kernel.
+#include <cooperative_groups.h>
+
 #include "diag.cuh"
 #include "slab.cuh"
 #include "tgemm.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace apsp {
 
@@ -73,12 +77,14 @@ template <> struct Store<float> {
 };
 
 // a1 for one graph, whole CTA: returns the largest finite weight (int32; 0 for float32).
+// rank / csize: this CTA normalises rows rank, rank + csize, ... (in warp-sized strides).
 template <typename S>
-__device__ int normalise_graph(int *D, int n, int ld, const BatchArgs &a, int *red) {
+__device__ int normalise_graph(int *D, int n, int ld, const BatchArgs &a, int *red, int rank, int csize) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int W = kBThreads / 32;
   bool bad = false;
   int m = 0;
-  for (int i = warp; i < n; i += kBThreads / 32) {
+  for (int i = warp + W * rank; i < n; i += W * csize) {
     int *row = D + (int64_t)i * ld;
     for (int j = lane; j < n; j += 32) {
       const int v = (j == i) ? 0 : Store<S>::fix(row[j], a, bad);
@@ -147,18 +153,20 @@ __device__ __forceinline__ PhaseTile phase_tile(bool rest, int t, int nb, int kb
 // f32: the exact fp32 instruction sequence, else the int32 one; the accumulators are fp32
 // registers either way (for non-negative values, ordering their bits as int32 or as fp32 agrees,
 // so the final min with the old C is the same operation for both).
+// This CTA takes tiles t0, t0 + tstride, ... of the phase (a cluster splits a phase this way).
 template <bool ACC>
-__device__ void phase_tiles(int *D, int n, int ld, int kb, int nb, int ntiles, int *sA, int *sB, int *sC, bool f32,
-                            int init_bits) {
+__device__ void phase_tiles(int *D, int n, int ld, int kb, int nb, int ntiles, int t0, int tstride, int *sA, int *sB,
+                            int *sC, bool f32, int init_bits) {
   typedef ArithF32 AR;
   typedef float T;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tm = (warp & 3) * 4 + (lane >> 3), tn = (warp >> 2) * 8 + (lane & 7);
   const int bk = min(kSlabM, n - kb * kSlabM);
   const int nk = (bk + kSlabK - 1) / kSlabK;
-  const int total = ntiles * nk;
+  const int mine = ntiles > t0 ? (ntiles - t0 + tstride - 1) / tstride : 0;
+  const int total = mine * nk;
   auto load_slab = [&](int g) {
-    const PhaseTile p = phase_tile(ACC, g / nk, nb, kb);
+    const PhaseTile p = phase_tile(ACC, t0 + (g / nk) * tstride, nb, kb);
     const int kt = g % nk, st = g % kBStages;
     int *As = sA + st * kBSlabInts, *Bs = sB + st * kBSlabInts;
 #pragma unroll
@@ -186,8 +194,8 @@ __device__ void phase_tiles(int *D, int n, int ld, int kb, int nb, int ntiles, i
   T acc[8][8];
   const T init = AR::from(init_bits);
   for (int g = 0; g < total; ++g) {
-    const int t = g / nk, kt = g - t * nk;
-    const PhaseTile p = phase_tile(ACC, t, nb, kb);
+    const int lt = g / nk, kt = g - lt * nk;
+    const PhaseTile p = phase_tile(ACC, t0 + lt * tstride, nb, kb);
     const int m_valid = min(kSlabM, n - p.cr), n_valid = min(kSlabN, n - p.cc);
     if (kt == 0) {
 #pragma unroll
@@ -253,23 +261,51 @@ __device__ void phase_tiles(int *D, int n, int ld, int kb, int nb, int ntiles, i
   __syncthreads();  // shared buffers are reused by the next phase
 }
 
-// Blocked Floyd-Warshall of one normalised graph by the whole CTA.
+// Orders every global-memory write of the group before every later read by the group: a CTA
+// barrier for a lone CTA, the hardware cluster barrier (release / acquire) for a cluster.
+__device__ __forceinline__ void group_sync(int csize) {
+  __threadfence();
+  if (csize > 1) cg::this_cluster().sync();
+  else __syncthreads();
+}
+
+// Blocked Floyd-Warshall of one normalised graph by a group of csize CTAs (this one has
+// rank `rank`): rank 0 closes each diagonal tile, the panel and remaining tiles are shared
+// round-robin, and a group barrier separates the phases.
 template <typename S>
-__device__ void close_blocked(int *D, int n, int ld, bool f32, int init_bits, int *sA, int *sB, int *sC, int *sT) {
+__device__ void close_blocked(int *D, int n, int ld, bool f32, int init_bits, int *sA, int *sB, int *sC, int *sT,
+                              int rank, int csize) {
   const int nb = (n + kSlabM - 1) / kSlabM;
   for (int kb = 0; kb < nb; ++kb) {
-    close_diag<S>(D, n, ld, kb * kSlabM, sT);
+    if (rank == 0) close_diag<S>(D, n, ld, kb * kSlabM, sT);
     if (nb == 1) break;
-    __threadfence();
-    __syncthreads();
-    phase_tiles<false>(D, n, ld, kb, nb, 2 * (nb - 1), sA, sB, sC, f32, init_bits);
-    __threadfence();
-    __syncthreads();
-    phase_tiles<true>(D, n, ld, kb, nb, (nb - 1) * (nb - 1), sA, sB, sC, f32, init_bits);
-    __threadfence();
-    __syncthreads();
+    group_sync(csize);
+    phase_tiles<false>(D, n, ld, kb, nb, 2 * (nb - 1), rank, csize, sA, sB, sC, f32, init_bits);
+    group_sync(csize);
+    phase_tiles<true>(D, n, ld, kb, nb, (nb - 1) * (nb - 1), rank, csize, sA, sB, sC, f32, init_bits);
+    group_sync(csize);
   }
 }
+
+// Checks graph g's descriptor; on failure flags APSP_ERR_ARG (rank 0) and returns null.
+__device__ __forceinline__ int *graph_base(const BatchArgs &a, int g, int &n, int &ld, bool flag) {
+  n = a.ns[g];
+  ld = a.lds[g];
+  const int64_t off = a.offsets[g];
+  if (n <= 0) return nullptr;
+  if (ld < n || (ld & 3) || (off & 3) || off < 0) {
+    if (flag && threadIdx.x == 0) flag_status(a.status, APSP_ERR_ARG);
+    return nullptr;
+  }
+  return a.pool + off;
+}
+
+// The persistent kernel runs as clusters of csize CTAs (csize = 1 without clusters).  Cluster
+// rank 0 pulls the next entry of the queue.  A graph of more than 128 vertices is closed by
+// the whole cluster together; otherwise rank 0 takes csize - 1 more entries and every CTA
+// closes one small graph alone.  The command travels to every CTA's shared memory through
+// distributed shared memory, followed by a cluster barrier; no CTA ever spins.
+enum { kCmdDone = 0, kCmdCluster = 1, kCmdAlone = 2, kCmdIdle = 3 };
 
 template <typename S>
 __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(const BatchArgs a) {
@@ -279,35 +315,136 @@ __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(const BatchArgs a
   int *sB = sA + kBStages * kBSlabInts;
   int *sC = sB + kBStages * kBSlabInts;  // a phase-3 tile's old C block
   int *sT = sC + kBTileInts;             // phase-1 row/column exchange buffer
-  __shared__ int s_idx;
+  __shared__ int s_cmd[2];
+  __shared__ int s_wmax;
   __shared__ int red[kBThreads / 32];
+  cg::cluster_group cl = cg::this_cluster();
+  const int csize = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   for (;;) {
-    if (threadIdx.x == 0) s_idx = atomicAdd(a.queue, 1);
-    __syncthreads();
-    const int64_t idx = s_idx;
-    __syncthreads();
-    if (idx >= a.count) break;
-    const int g = a.order ? a.order[idx] : (int)idx;
-    if (g < 0 || g >= a.count) {
-      if (threadIdx.x == 0) flag_status(a.status, APSP_ERR_ARG);
-      continue;
+    if (rank == 0 && threadIdx.x == 0) {
+      const int64_t idx = atomicAdd(a.queue, 1);
+      int g = -1, n = 0;
+      if (idx < a.count) {
+        g = a.order ? a.order[idx] : (int)idx;
+        if (g >= 0 && g < a.count) n = a.ns[g];
+      }
+      if (idx >= a.count) {
+        for (int q = 0; q < csize; ++q) cl.map_shared_rank(s_cmd, q)[0] = kCmdDone;
+      } else if (csize > 1 && n > kSlabM) {
+        s_wmax = 0;
+        for (int q = 0; q < csize; ++q) {
+          int *c = cl.map_shared_rank(s_cmd, q);
+          c[0] = kCmdCluster;
+          c[1] = (int)idx;
+        }
+      } else {
+        s_cmd[0] = kCmdAlone;
+        s_cmd[1] = (int)idx;
+        const int64_t base = csize > 1 ? atomicAdd(a.queue, csize - 1) : 0;
+        for (int q = 1; q < csize; ++q) {
+          int *c = cl.map_shared_rank(s_cmd, q);
+          c[0] = base + q - 1 < a.count ? kCmdAlone : kCmdIdle;
+          c[1] = (int)(base + q - 1);
+        }
+      }
     }
-    const int n = a.ns[g], ld = a.lds[g];
-    const int64_t off = a.offsets[g];
-    if (n <= 0) continue;
-    if (ld < n || (ld & 3) || (off & 3) || off < 0) {
-      if (threadIdx.x == 0) flag_status(a.status, APSP_ERR_ARG);
-      continue;
+    if (csize > 1) cl.sync();
+    else __syncthreads();
+    const int cmd = s_cmd[0], idx = s_cmd[1];
+    if (cmd == kCmdDone) break;
+    if (cmd != kCmdIdle) {
+      const int g = a.order ? a.order[idx] : idx;
+      const bool together = cmd == kCmdCluster;
+      const int grank = together ? rank : 0, gsize = together ? csize : 1;
+      int n = 0, ld = 0;
+      int *D = (g >= 0 && g < a.count) ? graph_base(a, g, n, ld, grank == 0) : nullptr;
+      if (g < 0 || g >= a.count) {
+        if (grank == 0 && threadIdx.x == 0) flag_status(a.status, APSP_ERR_ARG);
+      }
+      if (D) {
+        int wmax = normalise_graph<S>(D, n, ld, a, red, grank, gsize);
+        if (together) {
+          if (threadIdx.x == 0) atomicMax(cl.map_shared_rank(&s_wmax, 0), wmax);
+          group_sync(gsize);
+          wmax = *cl.map_shared_rank(&s_wmax, 0);
+        } else {
+          group_sync(1);
+        }
+        const bool f32 = Store<S>::is_float || small_int_bound(wmax, n - 1, 0);
+        close_blocked<S>(D, n, ld, f32, Store<S>::is_float ? 0x7f800000 : a.inf_i, sA, sB, sC, sT, grank, gsize);
+      }
     }
-    int *D = a.pool + off;
-    const int wmax = normalise_graph<S>(D, n, ld, a, red);
-    __threadfence();
-    __syncthreads();
-    const bool f32 = Store<S>::is_float || small_int_bound(wmax, n - 1, 0);
-    close_blocked<S>(D, n, ld, f32, Store<S>::is_float ? 0x7f800000 : a.inf_i, sA, sB, sC, sT);
-    __threadfence();
-    __syncthreads();
+    group_sync(csize);  // every CTA is done with this command before the next one is written
   }
+}
+
+// Launch shape of the persistent kernel: the largest cluster size (8, 4, 2) whose co-resident
+// clusters still cover at least 7/8 of the SMs, with that many clusters; else plain CTAs.
+struct BatchShape {
+  int csize = 1, clusters = 0;
+};
+
+template <typename S>
+static BatchShape batch_shape() {
+  static BatchShape cache[64];
+  static bool have[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && have[dev]) return cache[dev];
+  BatchShape best;
+  best.clusters = sm_count();
+  for (int c : {8, 4, 2}) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c * 16);
+    cfg.blockDim = dim3(kBThreads);
+    cfg.dynamicSmemBytes = kBSmemBytes;
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = c;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    int num = 0;
+    if (cudaOccupancyMaxActiveClusters(&num, batched_kernel<S>, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (num * c * 8 >= sm_count() * 7) {
+      best.csize = c;
+      best.clusters = num;
+      break;
+    }
+  }
+  if (dev >= 0 && dev < 64) {
+    cache[dev] = best;
+    have[dev] = true;
+  }
+  return best;
+}
+
+template <typename S>
+static int launch_batched(const BatchArgs &a, cudaStream_t s) {
+  if (cudaFuncSetAttribute(batched_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBSmemBytes) != cudaSuccess)
+    return APSP_ERR_CUDA;
+  const BatchShape sh = batch_shape<S>();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(sh.csize * sh.clusters);
+  cfg.blockDim = dim3(kBThreads);
+  cfg.dynamicSmemBytes = kBSmemBytes;
+  cfg.stream = s;
+  cudaLaunchAttribute at;
+  at.id = cudaLaunchAttributeClusterDimension;
+  at.val.clusterDim.x = sh.csize;
+  at.val.clusterDim.y = 1;
+  at.val.clusterDim.z = 1;
+  cfg.attrs = &at;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, batched_kernel<S>, a) != cudaSuccess) {
+    cudaGetLastError();
+    return APSP_ERR_CUDA;
+  }
+  return APSP_OK;
 }
 
 }  // namespace apsp
@@ -346,24 +483,7 @@ extern "C" int apsp_batched(void *pool, const int64_t *offsets, const int32_t *n
   a.status = status_word();
   int r = APSP_OK;
   if (cudaMemsetAsync(a.queue, 0, sizeof(int), s) != cudaSuccess) r = APSP_ERR_CUDA;
-  const int64_t sms = sm_count();
-  const int grid = (int)(count < sms ? count : sms);
-  if (!r) {
-    if (dtype == APSP_I32) {
-      if (cudaFuncSetAttribute(batched_kernel<int>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBSmemBytes) !=
-          cudaSuccess)
-        r = APSP_ERR_CUDA;
-      else
-        batched_kernel<int><<<grid, kBThreads, kBSmemBytes, s>>>(a);
-    } else {
-      if (cudaFuncSetAttribute(batched_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBSmemBytes) !=
-          cudaSuccess)
-        r = APSP_ERR_CUDA;
-      else
-        batched_kernel<float><<<grid, kBThreads, kBSmemBytes, s>>>(a);
-    }
-    if (!r && cudaGetLastError() != cudaSuccess) r = APSP_ERR_CUDA;
-  }
+  if (!r) r = dtype == APSP_I32 ? launch_batched<int>(a, s) : launch_batched<float>(a, s);
   if (own) cudaFreeAsync(own, s);
   return r;
 }

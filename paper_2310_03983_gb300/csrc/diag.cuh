@@ -98,7 +98,8 @@ __device__ __forceinline__ void load_tile_regs(int (&d)[8][8], const int *T, int
     for (int h = 0; h < 2; ++h) {
       const int c = 4 * tn + 64 * h;
       int4 v = make_int4(0, 0, 0, 0);
-      if (r < bk && c < bk) v = *reinterpret_cast<const int4 *>(T + (int64_t)r * ld + c);
+      // L2-only load: the tile may have been written by another CTA of a cluster
+      if (r < bk && c < bk) v = __ldcg(reinterpret_cast<const int4 *>(T + (int64_t)r * ld + c));
       d[i][4 * h] = v.x; d[i][4 * h + 1] = v.y; d[i][4 * h + 2] = v.z; d[i][4 * h + 3] = v.w;
     }
   }
