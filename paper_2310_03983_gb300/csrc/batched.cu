@@ -300,13 +300,14 @@ __device__ __forceinline__ int *graph_base(const BatchArgs &a, int g, int &n, in
   return a.pool + off;
 }
 
-// The persistent kernel runs as clusters of csize CTAs (csize = 1 without clusters).  Cluster
-// rank 0 pulls the next entry of the queue.  A graph of more than 128 vertices is closed by
-// the whole cluster together; otherwise rank 0 takes csize - 1 more entries and every CTA
-// closes one small graph alone.  The command travels to every CTA's shared memory through
-// distributed shared memory, followed by a cluster barrier; no CTA ever spins.
-enum { kCmdDone = 0, kCmdCluster = 1, kCmdAlone = 2, kCmdIdle = 3 };
-
+// The persistent kernel runs as clusters of csize CTAs (csize = 1 without clusters), in two
+// stages.  Stage 1: the leading run of the queue order whose graphs have more than
+// 64 * csize vertices (enough tiles per phase to keep a whole cluster busy; the order is
+// largest first) is closed one graph at a time by whole clusters: rank 0 takes the next
+// entry and writes it into every CTA's shared memory through distributed shared memory, and
+// hardware cluster barriers separate the steps.  Stage 2: every CTA pulls the remaining
+// graphs from its own counter and closes each alone, with no cluster barrier at all.  No CTA
+// ever spins.
 template <typename S>
 __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(const BatchArgs a) {
   extern __shared__ uint8_t smem_raw[];
@@ -315,66 +316,75 @@ __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(const BatchArgs a
   int *sB = sA + kBStages * kBSlabInts;
   int *sC = sB + kBStages * kBSlabInts;  // a phase-3 tile's old C block
   int *sT = sC + kBTileInts;             // phase-1 row/column exchange buffer
-  __shared__ int s_cmd[2];
+  __shared__ int s_idx;
   __shared__ int s_wmax;
   __shared__ int red[kBThreads / 32];
   cg::cluster_group cl = cg::this_cluster();
   const int csize = (int)cl.num_blocks(), rank = (int)cl.block_rank();
-  for (;;) {
+  const int init_bits = Store<S>::is_float ? 0x7f800000 : a.inf_i;
+
+  // Length of the cooperative prefix (the same for every CTA).
+  int nbig = 0;
+  if (csize > 1) {
+    const int big_n = 64 * csize;
+    if (threadIdx.x == 0) {
+      int k = 0;
+      while (k < a.count) {
+        const int g = a.order ? a.order[k] : k;
+        if (g < 0 || g >= a.count || a.ns[g] <= big_n) break;
+        ++k;
+      }
+      s_idx = k;
+    }
+    __syncthreads();
+    nbig = s_idx;
+    __syncthreads();
+  }
+
+  // Stage 1: large graphs, one per cluster at a time.
+  while (nbig > 0) {
     if (rank == 0 && threadIdx.x == 0) {
-      const int64_t idx = atomicAdd(a.queue, 1);
-      int g = -1, n = 0;
-      if (idx < a.count) {
-        g = a.order ? a.order[idx] : (int)idx;
-        if (g >= 0 && g < a.count) n = a.ns[g];
-      }
-      if (idx >= a.count) {
-        for (int q = 0; q < csize; ++q) cl.map_shared_rank(s_cmd, q)[0] = kCmdDone;
-      } else if (csize > 1 && n > kSlabM) {
-        s_wmax = 0;
-        for (int q = 0; q < csize; ++q) {
-          int *c = cl.map_shared_rank(s_cmd, q);
-          c[0] = kCmdCluster;
-          c[1] = (int)idx;
-        }
-      } else {
-        s_cmd[0] = kCmdAlone;
-        s_cmd[1] = (int)idx;
-        const int64_t base = csize > 1 ? atomicAdd(a.queue, csize - 1) : 0;
-        for (int q = 1; q < csize; ++q) {
-          int *c = cl.map_shared_rank(s_cmd, q);
-          c[0] = base + q - 1 < a.count ? kCmdAlone : kCmdIdle;
-          c[1] = (int)(base + q - 1);
-        }
-      }
+      const int idx = atomicAdd(&a.queue[0], 1);
+      s_wmax = 0;
+      for (int q = 0; q < csize; ++q) *cl.map_shared_rank(&s_idx, q) = idx;
     }
-    if (csize > 1) cl.sync();
-    else __syncthreads();
-    const int cmd = s_cmd[0], idx = s_cmd[1];
-    if (cmd == kCmdDone) break;
-    if (cmd != kCmdIdle) {
-      const int g = a.order ? a.order[idx] : idx;
-      const bool together = cmd == kCmdCluster;
-      const int grank = together ? rank : 0, gsize = together ? csize : 1;
-      int n = 0, ld = 0;
-      int *D = (g >= 0 && g < a.count) ? graph_base(a, g, n, ld, grank == 0) : nullptr;
-      if (g < 0 || g >= a.count) {
-        if (grank == 0 && threadIdx.x == 0) flag_status(a.status, APSP_ERR_ARG);
-      }
-      if (D) {
-        int wmax = normalise_graph<S>(D, n, ld, a, red, grank, gsize);
-        if (together) {
-          if (threadIdx.x == 0) atomicMax(cl.map_shared_rank(&s_wmax, 0), wmax);
-          group_sync(gsize);
-          wmax = *cl.map_shared_rank(&s_wmax, 0);
-        } else {
-          group_sync(1);
-        }
-        const bool f32 = Store<S>::is_float || small_int_bound(wmax, n - 1, 0);
-        close_blocked<S>(D, n, ld, f32, Store<S>::is_float ? 0x7f800000 : a.inf_i, sA, sB, sC, sT, grank, gsize);
-      }
+    cl.sync();
+    const int idx = s_idx;
+    if (idx >= nbig) break;  // every CTA of the cluster read the same value
+    const int g = a.order ? a.order[idx] : idx;
+    int n = 0, ld = 0;
+    int *D = graph_base(a, g, n, ld, rank == 0);
+    if (D) {
+      const int w = normalise_graph<S>(D, n, ld, a, red, rank, csize);
+      if (threadIdx.x == 0) atomicMax(cl.map_shared_rank(&s_wmax, 0), w);
+      group_sync(csize);
+      const int wmax = *cl.map_shared_rank(&s_wmax, 0);
+      const bool f32 = Store<S>::is_float || small_int_bound(wmax, n - 1, 0);
+      close_blocked<S>(D, n, ld, f32, init_bits, sA, sB, sC, sT, rank, csize);
     }
-    group_sync(csize);  // every CTA is done with this command before the next one is written
+    group_sync(csize);  // the whole cluster is done before rank 0 writes the next index
+  }
+
+  // Stage 2: every other graph, one per CTA.
+  for (;;) {
+    if (threadIdx.x == 0) s_idx = nbig + atomicAdd(&a.queue[1], 1);
+    __syncthreads();
+    const int idx = s_idx;
+    __syncthreads();
+    if (idx >= a.count) break;
+    const int g = a.order ? a.order[idx] : idx;
+    if (g < 0 || g >= a.count) {
+      if (threadIdx.x == 0) flag_status(a.status, APSP_ERR_ARG);
+      continue;
+    }
+    int n = 0, ld = 0;
+    int *D = graph_base(a, g, n, ld, true);
+    if (!D) continue;
+    const int wmax = normalise_graph<S>(D, n, ld, a, red, 0, 1);
+    group_sync(1);
+    const bool f32 = Store<S>::is_float || small_int_bound(wmax, n - 1, 0);
+    close_blocked<S>(D, n, ld, f32, init_bits, sA, sB, sC, sT, 0, 1);
+    group_sync(1);
   }
 }
 
@@ -482,7 +492,7 @@ extern "C" int apsp_batched(void *pool, const int64_t *offsets, const int32_t *n
   a.queue = reinterpret_cast<int *>(ws);
   a.status = status_word();
   int r = APSP_OK;
-  if (cudaMemsetAsync(a.queue, 0, sizeof(int), s) != cudaSuccess) r = APSP_ERR_CUDA;
+  if (cudaMemsetAsync(a.queue, 0, 2 * sizeof(int), s) != cudaSuccess) r = APSP_ERR_CUDA;
   if (!r) r = dtype == APSP_I32 ? launch_batched<int>(a, s) : launch_batched<float>(a, s);
   if (own) cudaFreeAsync(own, s);
   return r;
