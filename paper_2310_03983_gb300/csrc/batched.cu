@@ -316,14 +316,16 @@ __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(const BatchArgs a
   int *sB = sA + kBStages * kBSlabInts;
   int *sC = sB + kBStages * kBSlabInts;  // a phase-3 tile's old C block
   int *sT = sC + kBTileInts;             // phase-1 row/column exchange buffer
-  __shared__ int s_idx;
+  __shared__ int s_idx;   // stage 1: written by the cluster's rank 0 through DSMEM
+  __shared__ int s_nbig;
   __shared__ int s_wmax;
   __shared__ int red[kBThreads / 32];
   cg::cluster_group cl = cg::this_cluster();
   const int csize = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   const int init_bits = Store<S>::is_float ? 0x7f800000 : a.inf_i;
 
-  // Length of the cooperative prefix (the same for every CTA).
+  // Length of the cooperative prefix (the same for every CTA).  The cluster barrier after it
+  // keeps rank 0's first remote write out of any CTA's shared memory until that CTA is ready.
   int nbig = 0;
   if (csize > 1) {
     const int big_n = 64 * csize;
@@ -334,11 +336,11 @@ __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(const BatchArgs a
         if (g < 0 || g >= a.count || a.ns[g] <= big_n) break;
         ++k;
       }
-      s_idx = k;
+      s_nbig = k;
     }
     __syncthreads();
-    nbig = s_idx;
-    __syncthreads();
+    nbig = s_nbig;
+    cl.sync();
   }
 
   // Stage 1: large graphs, one per cluster at a time.
