@@ -301,9 +301,9 @@ __device__ __forceinline__ int *graph_base(const BatchArgs &a, int g, int &n, in
 }
 
 // The persistent kernel runs as clusters of csize CTAs (csize = 1 without clusters), in two
-// stages.  Stage 1: the leading run of the queue order whose graphs have more than
-// 64 * csize vertices (enough tiles per phase to keep a whole cluster busy; the order is
-// largest first) is closed one graph at a time by whole clusters: rank 0 takes the next
+// stages.  Stage 1: the leading run of the queue order whose graphs are each too large for
+// one CTA to close within the batch's average time per CTA (the order is largest first) is
+// closed one graph at a time by whole clusters: rank 0 takes the next
 // entry and writes it into every CTA's shared memory through distributed shared memory, and
 // hardware cluster barriers separate the steps.  Stage 2: every CTA pulls the remaining
 // graphs from its own counter and closes each alone, with no cluster barrier at all.  No CTA
@@ -324,20 +324,41 @@ __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(const BatchArgs a
   const int csize = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   const int init_bits = Store<S>::is_float ? 0x7f800000 : a.inf_i;
 
-  // Length of the cooperative prefix (the same for every CTA).  The cluster barrier after it
-  // keeps rank 0's first remote write out of any CTA's shared memory until that CTA is ready.
+  // Length of the cooperative prefix (the same for every CTA): the leading entries whose
+  // graph alone would take more than half of the average work per CTA (n^3 > W / (2 CTAs),
+  // W = sum of n^3) and has enough tiles for a cluster (n > 64 csize).  A batch whose graphs
+  // are all small next to the whole keeps every graph on one CTA.  The cluster barrier after
+  // it keeps rank 0's first remote write out of any CTA's shared memory until that CTA is ready.
   int nbig = 0;
   if (csize > 1) {
-    const int big_n = 64 * csize;
-    if (threadIdx.x == 0) {
-      int k = 0;
-      while (k < a.count) {
-        const int g = a.order ? a.order[k] : k;
-        if (g < 0 || g >= a.count || a.ns[g] <= big_n) break;
-        ++k;
+    __shared__ double s_work[kBThreads / 32];
+    double w = 0.0;
+    for (int k = threadIdx.x; k < a.count; k += kBThreads) {
+      const int g = a.order ? a.order[k] : k;
+      if (g >= 0 && g < a.count) {
+        const double n = (double)max(a.ns[g], 0);
+        w += n * n * n;
       }
-      s_nbig = k;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if ((threadIdx.x & 31) == 0) s_work[threadIdx.x >> 5] = w;
+    if (threadIdx.x == 0) s_nbig = a.count;
+    __syncthreads();
+    double total = 0.0;
+#pragma unroll
+    for (int i = 0; i < kBThreads / 32; ++i) total += s_work[i];
+    const double big3 = fmax(0.5 * total / (double)gridDim.x, (double)(64 * csize) * (64 * csize) * (64 * csize));
+    int first_small = a.count;
+    for (int k = threadIdx.x; k < a.count; k += kBThreads) {
+      const int g = a.order ? a.order[k] : k;
+      const double n = (g >= 0 && g < a.count) ? (double)a.ns[g] : 0.0;
+      if (!(n * n * n > big3)) {
+        first_small = k;
+        break;
+      }
+    }
+    atomicMin(&s_nbig, first_small);
     __syncthreads();
     nbig = s_nbig;
     cl.sync();
