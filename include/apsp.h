@@ -155,15 +155,18 @@ int apsp_rkleene_noalloc(void *d, int64_t n, int64_t ld, int dtype, const void *
  * apsp_fw would close it (a1 normalisation, then blocked Floyd-Warshall), so results are
  * identical to closing each graph alone.  `order` (device, optional) lists the graph indices
  * in processing order -- largest first balances the persistent CTAs best; NULL = 0..count-1.
- * offsets, ns, lds and order are DEVICE arrays of `count` entries.  pool must be 16-byte
+ * offsets, ns, lds and order are DEVICE arrays of `count` entries; ns_host (optional, host) is
+ * a copy of ns that lets the library pick the launch shape: when some graph would take longer
+ * alone than half the average work per SM, the kernel runs as thread-block clusters that close
+ * such graphs together; otherwise one CTA per graph on every SM (NULL: clusters).  pool must be 16-byte
  * aligned; every lds[g] and offsets[g] must be a multiple of 4 and lds[g] >= ns[g]: a graph
  * that breaks this, or an order entry outside [0, count), is skipped and sets APSP_ERR_ARG
  * in the device status word (the rest of the batch is still closed).  ns[g] <= 0 is skipped.
  * The workspace holds the work-queue counter (apsp_batched_workspace_bytes). */
 size_t apsp_batched_workspace_bytes(int64_t count);
 int apsp_batched(void *pool, const int64_t *offsets, const int32_t *ns, const int32_t *lds,
-                 const int32_t *order, int64_t count, int dtype, const void *inf, void *ws,
-                 size_t ws_bytes, void *stream);
+                 const int32_t *order, const int32_t *ns_host, int64_t count, int dtype,
+                 const void *inf, void *ws, size_t ws_bytes, void *stream);
 
 /* ---- a8: the planner's cost-model network ---------------------------------------------
  * A perceptron with two hidden layers of 64 ReLU units, fp32, that predicts the log run time

@@ -52,7 +52,7 @@ def _load():
         "apsp_rkleene": ([vp, i64, i64, i32, vp, i32, vp, sz, vp], i32),
         "apsp_probe_minplus": ([i32, i32, i32, i32, vp, vp], i32),
         "apsp_batched_workspace_bytes": ([i64], sz),
-        "apsp_batched": ([vp, vp, vp, vp, vp, i64, i32, vp, vp, sz, vp], i32),
+        "apsp_batched": ([vp, vp, vp, vp, vp, vp, i64, i32, vp, vp, sz, vp], i32),
         "apsp_mlp_param_count": ([i32], i64),
         "apsp_mlp_backward_workspace_bytes": ([i32, i32], sz),
         "apsp_mlp_forward": ([vp, i32, vp, i32, vp, vp, vp], i32),
@@ -274,19 +274,22 @@ def apsp_close_cta(d: torch.Tensor, inf=None, stream=None):
     off, ns, lds, ws = _OneGraph.get(n, ld, d.device)
     code = _dtype_code(d)
     ip, _keep = _inf_arg(inf, code)
-    _check(_lib.apsp_batched(p, off.data_ptr(), ns.data_ptr(), lds.data_ptr(), None, 1, code, ip, ws.data_ptr(),
+    nh = (ctypes.c_int32 * 1)(n)
+    _check(_lib.apsp_batched(p, off.data_ptr(), ns.data_ptr(), lds.data_ptr(), None, nh, 1, code, ip, ws.data_ptr(),
                              ws.numel(), _stream(stream)), "apsp_batched")
     return d
 
 
-def apsp_batched_raw(pool, d_offsets, d_ns, d_lds, d_order, count: int, ws, inf=None, stream=None):
+def apsp_batched_raw(pool, d_offsets, d_ns, d_lds, d_order, count: int, ws, inf=None, stream=None, ns_host=None):
     """apsp_batched on caller-built device descriptor arrays (int64 offsets, int32 ns, lds and
-    order) over `pool` (a 1-D int32 or float32 CUDA tensor)."""
+    order) over `pool` (a 1-D int32 or float32 CUDA tensor); ns_host: optional numpy copy of ns."""
     code = _dtype_code(pool)
     ip, _keep = _inf_arg(inf, code)
+    nh = None if ns_host is None else np.ascontiguousarray(ns_host, dtype=np.int32)
     _check(_lib.apsp_batched(pool.data_ptr(), d_offsets.data_ptr(), d_ns.data_ptr(), d_lds.data_ptr(),
-                             None if d_order is None else d_order.data_ptr(), count, code, ip, ws.data_ptr(),
-                             ws.numel() * ws.element_size(), _stream(stream)), "apsp_batched")
+                             None if d_order is None else d_order.data_ptr(),
+                             None if nh is None else nh.ctypes.data_as(ctypes.c_void_p), count, code, ip,
+                             ws.data_ptr(), ws.numel() * ws.element_size(), _stream(stream)), "apsp_batched")
 
 
 def apsp_batched(batch: Batch, inf=None, stream=None, pool=None):
@@ -295,7 +298,8 @@ def apsp_batched(batch: Batch, inf=None, stream=None, pool=None):
     ip, _keep = _inf_arg(inf, code)
     p = batch.pool if pool is None else pool
     _check(_lib.apsp_batched(p.data_ptr(), batch.d_offsets.data_ptr(), batch.d_ns.data_ptr(),
-                             batch.d_lds.data_ptr(), batch.d_order.data_ptr(), len(batch), code, ip,
+                             batch.d_lds.data_ptr(), batch.d_order.data_ptr(),
+                             batch.ns.ctypes.data_as(ctypes.c_void_p), len(batch), code, ip,
                              batch.ws.data_ptr(), batch.ws.numel(), _stream(stream)), "apsp_batched")
     return batch
 

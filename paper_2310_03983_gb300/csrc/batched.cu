@@ -456,11 +456,26 @@ static BatchShape batch_shape() {
   return best;
 }
 
+// Clusters pay off only when some graph would, alone on one CTA, take longer than half the
+// average work per SM; otherwise every graph stays on one CTA and all SMs take part.
+static bool needs_clusters(const int32_t *ns_host, int64_t count) {
+  if (!ns_host) return true;
+  double w = 0.0, mx = 0.0;
+  for (int64_t g = 0; g < count; ++g) {
+    const double n = (double)(ns_host[g] > 0 ? ns_host[g] : 0);
+    w += n * n * n;
+    mx = n > mx ? n : mx;
+  }
+  return mx > kSlabM && mx * mx * mx > 0.5 * w / (double)sm_count();
+}
+
 template <typename S>
-static int launch_batched(const BatchArgs &a, cudaStream_t s) {
+static int launch_batched(const BatchArgs &a, bool clusters, cudaStream_t s) {
   if (cudaFuncSetAttribute(batched_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBSmemBytes) != cudaSuccess)
     return APSP_ERR_CUDA;
-  const BatchShape sh = batch_shape<S>();
+  BatchShape sh;
+  sh.clusters = sm_count();
+  if (clusters) sh = batch_shape<S>();
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(sh.csize * sh.clusters);
   cfg.blockDim = dim3(kBThreads);
@@ -488,8 +503,8 @@ extern "C" size_t apsp_batched_workspace_bytes(int64_t count) {
 }
 
 extern "C" int apsp_batched(void *pool, const int64_t *offsets, const int32_t *ns, const int32_t *lds,
-                            const int32_t *order, int64_t count, int dtype, const void *inf, void *ws, size_t ws_bytes,
-                            void *stream) {
+                            const int32_t *order, const int32_t *ns_host, int64_t count, int dtype, const void *inf,
+                            void *ws, size_t ws_bytes, void *stream) {
   using namespace apsp;
   if (!dtype_ok(dtype) || count < 0 || count > INT32_MAX) return APSP_ERR_ARG;
   if (count == 0) return APSP_OK;
@@ -516,7 +531,8 @@ extern "C" int apsp_batched(void *pool, const int64_t *offsets, const int32_t *n
   a.status = status_word();
   int r = APSP_OK;
   if (cudaMemsetAsync(a.queue, 0, 2 * sizeof(int), s) != cudaSuccess) r = APSP_ERR_CUDA;
-  if (!r) r = dtype == APSP_I32 ? launch_batched<int>(a, s) : launch_batched<float>(a, s);
+  const bool clusters = needs_clusters(ns_host, count);
+  if (!r) r = dtype == APSP_I32 ? launch_batched<int>(a, clusters, s) : launch_batched<float>(a, clusters, s);
   if (own) cudaFreeAsync(own, s);
   return r;
 }

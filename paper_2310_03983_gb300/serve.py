@@ -240,7 +240,7 @@ class Server:
                 k = len(group)
                 d_off = dmeta[:2 * k].view(torch.int64)
                 apsp_batched_raw(self.pool if work[1] == "int32" else self.pool.view(torch.float32), d_off,
-                                 dmeta[2 * k:3 * k], dmeta[3 * k:4 * k], dmeta[4 * k:5 * k], k, ws)
+                                 dmeta[2 * k:3 * k], dmeta[3 * k:4 * k], dmeta[4 * k:5 * k], k, ws, ns_host=ns)
                 reqs = group
                 keep = (meta, dmeta)
             else:

@@ -73,3 +73,19 @@ def test_batched_bad_entries_are_skipped(apsp):
     apsp.apsp_batched(b)
     assert apsp.apsp_device_status() == 1
     assert_dist_equal(b.graph(0).cpu().numpy(), oracle.fw(mats[0]), "graph 0")
+
+
+def test_batched_balanced_batch_runs_one_cta_per_graph(apsp):
+    """600 graphs of 150 vertices: no graph dominates, so the launch uses one CTA per graph
+    with no clusters; the same pool closed with the cluster shape must agree bit for bit."""
+    mats = [workloads.er_graph(150, 0.05, "int32", lo=1, hi=100, seed=70 + g) for g in range(600)]
+    b = apsp.Batch(mats)
+    pristine = b.pool.clone()
+    apsp.apsp_batched(b)                          # host sizes given: plain launch
+    plain = b.pool.clone()
+    b.pool.copy_(pristine)
+    apsp.apsp_batched_raw(b.pool, b.d_offsets, b.d_ns, b.d_lds, b.d_order, len(b), b.ws)  # no hint: clusters
+    assert torch.equal(plain, b.pool)
+    for g in (0, 299, 599):
+        assert_dist_equal(b.graph(g, plain).cpu().numpy(), oracle.fw(mats[g]), f"graph {g}")
+    assert apsp.apsp_device_status() == 0
