@@ -157,7 +157,7 @@ int apsp_rkleene_noalloc(void *d, int64_t n, int64_t ld, int dtype, const void *
  * in processing order -- largest first balances the persistent CTAs best; NULL = 0..count-1.
  * offsets, ns, lds and order are DEVICE arrays of `count` entries; ns_host (optional, host) is
  * a copy of ns that lets the library pick the launch shape: when some graph would take longer
- * alone than half the average work per SM, the kernel runs as thread-block clusters that close
+ * alone than the average work per SM, the kernel runs as thread-block clusters that close
  * such graphs together; otherwise one CTA per graph on every SM (NULL: clusters).  pool must be 16-byte
  * aligned; every lds[g] and offsets[g] must be a multiple of 4 and lds[g] >= ns[g]: a graph
  * that breaks this, or an order entry outside [0, count), is skipped and sets APSP_ERR_ARG

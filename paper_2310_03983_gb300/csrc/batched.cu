@@ -456,8 +456,9 @@ static BatchShape batch_shape() {
   return best;
 }
 
-// Clusters pay off only when some graph would, alone on one CTA, take longer than half the
-// average work per SM; otherwise every graph stays on one CTA and all SMs take part.
+// Clusters pay off only when some graph would, alone on one CTA, take longer than the average
+// work per SM (then largest-first list scheduling cannot hide it); otherwise every graph stays
+// on one CTA and all SMs take part.
 static bool needs_clusters(const int32_t *ns_host, int64_t count) {
   if (!ns_host) return true;
   double w = 0.0, mx = 0.0;
@@ -466,7 +467,7 @@ static bool needs_clusters(const int32_t *ns_host, int64_t count) {
     w += n * n * n;
     mx = n > mx ? n : mx;
   }
-  return mx > kSlabM && mx * mx * mx > 0.5 * w / (double)sm_count();
+  return mx > kSlabM && mx * mx * mx > w / (double)sm_count();
 }
 
 template <typename S>
