@@ -13,6 +13,15 @@ What is here, each citing the passage it follows:
   * ``dijkstra_rows`` -- single-source distances from chosen sources by array Dijkstra: an
                          independent algorithm for the same definition, used to check large
                          matrices row by row.
+  * ``fw_pred``       -- Eq. 1 with the predecessor indices of Sec. 2 (pred[i, j] becomes
+                         pred[k, j] whenever the path through k is shorter).
+  * ``last_hop``      -- the predecessor matrix by definition from a closed d and the costs w:
+                         the smallest k != j minimising d[i, k] + w[k, j] (the argmin of
+                         Sec. 3.1 over the last edge); float32 sums in float32.
+  * ``check_predecessors`` -- what any valid predecessor matrix satisfies: -1 exactly on the
+                         diagonal and unreachable pairs, a real last edge that is tight
+                         (d[i, p] + w[p, j] = d[i, j]), and walks back to the source whose
+                         edge costs re-sum to d[i, j] (the path recovery of Sec. 2).
   * ``reachability``  -- the transitive closure by breadth-first search (which pairs are
                          connected at all; needs no arithmetic).
   * ``check_invariants`` -- properties every closed distance matrix has: zero diagonal,
@@ -67,6 +76,13 @@ def _bind(lib):
     lib.oracle_minplus_f64.argtypes = [f64p, f64p, f64p, I64, I64, I64, INT]
     lib.oracle_dijkstra_rows_i64.argtypes = [i64p, I64, I64, i64p, I64, i64p, INT]
     lib.oracle_dijkstra_rows_f64.argtypes = [f64p, I64, i64p, I64, f64p, INT]
+    f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+    lib.oracle_fw_pred_i64.argtypes = [i64p, i64p, I64, I64]
+    lib.oracle_fw_pred_f64.argtypes = [f64p, i64p, I64]
+    lib.oracle_last_hop_i64.argtypes = [i64p, i64p, i64p, I64, I64, INT]
+    lib.oracle_last_hop_f32.argtypes = [f32p, f32p, i64p, I64, INT]
+    for f in ("oracle_fw_pred_i64", "oracle_fw_pred_f64", "oracle_last_hop_i64", "oracle_last_hop_f32"):
+        getattr(lib, f).restype = None
     lib.oracle_openmp_enabled.restype = INT
     for f in ("oracle_fw_i64", "oracle_fw_f64", "oracle_fw_i64_steps", "oracle_fw_f64_steps", "oracle_minplus_i64", "oracle_minplus_f64",
               "oracle_dijkstra_rows_i64", "oracle_dijkstra_rows_f64"):
@@ -162,6 +178,93 @@ def dijkstra_rows(w: np.ndarray, sources, inf: int = INF_I32, threads: int | Non
     out = np.empty((len(src), n), np.float64)
     lib.oracle_dijkstra_rows_f64(W, n, src, len(src), out, _threads(threads))
     return out
+
+
+def fw_pred(h: np.ndarray, inf: int = INF_I32, lib=None):
+    """(d, pred) by Eq. 1 with the predecessor indices of Sec. 2 (single thread)."""
+    lib = lib or load()
+    h = np.asarray(h)
+    n = h.shape[0]
+    pred = np.empty((n, n), np.int64)
+    if h.dtype.kind in "iu":
+        d = np.ascontiguousarray(h, dtype=np.int64).copy()
+        lib.oracle_fw_pred_i64(d, pred, n, int(inf))
+        return (d.astype(np.int32) if h.dtype == np.int32 else d), pred.astype(np.int32)
+    d = np.ascontiguousarray(h, dtype=np.float64).copy()
+    lib.oracle_fw_pred_f64(d, pred, n)
+    return d, pred.astype(np.int32)
+
+
+def last_hop(d: np.ndarray, w: np.ndarray, inf: int = INF_I32, threads: int | None = None, lib=None) -> np.ndarray:
+    """pred[i, j] = smallest k != j minimising d[i, k] + w[k, j]; -1 on the diagonal and where
+    j is unreachable.  Integers: exact (int64), entries >= inf missing.  float32: the sums are
+    formed in float32 (d and w are taken as float32), +inf missing."""
+    lib = lib or load()
+    n = d.shape[0]
+    pred = np.empty((n, n), np.int64)
+    if d.dtype.kind in "iu":
+        D = np.ascontiguousarray(np.minimum(d.astype(np.int64), inf))
+        W = np.ascontiguousarray(np.minimum(w.astype(np.int64), inf))
+        lib.oracle_last_hop_i64(D, W, pred, n, int(inf), _threads(threads))
+    else:
+        D = np.ascontiguousarray(d, dtype=np.float32)
+        W = np.ascontiguousarray(w, dtype=np.float32)
+        lib.oracle_last_hop_f32(D, W, pred, n, _threads(threads))
+    return pred.astype(np.int32)
+
+
+def check_predecessors(pred: np.ndarray, d: np.ndarray, h: np.ndarray, inf: int = INF_I32, rtol: float = 0.0,
+                       rows=None) -> list[str]:
+    """Violations of the properties every valid predecessor matrix of the closure d of h has.
+
+    For each checked source row i (all rows, or ``rows``): pred[i, i] = -1; pred[i, j] = -1
+    exactly where j is unreachable; otherwise p = pred[i, j] is a vertex != j with an edge
+    p -> j and d[i, p] + w[p, j] = d[i, j] (within rtol for floats); and walking back from
+    every j reaches i within n steps along edges whose costs sum to d[i, j].
+    """
+    bad = []
+    n = h.shape[0]
+    isint = h.dtype.kind in "iu"
+    W = np.minimum(h.astype(np.int64), inf) if isint else h.astype(np.float64)
+    D = d.astype(np.int64) if isint else d.astype(np.float64)
+    P = np.asarray(pred).astype(np.int64)
+    fin = (lambda a: a < inf) if isint else np.isfinite
+    close = (lambda a, b: a == b) if isint else (lambda a, b: np.abs(a - b) <= rtol * np.abs(b))
+    for i in (range(n) if rows is None else rows):
+        reach = fin(D[i])
+        reach[i] = False
+        p = P[i]
+        if p[i] != -1:
+            bad.append(f"pred[{i},{i}] != -1")
+        if np.any(p[~reach] != -1):
+            bad.append(f"row {i}: unreachable or diagonal entry with a predecessor")
+        js = np.nonzero(reach)[0]
+        if js.size == 0:
+            continue
+        pj = p[js]
+        if np.any((pj < 0) | (pj >= n) | (pj == js)):
+            bad.append(f"row {i}: predecessor out of range or equal to its vertex")
+            continue
+        wl = W[pj, js]
+        if not np.all(fin(wl)):
+            bad.append(f"row {i}: predecessor without an edge to its vertex")
+            continue
+        if not np.all(close(D[i, pj] + wl, D[i, js])):
+            bad.append(f"row {i}: last edge not tight (d[i,p] + w[p,j] != d[i,j])")
+            continue
+        cur, cost = js.copy(), np.zeros(js.size, W.dtype)
+        for _ in range(n):
+            live = cur != i
+            if not live.any():
+                break
+            prev = P[i, cur[live]]
+            cost[live] += W[prev, cur[live]]
+            cur[live] = prev
+        if np.any(cur != i):
+            bad.append(f"row {i}: a predecessor walk does not reach the source")
+        elif not np.all(close(cost, D[i, js])):
+            bad.append(f"row {i}: a walked path's cost differs from d[i,j]")
+    return bad
 
 
 def edge_mask(h: np.ndarray, inf: int = INF_I32) -> np.ndarray:

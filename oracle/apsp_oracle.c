@@ -16,6 +16,14 @@
  *   - oracle_minplus_i64 / oracle_minplus_f64: the (min,+) product of Eq. 2,
  *       Z[i,j] = min_k ( X[i,k] + Y[k,j] ),
  *     as a triple loop, optionally folded into an existing Z (Z = min(Z, X (x) Y)).
+ *   - oracle_fw_pred_i64 / _f64: Eq. 1 with the predecessor indices of Sec. 2: pred[i][j]
+ *     starts as i where the edge i -> j exists and, whenever the path through k shortens
+ *     d[i][j], becomes pred[k][j], the vertex before j on the path from k.
+ *   - oracle_last_hop_i64 / _f32: the predecessor matrix by its plain definition from a closed
+ *     d and the costs w: pred[i][j] = the smallest k != j minimising d[i][k] + w[k][j] (the
+ *     argmin of Sec. 3.1 restricted to the last edge), -1 on the diagonal and where the
+ *     minimum is unreachable.  The float32 variant adds in float32 (one rounding per sum),
+ *     the precision in which the library takes the same decision.
  *   - oracle_dijkstra_rows_i64 / _f64: single-source shortest paths from selected sources by
  *     textbook O(n^2) array Dijkstra (valid because every weight is >= 0; Sec. 3.1 assumes
  *     no negative cycles and the generator draws costs >= 0, Sec. 3.4).  It is a second,
@@ -222,4 +230,91 @@ void oracle_dijkstra_rows_f64(const double *w, int64_t n, const int64_t *src, in
     }
     free(done);
   }
+}
+
+/* Eq. 1 with predecessor indices (Sec. 2), int64 with threshold inf; d is closed in place like
+ * oracle_fw_i64 and pred (n x n) receives the predecessor of j on the path found from i. */
+void oracle_fw_pred_i64(int64_t *d, int64_t *pred, int64_t n, int64_t inf) {
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j) {
+      if (d[i * n + j] >= inf) d[i * n + j] = inf;
+      if (i == j) d[i * n + j] = 0;
+      pred[i * n + j] = (i != j && d[i * n + j] < inf) ? i : -1;
+    }
+  for (int64_t k = 0; k < n; ++k)
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t dik = d[i * n + k];
+      if (dik >= inf) continue;
+      for (int64_t j = 0; j < n; ++j) {
+        const int64_t dkj = d[k * n + j];
+        if (dkj >= inf) continue;
+        if (dik + dkj < d[i * n + j]) {
+          d[i * n + j] = dik + dkj;
+          pred[i * n + j] = pred[k * n + j];
+        }
+      }
+    }
+}
+
+void oracle_fw_pred_f64(double *d, int64_t *pred, int64_t n) {
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j) {
+      if (i == j) d[i * n + j] = 0.0;
+      pred[i * n + j] = (i != j && !isinf(d[i * n + j])) ? i : -1;
+    }
+  for (int64_t k = 0; k < n; ++k)
+    for (int64_t i = 0; i < n; ++i) {
+      const double dik = d[i * n + k];
+      if (isinf(dik)) continue;
+      for (int64_t j = 0; j < n; ++j)
+        if (dik + d[k * n + j] < d[i * n + j]) {
+          d[i * n + j] = dik + d[k * n + j];
+          pred[i * n + j] = pred[k * n + j];
+        }
+    }
+}
+
+/* pred[i][j] = smallest k != j minimising d[i][k] + w[k][j] over int64 (entries >= inf are
+ * unreachable / missing); -1 when i == j or no finite sum stays below inf. */
+void oracle_last_hop_i64(const int64_t *d, const int64_t *w, int64_t *pred, int64_t n, int64_t inf,
+                         int threads) {
+  set_threads(threads);
+#pragma omp parallel for schedule(static) if (threads > 1)
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j) {
+      int64_t best = inf, arg = -1;
+      if (i != j)
+        for (int64_t k = 0; k < n; ++k) {
+#if ORACLE_PLANT != 6 /* plant 6: let j be its own last hop */
+          if (k == j) continue;
+#endif
+          const int64_t dik = d[i * n + k];
+#if ORACLE_PLANT == 5 /* plant 5: transposed cost, w[j][k] */
+          const int64_t wkj = w[j * n + k];
+#else
+          const int64_t wkj = w[k * n + j];
+#endif
+          if (dik >= inf || wkj >= inf) continue;
+          if (dik + wkj < best) { best = dik + wkj; arg = k; }
+        }
+      pred[i * n + j] = arg;
+    }
+}
+
+/* The same over float32 sums (round to nearest); +infinity = unreachable / missing. */
+void oracle_last_hop_f32(const float *d, const float *w, int64_t *pred, int64_t n, int threads) {
+  set_threads(threads);
+#pragma omp parallel for schedule(static) if (threads > 1)
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j) {
+      float best = INFINITY;
+      int64_t arg = -1;
+      if (i != j)
+        for (int64_t k = 0; k < n; ++k) {
+          if (k == j) continue;
+          const float s = d[i * n + k] + w[k * n + j];
+          if (s < best) { best = s; arg = k; }
+        }
+      pred[i * n + j] = arg;
+    }
 }
