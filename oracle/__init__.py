@@ -79,8 +79,8 @@ def _bind(lib):
     f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
     lib.oracle_fw_pred_i64.argtypes = [i64p, i64p, I64, I64]
     lib.oracle_fw_pred_f64.argtypes = [f64p, i64p, I64]
-    lib.oracle_last_hop_i64.argtypes = [i64p, i64p, i64p, I64, I64, INT]
-    lib.oracle_last_hop_f32.argtypes = [f32p, f32p, i64p, I64, INT]
+    lib.oracle_last_hop_i64.argtypes = [i64p, i64p, i64p, I64, i64p, I64, I64, INT]
+    lib.oracle_last_hop_f32.argtypes = [f32p, f32p, i64p, I64, i64p, I64, INT]
     for f in ("oracle_fw_pred_i64", "oracle_fw_pred_f64", "oracle_last_hop_i64", "oracle_last_hop_f32"):
         getattr(lib, f).restype = None
     lib.oracle_openmp_enabled.restype = INT
@@ -195,21 +195,26 @@ def fw_pred(h: np.ndarray, inf: int = INF_I32, lib=None):
     return d, pred.astype(np.int32)
 
 
-def last_hop(d: np.ndarray, w: np.ndarray, inf: int = INF_I32, threads: int | None = None, lib=None) -> np.ndarray:
+def last_hop(d: np.ndarray, w: np.ndarray, inf: int = INF_I32, threads: int | None = None, lib=None,
+             rows=None) -> np.ndarray:
     """pred[i, j] = smallest k != j minimising d[i, k] + w[k, j]; -1 on the diagonal and where
     j is unreachable.  Integers: exact (int64), entries >= inf missing.  float32: the sums are
-    formed in float32 (d and w are taken as float32), +inf missing."""
+    formed in float32 (d and w are taken as float32), +inf missing.  With ``rows`` only those
+    source rows are computed and returned (len(rows) x n); d may then hold just those rows."""
     lib = lib or load()
-    n = d.shape[0]
-    pred = np.empty((n, n), np.int64)
-    if d.dtype.kind in "iu":
+    n = w.shape[0]
+    src = np.arange(n, dtype=np.int64) if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    if d.shape[0] != len(src):
+        d = d[src]
+    pred = np.empty((len(src), n), np.int64)
+    if w.dtype.kind in "iu":
         D = np.ascontiguousarray(np.minimum(d.astype(np.int64), inf))
         W = np.ascontiguousarray(np.minimum(w.astype(np.int64), inf))
-        lib.oracle_last_hop_i64(D, W, pred, n, int(inf), _threads(threads))
+        lib.oracle_last_hop_i64(D, W, pred, n, src, len(src), int(inf), _threads(threads))
     else:
         D = np.ascontiguousarray(d, dtype=np.float32)
         W = np.ascontiguousarray(w, dtype=np.float32)
-        lib.oracle_last_hop_f32(D, W, pred, n, _threads(threads))
+        lib.oracle_last_hop_f32(D, W, pred, n, src, len(src), _threads(threads))
     return pred.astype(np.int32)
 
 

@@ -275,12 +275,14 @@ void oracle_fw_pred_f64(double *d, int64_t *pred, int64_t n) {
 }
 
 /* pred[i][j] = smallest k != j minimising d[i][k] + w[k][j] over int64 (entries >= inf are
- * unreachable / missing); -1 when i == j or no finite sum stays below inf. */
-void oracle_last_hop_i64(const int64_t *d, const int64_t *w, int64_t *pred, int64_t n, int64_t inf,
-                         int threads) {
+ * unreachable / missing); -1 when i == j or no finite sum stays below inf.  Only the source
+ * rows rows[0..nrows) are computed: d and pred hold those rows (nrows x n), w is n x n. */
+void oracle_last_hop_i64(const int64_t *d, const int64_t *w, int64_t *pred, int64_t n, const int64_t *rows,
+                         int64_t nrows, int64_t inf, int threads) {
   set_threads(threads);
 #pragma omp parallel for schedule(static) if (threads > 1)
-  for (int64_t i = 0; i < n; ++i)
+  for (int64_t r = 0; r < nrows; ++r) {
+    const int64_t i = rows[r];
     for (int64_t j = 0; j < n; ++j) {
       int64_t best = inf, arg = -1;
       if (i != j)
@@ -288,7 +290,7 @@ void oracle_last_hop_i64(const int64_t *d, const int64_t *w, int64_t *pred, int6
 #if ORACLE_PLANT != 6 /* plant 6: let j be its own last hop */
           if (k == j) continue;
 #endif
-          const int64_t dik = d[i * n + k];
+          const int64_t dik = d[r * n + k];
 #if ORACLE_PLANT == 5 /* plant 5: transposed cost, w[j][k] */
           const int64_t wkj = w[j * n + k];
 #else
@@ -297,24 +299,28 @@ void oracle_last_hop_i64(const int64_t *d, const int64_t *w, int64_t *pred, int6
           if (dik >= inf || wkj >= inf) continue;
           if (dik + wkj < best) { best = dik + wkj; arg = k; }
         }
-      pred[i * n + j] = arg;
+      pred[r * n + j] = arg;
     }
+  }
 }
 
 /* The same over float32 sums (round to nearest); +infinity = unreachable / missing. */
-void oracle_last_hop_f32(const float *d, const float *w, int64_t *pred, int64_t n, int threads) {
+void oracle_last_hop_f32(const float *d, const float *w, int64_t *pred, int64_t n, const int64_t *rows,
+                         int64_t nrows, int threads) {
   set_threads(threads);
 #pragma omp parallel for schedule(static) if (threads > 1)
-  for (int64_t i = 0; i < n; ++i)
+  for (int64_t r = 0; r < nrows; ++r) {
+    const int64_t i = rows[r];
     for (int64_t j = 0; j < n; ++j) {
       float best = INFINITY;
       int64_t arg = -1;
       if (i != j)
         for (int64_t k = 0; k < n; ++k) {
           if (k == j) continue;
-          const float s = d[i * n + k] + w[k * n + j];
+          const float s = d[r * n + k] + w[k * n + j];
           if (s < best) { best = s; arg = k; }
         }
-      pred[i * n + j] = arg;
+      pred[r * n + j] = arg;
     }
+  }
 }

@@ -177,3 +177,13 @@ def test_check_predecessors_rejects_broken_matrices():
 def test_pred_pins_catch_planted_mistakes(plant):
     """A transposed cost (w[j][k]) and a last hop allowed to be j itself must each fail."""
     assert not _last_hop_pins_pass(oracle.load(plant=plant), trials=30)
+
+
+def test_last_hop_rows_subset_equals_full():
+    h = workloads.er_graph(150, 0.05, "int32", lo=1, hi=100, seed=8)
+    d = oracle.fw(h)
+    rows = [0, 7, 149]
+    assert np.array_equal(oracle.last_hop(d, h, rows=rows), oracle.last_hop(d, h)[rows])
+    hf = workloads.er_graph(150, 0.05, "float32", dist="lognormal", lo=0.0, hi=1.0, seed=8)
+    df = oracle.fw(hf).astype(np.float32)
+    assert np.array_equal(oracle.last_hop(df[rows], hf, rows=rows), oracle.last_hop(df, hf)[rows])
