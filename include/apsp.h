@@ -168,6 +168,31 @@ int apsp_batched(void *pool, const int64_t *offsets, const int32_t *ns, const in
                  const int32_t *order, const int32_t *ns_host, int64_t count, int dtype,
                  const void *inf, void *ws, size_t ws_bytes, void *stream);
 
+/* ---- predecessors and path reconstruction (pred[i, j] of Sec. 2; the argmin of Sec. 3.1) --
+ * pred (n x n int32, leading dimension ldp) receives, for each pair, the vertex just before j
+ * on a shortest i -> j path:
+ *     pred[i][j] = the smallest k != j minimising d[i][k] + w[k][j]
+ * where d (ldd) is the CLOSED distance matrix (the output of apsp_fw, apsp_rkleene or
+ * apsp_batched) and w (ldw) the cost matrix it was closed from; w's diagonal is never used and
+ * its entries >= inf count as missing edges.  pred[i][i] = -1, and pred[i][j] = -1 where j is
+ * unreachable from i.  Walking back from j (p = pred[i][j], then pred[i][p], ...) reaches i and
+ * spells out a shortest path whose edge costs sum to d[i][j] (int32 exactly) -- guaranteed
+ * when every off-diagonal weight is positive, the assumption of Sec. 3.1.  With zero-cost
+ * edges each pred entry is still a last hop of some shortest path, but a walk may cycle
+ * through a zero-cost loop.  Negative entries or NaN in d or w set APSP_ERR_DOMAIN.
+ * int32: sums are exact and ties go to the smallest k.  When pred is 16-byte aligned with ldp
+ * a multiple of 4, the argmin runs as one (min,+) product of encoded copies of d and w
+ * (index bits below the value bits) on the tropical GEMM engine, provided the encoded sums fit
+ * below 0x3FFFFFFF (checked on the device); otherwise a direct argmin kernel runs.  The
+ * workspace (apsp_predecessors_workspace_bytes) holds the bound words and the two encoded
+ * copies (2 x n x round_up(n, 4) int32).
+ * float32: the direct kernel, with each sum rounded once (round to nearest) and ties to the
+ * smallest k; the workspace is only the 256 bytes of bound words. */
+size_t apsp_predecessors_workspace_bytes(int64_t n, int dtype);
+int apsp_predecessors(const void *d, int64_t ldd, const void *w, int64_t ldw, int32_t *pred,
+                      int64_t ldp, int64_t n, int dtype, const void *inf, void *ws,
+                      size_t ws_bytes, void *stream);
+
 /* ---- a8: the planner's cost-model network ---------------------------------------------
  * A perceptron with two hidden layers of 64 ReLU units, fp32, that predicts the log run time
  * of a closure configuration from a feature vector of in_dim (1..32) floats:

@@ -51,6 +51,8 @@ def _load():
         "apsp_rkleene_workspace_bytes": ([i64, i64, i32, i32], sz),
         "apsp_rkleene": ([vp, i64, i64, i32, vp, i32, vp, sz, vp], i32),
         "apsp_probe_minplus": ([i32, i32, i32, i32, vp, vp], i32),
+        "apsp_predecessors_workspace_bytes": ([i64, i32], sz),
+        "apsp_predecessors": ([vp, i64, vp, i64, vp, i64, i64, i32, vp, vp, sz, vp], i32),
         "apsp_batched_workspace_bytes": ([i64], sz),
         "apsp_batched": ([vp, vp, vp, vp, vp, vp, i64, i32, vp, vp, sz, vp], i32),
         "apsp_mlp_param_count": ([i32], i64),
@@ -74,6 +76,7 @@ _lib = _load()
 EXPORTS = ("apsp_version", "apsp_status_str", "apsp_device_status", "apsp_normalise",
            "tropical_gemm_workspace_bytes", "tropical_gemm",
            "apsp_fw_workspace_bytes", "apsp_fw", "apsp_rkleene_workspace_bytes", "apsp_rkleene",
+           "apsp_predecessors_workspace_bytes", "apsp_predecessors",
            "apsp_probe_minplus", "apsp_trace_enable", "apsp_trace_read", "apsp_batched_workspace_bytes",
            "apsp_batched", "apsp_mlp_param_count", "apsp_mlp_backward_workspace_bytes", "apsp_mlp_forward",
            "apsp_mlp_loss", "apsp_mlp_backward", "apsp_mlp_adam")
@@ -185,6 +188,56 @@ def apsp_rkleene(d: torch.Tensor, inf=None, cutoff: int = 0, ws: torch.Tensor | 
     """Close d in place by R-Kleene (Sec. 3.3) with blocked-FW leaves of <= cutoff vertices."""
     return _closure(_lib.apsp_rkleene, _lib.apsp_rkleene_workspace_bytes, d, inf, cutoff, ws, stream,
                     "apsp_rkleene")
+
+
+def apsp_predecessors_workspace_bytes(n: int, dtype=torch.int32) -> int:
+    return _lib.apsp_predecessors_workspace_bytes(n, APSP_I32 if dtype == torch.int32 else APSP_F32)
+
+
+def apsp_predecessors(d: torch.Tensor, w: torch.Tensor, pred: torch.Tensor | None = None, inf=None,
+                      ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """pred[i][j] = the vertex before j on a shortest i -> j path (-1 on the diagonal and for
+    unreachable pairs), from the closed matrix d and the cost matrix w it was closed from."""
+    n = d.shape[0]
+    if tuple(d.shape) != (n, n) or tuple(w.shape) != (n, n):
+        raise ValueError("d and w must be n x n")
+    if w.dtype != d.dtype:
+        raise TypeError("d and w must share a dtype")
+    code = _dtype_code(d)
+    if pred is None:
+        pred = torch.empty((n, n), dtype=torch.int32, device=d.device)
+    if pred.dtype != torch.int32 or tuple(pred.shape) != (n, n):
+        raise ValueError("pred must be an n x n int32 tensor")
+    pd, ldd = _mat(d, "d")
+    pw, ldw = _mat(w, "w")
+    pp, ldp = _mat(pred, "pred")
+    ip, _keep = _inf_arg(inf, code)
+    wp, wb = (None, 0) if ws is None else (ws.data_ptr(), ws.numel() * ws.element_size())
+    _check(_lib.apsp_predecessors(pd, ldd, pw, ldw, pp, ldp, n, code, ip, wp, wb, _stream(stream)),
+           "apsp_predecessors")
+    return pred
+
+
+def path(pred, i: int, j: int) -> list[int] | None:
+    """Vertices of the shortest i -> j path spelled out by a predecessor matrix (host array or
+    CPU tensor), or None when j is unreachable from i.  Raises if the walk does not reach i
+    within n steps (possible only with zero-cost cycles)."""
+    pred = np.asarray(pred)
+    n = pred.shape[0]
+    if i == j:
+        return [i]
+    if pred[i, j] < 0:
+        return None
+    out = [j]
+    v = j
+    for _ in range(n):
+        v = int(pred[i, v])
+        if v < 0:
+            raise ValueError(f"broken predecessor chain {i} -> {j}")
+        out.append(v)
+        if v == i:
+            return out[::-1]
+    raise ValueError(f"predecessor walk {i} -> {j} did not reach {i} in {n} steps")
 
 
 def apsp_probe_minplus(variant: int, blocks: int, threads: int, iters: int, sink: torch.Tensor, stream=None):
@@ -348,21 +401,25 @@ def apsp_mlp_adam(params, grads, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-
 ALGOS = {"fw": apsp_fw, "rkleene": apsp_rkleene}
 
 
-def solve(h, algo: str = "fw", inf=None, param: int = 0, device=None, out=None):
+def solve(h, algo: str = "fw", inf=None, param: int = 0, device=None, out=None, predecessors: bool = False):
     """End-to-end solve of a HOST cost matrix (numpy array or CPU tensor): copy it to the
     device, close it there, copy the distances back.  Returns a CPU tensor (``out`` if given,
-    pinned memory recommended)."""
+    pinned memory recommended); with predecessors=True, a pair (distances, pred) where pred is
+    the int32 predecessor matrix of apsp_predecessors (walk it with ``path``)."""
     t = torch.as_tensor(h)
     dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
     d = t.to(dev, non_blocking=True)
+    w = d.clone() if predecessors else None
     if algo == "fw":
         apsp_fw(d, inf=inf, tile=param)
     elif algo == "rkleene":
         apsp_rkleene(d, inf=inf, cutoff=param)
     else:
         raise ValueError(f"unknown algorithm {algo!r}")
+    pred = apsp_predecessors(d, w, inf=inf).cpu() if predecessors else None
     if out is None:
-        return d.cpu()
-    out.copy_(d, non_blocking=True)
-    torch.cuda.current_stream(dev).synchronize()
-    return out
+        out = d.cpu()
+    else:
+        out.copy_(d, non_blocking=True)
+        torch.cuda.current_stream(dev).synchronize()
+    return (out, pred) if predecessors else out

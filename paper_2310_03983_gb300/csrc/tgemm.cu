@@ -6,10 +6,11 @@
 // (Sec. 3.1); that costs n^3 memory and capped its graphs at 1000 vertices.  Here the same
 // reduction is blocked so that nothing but the n x n operands ever lives in HBM:
 //
-//  * A persistent grid (one CTA per SM, 288 threads) walks a list of 128 x 128 output tiles.
-//  * Warp 8 is the producer: one elected lane issues TMA copies of the 128 x 32 A slab and
-//    the 32 x 128 B slab of each k-step into a 4-stage shared-memory ring (mbarrier
-//    full/empty handshakes), and, when folding into an existing C, the 128 x 128 C tile.
+//  * A persistent grid (one CTA per SM, 384 threads) walks a list of 128 x 128 output tiles.
+//  * Warps 8-11 are the producer warpgroup: one lane of warp 8 issues TMA copies of the
+//    128 x 32 A slab and the 32 x 128 B slab of each k-step into a 4-stage shared-memory
+//    ring (mbarrier full/empty handshakes), and, when folding into an existing C, the
+//    128 x 128 C tile.
 //  * Warps 0-7 are consumers: each thread owns an 8 x 8 register tile of C (rows
 //    tm + 16 i, columns 4 tn + q + 64 h), reads A as 128-bit row quads (a broadcast within
 //    each quarter-warp) and B as 128-bit column quads (eight lanes cover 32 banks), and
@@ -163,6 +164,7 @@ template <typename S, int MODE, bool ACC>
 __global__ void __launch_bounds__(kThreads, 1)
     tgemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
                  const __grid_constant__ CUtensorMap mC, const TileProblem p) {
+  if (p.skip && *p.skip) return;  // uniform across the grid, before any barrier exists
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   int *sA = reinterpret_cast<int *>(smem);

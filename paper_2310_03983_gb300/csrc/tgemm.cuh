@@ -43,6 +43,9 @@ struct TileProblem {
   // largest finite entries of A and B).
   const int *wmax;
   int64_t wmult;
+  // Optional device word (may be null): when it holds a non-zero value at launch time every
+  // CTA returns at once, so a later kernel can take over the product (predecessors).
+  const int *skip;
 };
 
 // Launch one tile pass.  acc: fold into the existing C (min) instead of overwriting it.
