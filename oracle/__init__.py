@@ -10,6 +10,8 @@ What is here, each citing the passage it follows:
                          int64 for int32 inputs and fp64 for float32 inputs; ``fw_steps`` runs
                          the same loop over a range of intermediate vertices.
   * ``minplus``       -- Eq. 2 (Sec. 3), the (min,+) product, as a triple loop in C.
+  * ``squaring``      -- the paper's "Floyd-Warshall on GPU" (Sec. 3.2): H <- H (x) H with
+                         ``minplus`` until nothing changes (or a given number of products).
   * ``dijkstra_rows`` -- single-source distances from chosen sources by array Dijkstra: an
                          independent algorithm for the same definition, used to check large
                          matrices row by row.
@@ -161,6 +163,28 @@ def minplus(x: np.ndarray, y: np.ndarray, z: np.ndarray | None = None, inf: int 
     Z = np.full((M, N), np.inf) if z is None else np.ascontiguousarray(z, dtype=np.float64).copy()
     lib.oracle_minplus_f64(Z, X, Y, M, N, K, int(z is not None))
     return Z
+
+
+def squaring(h: np.ndarray, inf: int = INF_I32, max_iters: int | None = None, lib=None):
+    """Sec. 3.2: repeat the (min,+) product of Eq. 2 of the matrix with itself until it stops
+    changing, or for at most ``max_iters`` products.  Returns (d, number of products that
+    changed something).  The diagonal is set to 0 first (a self-loop costs nothing)."""
+    h = np.asarray(h)
+    isint = h.dtype.kind in "iu"
+    d = np.minimum(h.astype(np.int64), inf) if isint else h.astype(np.float64)
+    np.fill_diagonal(d, 0)
+    changed = 0
+    t = 0
+    while max_iters is None or t < max_iters:
+        nxt = minplus(d, d, inf=inf, lib=lib)
+        t += 1
+        if np.array_equal(nxt, d):
+            break
+        d = nxt
+        changed += 1
+    if isint and h.dtype == np.int32:
+        d = d.astype(np.int32)
+    return d, changed
 
 
 def dijkstra_rows(w: np.ndarray, sources, inf: int = INF_I32, threads: int | None = None,

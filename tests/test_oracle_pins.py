@@ -264,3 +264,37 @@ def test_pins_catch_planted_mistakes(plant):
     """Each compiled-in mistake (no zero diagonal, k innermost, swapped index, transposed
     product operand) must make the pins fail."""
     assert not _pins_pass(oracle.load(plant=plant))
+
+
+def test_squaring_reaches_eq1_closure():
+    """Sec. 3.2's repeated squaring ends at the same closure as Eq. 1."""
+    rng = np.random.default_rng(21)
+    for trial in range(30):
+        n = int(rng.integers(1, 40))
+        h = _rand_graph(rng, n, float(rng.uniform(0.05, 0.6)), np.int32)
+        d, _ = oracle.squaring(h)
+        assert np.array_equal(d, oracle.fw(h)), trial
+    hf = workloads.er_graph(70, 0.05, "float32", dist="lognormal", lo=0.0, hi=1.0, seed=21)
+    df, _ = oracle.squaring(hf)
+    want = oracle.fw(hf)
+    assert np.array_equal(np.isinf(df), np.isinf(want))
+    f = np.isfinite(want)
+    assert np.allclose(df[f], want[f], rtol=1e-12)
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 9, 17, 40])
+def test_squaring_on_a_path_closed_form(n):
+    """On the directed path 0 -> 1 -> ... -> n-1, t products reach exactly the pairs j - i <= 2^t
+    (a shortest walk of at most 2^t edges), so ceil(log2(n - 1)) products change something and
+    the next one does not."""
+    h = np.full((n, n), INF, np.int32)
+    np.fill_diagonal(h, 0)
+    for v in range(n - 1):
+        h[v, v + 1] = 1
+    need = int(np.ceil(np.log2(n - 1))) if n > 2 else 0
+    assert oracle.squaring(h)[1] == need
+    for t in range(need + 1):
+        d, _ = oracle.squaring(h, max_iters=t)
+        i, j = np.indices((n, n))
+        want = np.where((j >= i) & (j - i <= 2 ** t), j - i, INF)
+        assert np.array_equal(d, want), t
