@@ -131,6 +131,22 @@ size_t apsp_rkleene_workspace_bytes(int64_t n, int64_t ld, int dtype, int cutoff
 int apsp_rkleene(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int cutoff,
                  void *ws, size_t ws_bytes, void *stream);
 
+/* ---- the paper's "Floyd-Warshall on GPU" (Sec. 3.2): repeated (min,+) squaring ----------
+ * Closes d in place by D <- D (x) D (Eq. 2) until no entry changes.  After t products D[i][j]
+ * is the shortest path of at most 2^t edges, so max_iters = 0 selects ceil(log2(n - 1))
+ * products, which always reach the closure; the loop stops doing work after the first product
+ * that changes nothing (checked on the device, so nothing waits on the host).  A positive
+ * max_iters caps the number of products (at most 48); with fewer than needed the result holds
+ * the shortest paths of at most 2^max_iters edges.  Runs a1 first.  Costs n^3 (min,+) pairs per
+ * product: O(n^3 log n) in the worst case against Floyd-Warshall's n^3, but only a few products
+ * for graphs of small diameter.  d must be 16-byte aligned.  The workspace holds the 256 bytes
+ * of bound words, the product matrix (n x round_up(n, 4) elements) and, when ld is not a
+ * multiple of 4, an aligned copy of d.  int32 results equal apsp_fw's exactly; float32 results
+ * differ from them only in summation order. */
+size_t apsp_squaring_workspace_bytes(int64_t n, int64_t ld, int dtype);
+int apsp_squaring(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int max_iters,
+                  void *ws, size_t ws_bytes, void *stream);
+
 /* ---- R-Kleene with no device allocation ------------------------------------------------
  * The paper has no counterpart to this entry point.  It is apsp_rkleene for callers that
  * cannot call cudaMalloc -- code inside a framework or plugin host that owns all device

@@ -51,6 +51,8 @@ def _load():
         "apsp_rkleene_workspace_bytes": ([i64, i64, i32, i32], sz),
         "apsp_rkleene": ([vp, i64, i64, i32, vp, i32, vp, sz, vp], i32),
         "apsp_probe_minplus": ([i32, i32, i32, i32, vp, vp], i32),
+        "apsp_squaring_workspace_bytes": ([i64, i64, i32], sz),
+        "apsp_squaring": ([vp, i64, i64, i32, vp, i32, vp, sz, vp], i32),
         "apsp_predecessors_workspace_bytes": ([i64, i32], sz),
         "apsp_predecessors": ([vp, i64, vp, i64, vp, i64, i64, i32, vp, vp, sz, vp], i32),
         "apsp_batched_workspace_bytes": ([i64], sz),
@@ -76,7 +78,7 @@ _lib = _load()
 EXPORTS = ("apsp_version", "apsp_status_str", "apsp_device_status", "apsp_normalise",
            "tropical_gemm_workspace_bytes", "tropical_gemm",
            "apsp_fw_workspace_bytes", "apsp_fw", "apsp_rkleene_workspace_bytes", "apsp_rkleene",
-           "apsp_predecessors_workspace_bytes", "apsp_predecessors",
+           "apsp_squaring_workspace_bytes", "apsp_squaring", "apsp_predecessors_workspace_bytes", "apsp_predecessors",
            "apsp_probe_minplus", "apsp_trace_enable", "apsp_trace_read", "apsp_batched_workspace_bytes",
            "apsp_batched", "apsp_mlp_param_count", "apsp_mlp_backward_workspace_bytes", "apsp_mlp_forward",
            "apsp_mlp_loss", "apsp_mlp_backward", "apsp_mlp_adam")
@@ -188,6 +190,16 @@ def apsp_rkleene(d: torch.Tensor, inf=None, cutoff: int = 0, ws: torch.Tensor | 
     """Close d in place by R-Kleene (Sec. 3.3) with blocked-FW leaves of <= cutoff vertices."""
     return _closure(_lib.apsp_rkleene, _lib.apsp_rkleene_workspace_bytes, d, inf, cutoff, ws, stream,
                     "apsp_rkleene")
+
+
+def apsp_squaring_workspace_bytes(n: int, ld: int, dtype=torch.int32) -> int:
+    return _lib.apsp_squaring_workspace_bytes(n, ld, APSP_I32 if dtype == torch.int32 else APSP_F32)
+
+
+def apsp_squaring(d: torch.Tensor, inf=None, max_iters: int = 0, ws: torch.Tensor | None = None, stream=None):
+    """Close d in place by repeated (min,+) squaring until nothing changes (Sec. 3.2);
+    max_iters > 0 caps the number of products."""
+    return _closure(_lib.apsp_squaring, None, d, inf, max_iters, ws, stream, "apsp_squaring")
 
 
 def apsp_predecessors_workspace_bytes(n: int, dtype=torch.int32) -> int:
@@ -398,7 +410,7 @@ def apsp_mlp_adam(params, grads, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-
                               step, _stream(stream)), "apsp_mlp_adam")
 
 
-ALGOS = {"fw": apsp_fw, "rkleene": apsp_rkleene}
+ALGOS = {"fw": apsp_fw, "rkleene": apsp_rkleene, "squaring": apsp_squaring}
 
 
 def solve(h, algo: str = "fw", inf=None, param: int = 0, device=None, out=None, predecessors: bool = False):
@@ -414,6 +426,8 @@ def solve(h, algo: str = "fw", inf=None, param: int = 0, device=None, out=None, 
         apsp_fw(d, inf=inf, tile=param)
     elif algo == "rkleene":
         apsp_rkleene(d, inf=inf, cutoff=param)
+    elif algo == "squaring":
+        apsp_squaring(d, inf=inf, max_iters=param)
     else:
         raise ValueError(f"unknown algorithm {algo!r}")
     pred = apsp_predecessors(d, w, inf=inf).cpu() if predecessors else None
