@@ -1,8 +1,9 @@
 """a8: choosing how to close a graph -- exhaustive autotuning and a learned cost model.
 
 A closure can run as blocked Floyd-Warshall (many launches over all SMs), as R-Kleene with a
-leaf cutoff (Sec. 3.3), or on a single CTA in one launch (the batched kernel on a batch of one);
-which is fastest depends on the size and type of the graph.  Two planners pick the
+leaf cutoff (Sec. 3.3), as repeated (min,+) squaring (Sec. 3.2; a few products when the graph's
+diameter is small), or on a single CTA in one launch (the batched kernel on a batch of one);
+which is fastest depends on the size, density and type of the graph.  Two planners pick the
 configuration from the graph's features (vertex count, edge density, dtype):
 
 * ``Autotuner`` times every candidate on the GPU (median of a few runs) and keeps the fastest.
@@ -28,11 +29,12 @@ import numpy as np
 import torch
 
 from . import (apsp_close_cta, apsp_fw, apsp_mlp_adam, apsp_mlp_backward, apsp_mlp_forward, apsp_mlp_loss, apsp_mlp_param_count,
-               apsp_rkleene, apsp_rkleene_workspace_bytes, lib)
+               apsp_rkleene, apsp_rkleene_workspace_bytes, apsp_squaring, apsp_squaring_workspace_bytes, lib)
 
-CANDIDATES = (("fw", 0), ("rkleene", 128), ("rkleene", 256), ("rkleene", 512), ("rkleene", 1024), ("cta", 0))
+CANDIDATES = (("fw", 0), ("rkleene", 128), ("rkleene", 256), ("rkleene", 512), ("rkleene", 1024), ("cta", 0),
+              ("squaring", 0))
 CTA_MAX_N = 1024  # beyond this one SM is far too slow to be worth timing
-IN_DIM = 8
+IN_DIM = 9
 HIDDEN = 64
 
 
@@ -42,7 +44,8 @@ def features(n: int, density: float, dtype: str, algo: str, param: int) -> list[
     return [math.log2(max(n, 1)) / 15.0, float(density), 1.0 if dtype == "float32" else 0.0,
             1.0 if algo == "fw" else 0.0, 1.0 if rk else 0.0, 1.0 if algo == "cta" else 0.0,
             math.log2(param) / 11.0 if rk else 0.0,
-            (math.log2(max(n, 1)) - math.log2(param)) / 8.0 if rk and param else 0.0]
+            (math.log2(max(n, 1)) - math.log2(param)) / 8.0 if rk and param else 0.0,
+            1.0 if algo == "squaring" else 0.0]
 
 
 def applicable(n: int):
@@ -65,6 +68,8 @@ def run_config(d: torch.Tensor, algo: str, param: int, ws: torch.Tensor | None =
         apsp_fw(d, ws=ws)
     elif algo == "cta":
         apsp_close_cta(d)
+    elif algo == "squaring":
+        apsp_squaring(d, ws=ws)
     else:
         apsp_rkleene(d, cutoff=param, ws=ws)
 
@@ -72,8 +77,8 @@ def run_config(d: torch.Tensor, algo: str, param: int, ws: torch.Tensor | None =
 def time_config(d0: torch.Tensor, algo: str, param: int, reps: int = 3) -> float:
     """Median milliseconds of one closure of a fresh copy of d0 (CUDA events)."""
     n = d0.shape[0]
-    ws = torch.empty(max(256, apsp_rkleene_workspace_bytes(n, n, d0.dtype, param or 256)), dtype=torch.uint8,
-                     device=d0.device)
+    ws = torch.empty(max(256, apsp_rkleene_workspace_bytes(n, n, d0.dtype, param or 256),
+                         apsp_squaring_workspace_bytes(n, n, d0.dtype)), dtype=torch.uint8, device=d0.device)
     work = d0.clone()
     run_config(work, algo, param, ws)  # warm-up (first-launch set-up)
     out = []

@@ -252,6 +252,9 @@ class Server:
                 elif algo == "cta":
                     from . import apsp_close_cta
                     apsp_close_cta(v)
+                elif algo == "squaring":
+                    from . import apsp_squaring
+                    apsp_squaring(v)
                 else:
                     apsp_fw(v)
                 reqs = [r]
