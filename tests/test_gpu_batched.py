@@ -89,3 +89,24 @@ def test_batched_balanced_batch_runs_one_cta_per_graph(apsp):
     for g in (0, 299, 599):
         assert_dist_equal(b.graph(g, plain).cpu().numpy(), oracle.fw(mats[g]), f"graph {g}")
     assert apsp.apsp_device_status() == 0
+
+
+def test_paper_sweep_through_batched(apsp):
+    """The paper's 1000 generator graphs (Sec. 3.4, Sec. 4: V uniform in [4, 1000], rho uniform
+    in [0, 100], costs in [0, 100] including zero) closed in one apsp_batched call.  Every graph
+    of at most 320 vertices is compared with the oracle in full, plus the ten largest graphs on
+    32 sampled source rows each (Dijkstra), all bit-exact."""
+    ns, _, _, mats = workloads.paper_sweep(1000, seed=0)
+    batch = apsp.Batch(mats)
+    apsp.apsp_batched(batch)
+    out = batch.pool.cpu()
+    assert apsp.apsp_device_status() == 0
+    small = [g for g in range(len(mats)) if ns[g] <= 320]
+    assert len(small) > 250
+    for g in small:
+        assert_dist_equal(batch.graph(g, out).numpy(), oracle.fw(mats[g], threads=THREADS), f"graph {g} (n={ns[g]})")
+    rng = np.random.default_rng(5)
+    for g in np.argsort(ns)[-10:]:
+        rows = rng.choice(int(ns[g]), 32, replace=False)
+        got = batch.graph(int(g), out).numpy()[rows]
+        assert_dist_equal(got, oracle.dijkstra_rows(mats[g], rows, threads=THREADS), f"graph {g}")

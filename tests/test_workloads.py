@@ -40,3 +40,17 @@ def test_paper_generator():
     assert np.all(np.diagonal(h) == 0)
     w = h[h < workloads.INF_I32]
     assert w.min() >= 0 and w.max() <= 100
+
+
+def test_paper_sweep_shape_and_order():
+    ns, rhos, edges, mats = workloads.paper_sweep(count=60, seed=3)
+    assert len(mats) == 60 and all(m.shape == (n, n) for n, m in zip(ns, mats))
+    assert ns.min() >= 4 and ns.max() <= 1000 and rhos.min() >= 0 and rhos.max() <= 100
+    assert np.all(np.diff(edges) >= 0)  # ascending number of edges, as the paper orders them
+    for n, e, m in zip(ns, edges, mats):
+        assert np.all(np.diagonal(m) == 0)
+        fin = m[m < workloads.INF_I32]
+        assert fin.min() >= 0 and fin.max() <= 100
+        assert e == np.count_nonzero(m < workloads.INF_I32) - n
+    ns2, _, _, mats2 = workloads.paper_sweep(count=60, seed=3)
+    assert np.array_equal(ns, ns2) and all(np.array_equal(a, b) for a, b in zip(mats, mats2))

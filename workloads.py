@@ -16,7 +16,7 @@ Graph families:
   * paper_graph: the paper's generator f(V, rho, alpha) of Sec. 3.4: a uniform probability
     matrix P scaled by rho, a Bernoulli draw per entry, integer costs in [0, alpha], zero
     diagonal.  rho * P is clipped to [0, 1] (the paper's rho ~ U[0, 100] would otherwise give
-    "probabilities" above 1).
+    "probabilities" above 1).  paper_sweep draws the paper's 1000 such graphs (Sec. 4).
 """
 from __future__ import annotations
 
@@ -92,6 +92,22 @@ def paper_graph(V: int, rho: float, alpha: int = 100, seed: int = 0, inf: int = 
     H = np.where(A, rng.integers(0, alpha, size=(V, V), endpoint=True), inf).astype(np.int32)
     np.fill_diagonal(H, 0)
     return H
+
+
+def paper_sweep(count: int = 1000, v_lo: int = 4, v_hi: int = 1000, rho_hi: float = 100.0, alpha: int = 100,
+                seed: int = 0, threads: int | None = None):
+    """The paper's experiment inputs (Sec. 3.4 and Sec. 4): ``count`` graphs f(V, rho, alpha) with V
+    uniform on the integers [v_lo, v_hi], rho uniform in [0, rho_hi] and alpha = 100, sorted by
+    ascending number of edges as the paper sorts them.  Graph g of the draw is
+    paper_graph(V[g], rho[g], alpha, seed=2000 + g).  Returns (ns, rhos, edges, mats) in that order."""
+    rng = np.random.Generator(np.random.PCG64([int(seed), 0x53574550]))
+    Vs = rng.integers(v_lo, v_hi, size=count, endpoint=True)
+    rhos = rng.uniform(0.0, rho_hi, size=count)
+    with ThreadPoolExecutor(threads or min(16, os.cpu_count() or 1)) as ex:
+        mats = list(ex.map(lambda g: paper_graph(int(Vs[g]), float(rhos[g]), alpha, seed=2000 + g), range(count)))
+    edges = np.array([int(np.count_nonzero(m < INF_I32)) - m.shape[0] for m in mats], np.int64)
+    order = np.argsort(edges, kind="stable")
+    return (Vs[order].astype(np.int64), rhos[order], edges[order], [mats[g] for g in order])
 
 
 def batch_specs(count: int = 2048, n_lo: int = 32, n_hi: int = 1024, p_lo: float = 0.02,
