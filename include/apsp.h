@@ -94,9 +94,13 @@ int apsp_normalise(void *d, int64_t n, int64_t ld, int dtype, const void *inf, v
  * or B (APSP_ERR_ARG).  K = 0 gives C = inf (or leaves C unchanged when accumulating);
  * M = 0 or N = 0 is a no-op.  When every base is 16-byte aligned and every leading
  * dimension a multiple of 4, the TMA-fed engine runs; otherwise a plain-load kernel.
- * int32: when the largest finite entries of A and B sum below 2^24 the product runs in
- * exact fp32 arithmetic on the int32 bit patterns, else in int32; results are identical.
- * The workspace (tropical_gemm_workspace_bytes) holds those two maxima. */
+ * int32 arithmetic is chosen on the device from the largest finite entries of A and B (a
+ * scan): when they sum below 0x3FFF and the workspace has room for packed copies, the operands
+ * are packed into 16-bit pairs and each DPX operation performs two (min,+) pairs; else, below
+ * 2^24, exact fp32 arithmetic on the int32 bit patterns; else int32.  Results are identical.
+ * The workspace (tropical_gemm_workspace_bytes) holds the two maxima (256 bytes) and, for
+ * int32, the packed copies (M x round_up(ceil(K/2), 4) + ceil(K/2) x round_up(N, 4) words); a
+ * workspace of only 256 bytes is accepted and skips the 16-bit path. */
 size_t tropical_gemm_workspace_bytes(int64_t M, int64_t N, int64_t K, int dtype);
 int tropical_gemm(void *C, const void *A, const void *B, int64_t M, int64_t N, int64_t K,
                   int64_t lda, int64_t ldb, int64_t ldc, int dtype, const void *inf,

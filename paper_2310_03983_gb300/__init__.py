@@ -138,6 +138,10 @@ def apsp_normalise(d: torch.Tensor, inf=None, stream=None):
     return d
 
 
+def tropical_gemm_workspace_bytes(M: int, N: int, K: int, dtype=torch.int32) -> int:
+    return _lib.tropical_gemm_workspace_bytes(M, N, K, APSP_I32 if dtype == torch.int32 else APSP_F32)
+
+
 def tropical_gemm(C: torch.Tensor, A: torch.Tensor, B: torch.Tensor, accumulate: bool = False, inf=None,
                   ws: torch.Tensor | None = None, stream=None):
     """C = A (x) B, or C = min(C, A (x) B) when accumulate (Eq. 2)."""

@@ -79,6 +79,28 @@ template <> struct ProbeBody<5> {
 // (v * 2^-149), the form in which the library adds small integers exactly in fp32.
 template <> struct ProbeBody<6> : ProbeBody<5> {};
 
+// 7: packed int16 pairs, one fused DPX add-min over two 16-bit lanes per operation
+//    (__viaddmin_s16x2): 128 pairs per iteration instead of 64.
+template <> struct ProbeBody<7> {
+  typedef int T;
+  static __device__ __forceinline__ void run(int *c, int b0, int b1) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) c[j] = (int)__viaddmin_s16x2((unsigned)c[(j + 1) & 31], (unsigned)b0, (unsigned)c[j]);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) c[j] = (int)__viaddmin_s16x2((unsigned)c[(j + 3) & 31], (unsigned)b1, (unsigned)c[j]);
+  }
+};
+// 8: packed int16 pairs, SIMD add then SIMD min (__vadd2, __vmins2): 128 pairs per iteration.
+template <> struct ProbeBody<8> {
+  typedef int T;
+  static __device__ __forceinline__ void run(int *c, int b0, int b1) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) c[j] = (int)__vmins2((unsigned)c[j], __vadd2((unsigned)c[(j + 1) & 31], (unsigned)b0));
+#pragma unroll
+    for (int j = 0; j < 32; ++j) c[j] = (int)__vmins2((unsigned)c[j], __vadd2((unsigned)c[(j + 3) & 31], (unsigned)b1));
+  }
+};
+
 template <int V> __device__ __forceinline__ typename ProbeBody<V>::T probe_init(int v) {
   return (typename ProbeBody<V>::T)v;
 }
@@ -114,6 +136,8 @@ extern "C" int apsp_probe_minplus(int variant, int blocks, int threads, int iter
     case 4: probe_kernel<4><<<blocks, threads, 0, s>>>(iters, o); break;
     case 5: probe_kernel<5><<<blocks, threads, 0, s>>>(iters, o); break;
     case 6: probe_kernel<6><<<blocks, threads, 0, s>>>(iters, o); break;
+    case 7: probe_kernel<7><<<blocks, threads, 0, s>>>(iters, o); break;
+    case 8: probe_kernel<8><<<blocks, threads, 0, s>>>(iters, o); break;
     default: return APSP_ERR_ARG;
   }
   APSP_LAUNCH_CHECK();

@@ -42,6 +42,7 @@ struct ArithF32 {
   static __device__ __forceinline__ T from(int v) { return __int_as_float(v); }
   static __device__ __forceinline__ int to(T v) { return __float_as_int(v); }
   static __device__ __forceinline__ T mn(T a, T b) { return fminf(a, b); }
+  static __device__ __forceinline__ T collapse(T v, int) { return v; }
   // Column pairs: {A[i][k], A[i][k]} + {B[k][c], B[k][c+1]} in one packed add (the B pair comes
   // straight from a 128-bit load, the duplicated A value is built once per row and k), the
   // four adds of one duplicated A value issued back to back so it stays in the operand reuse
@@ -106,11 +107,31 @@ __device__ __forceinline__ int acc_bits(float v) { return __float_as_int(v); }
 __device__ __forceinline__ void set_acc(int &d, int v) { d = v; }
 __device__ __forceinline__ void set_acc(float &d, int v) { d = __int_as_float(v); }
 
-struct ArithI32 {
+// ArithInt<false> = ArithI32: one fused DPX add-min (__viaddmin_s32) per pair.
+// ArithInt<true> = ArithI16x2: every 32-bit operand word packs two 16-bit values, and one DPX
+//   operation (__viaddmin_s16x2) performs two pairs.  The operands are packed so that the two
+//   halves are consecutive k: A words {A[i][2w], A[i][2w+1]}, B words {B[2w][j], B[2w+1][j]}, so
+//   each accumulator word keeps the running minimum over even k in its low half and over odd k in
+//   its high half, and the word-level loop is exactly the int32 loop over K / 2 "k" steps.
+//   Values are capped at kCap16 = 0x3FFF (sums stay below 2^15, no wrap); collapse() folds the
+//   halves and maps a capped result back to the int32 sentinel.
+constexpr int kCap16 = 0x3FFF;
+
+template <bool P16>
+struct ArithInt {
   typedef int T;
   static __device__ __forceinline__ T from(int v) { return v; }
   static __device__ __forceinline__ int to(T v) { return v; }
   static __device__ __forceinline__ T mn(T a, T b) { return min(a, b); }
+  static __device__ __forceinline__ int addmin(int a, int b, int c) {
+    if (P16) return (int)__viaddmin_s16x2((unsigned)a, (unsigned)b, (unsigned)c);
+    return __viaddmin_s32(a, b, c);
+  }
+  static __device__ __forceinline__ T collapse(T v, int inf) {
+    if (!P16) return v;
+    const int m = min(v & 0xFFFF, (int)((unsigned)v >> 16));
+    return m >= kCap16 ? inf : m;
+  }
   template <typename A>
   static __device__ __forceinline__ void slab_full(const int *As, const int *Bs, int tm, int tn, A (&acc)[8][8]) {
 #pragma unroll 1
@@ -128,8 +149,7 @@ struct ArithI32 {
         for (int i = 0; i < 8; ++i) {
           const int a0 = kp ? a[i].z : a[i].x, a1 = kp ? a[i].w : a[i].y;
 #pragma unroll
-          for (int j = 0; j < 8; ++j)
-            set_acc(acc[i][j], __viaddmin_s32(a1, b1[j], __viaddmin_s32(a0, b0[j], acc_bits(acc[i][j]))));
+          for (int j = 0; j < 8; ++j) set_acc(acc[i][j], addmin(a1, b1[j], addmin(a0, b0[j], acc_bits(acc[i][j]))));
         }
       }
     }
@@ -147,10 +167,12 @@ struct ArithI32 {
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) set_acc(acc[i][j], __viaddmin_s32(a[i], b[j], acc_bits(acc[i][j])));
+        for (int j = 0; j < 8; ++j) set_acc(acc[i][j], addmin(a[i], b[j], acc_bits(acc[i][j])));
     }
   }
 };
+typedef ArithInt<false> ArithI32;
+typedef ArithInt<true> ArithI16x2;
 
 // True when int32 operands may take the exact fp32 path: every finite sum stays below 2^24
 // (w0 * mult + w1 < 2^24, with w0, w1 the largest finite entries involved).

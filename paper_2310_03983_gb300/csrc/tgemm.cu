@@ -121,6 +121,10 @@ __device__ __forceinline__ void consume(const TileProblem &p, const Smem &sm, in
       if (lane == 0) mbar_arrive(&sm.empty[stage]);
       if (++stage == kStages) { stage = 0; phase ^= 1; }
     }
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = AR::collapse(acc[i][j], p.inf_i);
     if (ACC) {
       if (!mbar_wait(sm.cfull, cphase, p.status)) return;
 #pragma unroll
@@ -164,7 +168,7 @@ template <typename S, int MODE, bool ACC>
 __global__ void __launch_bounds__(kThreads, 1)
     tgemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
                  const __grid_constant__ CUtensorMap mC, const TileProblem p) {
-  if (p.skip && *p.skip) return;  // uniform across the grid, before any barrier exists
+  if ((p.skip && *p.skip) || (p.run_if && !*p.run_if)) return;  // uniform, before any barrier exists
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   int *sA = reinterpret_cast<int *>(smem);
@@ -229,6 +233,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   const Smem sm = {sA, sB, sC, full, empty, cfull, cempty};
   if (sizeof(S) == 4 && S(0.5) != S(0)) {  // float storage
     consume<ArithF32, MODE, ACC>(p, sm, warp, lane, 0x7f800000);
+  } else if (p.arith16) {
+    consume<ArithI16x2, MODE, ACC>(p, sm, warp, lane, (kCap16 << 16) | kCap16);
   } else if (p.wmax && small_int_bound(p.wmax[0], p.wmult, p.wmax[1])) {
     consume<ArithF32, MODE, ACC>(p, sm, warp, lane, p.inf_i);
   } else {
@@ -260,7 +266,7 @@ static int launch_one(const CUtensorMap &mA, const CUtensorMap &mB, const CUtens
   const int64_t sms = sm_count();
   const int grid = (int)(p.ntiles < sms ? p.ntiles : sms);
   void *ev = nullptr;
-  const bool tr = trace_on();
+  const bool tr = trace_on() && !p.no_trace;
   if (tr) trace_begin(s, &ev);
   k<<<grid, kThreads, kSmemBytes + 1024, s>>>(mA, mB, mC, p);
   APSP_LAUNCH_CHECK();
@@ -292,6 +298,63 @@ int make_operand_maps(const void *base, int64_t rows, int64_t cols, int64_t ld, 
   if (mA && (r = make_tmap_2d(mA, base, rows, cols, ld, kBM, kBK, dtype, true))) return r;
   if (mB && (r = make_tmap_2d(mB, base, rows, cols, ld, kBK, kBN, dtype))) return r;
   if (mC && (r = make_tmap_2d(mC, base, rows, cols, ld, kBM, kBN, dtype))) return r;
+  return APSP_OK;
+}
+
+// ------------------------------ 16-bit packing -----------------------------------------
+__device__ __forceinline__ bool fits16(const int *words) {
+  return (int64_t)words[0] + (int64_t)words[1] < kCap16;
+}
+__device__ __forceinline__ int cap16(int v, int inf) { return v >= inf ? kCap16 : v; }
+
+__global__ void __launch_bounds__(256) pack16_a_kernel(const int *A, int64_t lda, int64_t M, int64_t K, int *A16,
+                                                       int64_t ld16, int inf, int *words) {
+  if (!fits16(words)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) words[4] = 1;
+  const int64_t kw = (K + 1) >> 1;
+  for (int64_t i = blockIdx.x; i < M; i += gridDim.x) {
+    const int *ar = A + i * lda;
+    int *o = A16 + i * ld16;
+    for (int64_t w = threadIdx.x; w < kw; w += blockDim.x) {
+      const int64_t k = 2 * w;
+      const int lo = cap16(ar[k], inf), hi = k + 1 < K ? cap16(ar[k + 1], inf) : kCap16;
+      o[w] = (hi << 16) | lo;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) pack16_b_kernel(const int *B, int64_t ldb, int64_t K, int64_t N, int *B16,
+                                                       int64_t ld16, int inf, int *words) {
+  if (!fits16(words)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) words[4] = 1;
+  const int64_t kw = (K + 1) >> 1;
+  for (int64_t w = blockIdx.x; w < kw; w += gridDim.x) {
+    const int *r0 = B + 2 * w * ldb, *r1 = r0 + ldb;
+    const bool has1 = 2 * w + 1 < K;
+    int *o = B16 + w * ld16;
+    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+      const int lo = cap16(r0[j], inf), hi = has1 ? cap16(r1[j], inf) : kCap16;
+      o[j] = (hi << 16) | lo;
+    }
+  }
+}
+
+int launch_pack16_a(const int *A, int64_t lda, int64_t M, int64_t K, int *A16, int64_t ld16, int inf, int *words,
+                    cudaStream_t s) {
+  if (M == 0 || K == 0) return APSP_OK;
+  const int64_t cap = (int64_t)sm_count() * 8;
+  pack16_a_kernel<<<(int)(M < cap ? M : cap), 256, 0, s>>>(A, lda, M, K, A16, ld16, inf, words);
+  APSP_LAUNCH_CHECK();
+  return APSP_OK;
+}
+
+int launch_pack16_b(const int *B, int64_t ldb, int64_t K, int64_t N, int *B16, int64_t ld16, int inf, int *words,
+                    cudaStream_t s) {
+  const int64_t kw = (K + 1) >> 1;
+  if (kw == 0 || N == 0) return APSP_OK;
+  const int64_t cap = (int64_t)sm_count() * 8;
+  pack16_b_kernel<<<(int)(kw < cap ? kw : cap), 256, 0, s>>>(B, ldb, K, N, B16, ld16, inf, words);
+  APSP_LAUNCH_CHECK();
   return APSP_OK;
 }
 
@@ -386,9 +449,19 @@ int launch_copy2d(void *dst, int64_t ldd, const void *src, int64_t lds, int64_t 
 }  // namespace apsp
 
 // ------------------------------------ C ABI -------------------------------------------
+namespace apsp {
+// Workspace of the packed 16-bit path of tropical_gemm: A16 (M x round_up(ceil(K/2), 4) words)
+// and B16 (ceil(K/2) x round_up(N, 4) words) after the bound words.
+static size_t packed16_bytes(int64_t M, int64_t N, int64_t K) {
+  const int64_t kw = (K + 1) >> 1;
+  return (size_t)round_up(M * round_up(kw, 4) * 4, 256) + (size_t)round_up(kw * round_up(N, 4) * 4, 256);
+}
+}  // namespace apsp
+
 extern "C" size_t tropical_gemm_workspace_bytes(int64_t M, int64_t N, int64_t K, int dtype) {
-  (void)M; (void)N; (void)K; (void)dtype;
-  return apsp::kFlagBytes;
+  using namespace apsp;
+  if (dtype != APSP_I32 || M <= 0 || N <= 0 || K <= 0) return kFlagBytes;
+  return kFlagBytes + packed16_bytes(M, N, K);
 }
 
 extern "C" int tropical_gemm(void *C, const void *A, const void *B, int64_t M, int64_t N, int64_t K, int64_t lda,
@@ -427,14 +500,15 @@ extern "C" int tropical_gemm(void *C, const void *A, const void *B, int64_t M, i
   int *words = nullptr;
   if (dtype == APSP_I32) {  // largest finite entries of A and B decide the exact fp32 path
     if (!ws) {
-      if (cudaMallocAsync(&own, kFlagBytes, s) != cudaSuccess) {
+      ws_bytes = tropical_gemm_workspace_bytes(M, N, K, dtype);
+      if (cudaMallocAsync(&own, ws_bytes, s) != cudaSuccess) {
         cudaGetLastError();
         return APSP_ERR_NOMEM;
       }
       ws = own;
     }
     words = reinterpret_cast<int *>(ws);
-    if (cudaMemsetAsync(words, 0, 16, s) != cudaSuccess) r = APSP_ERR_CUDA;
+    if (cudaMemsetAsync(words, 0, 32, s) != cudaSuccess) r = APSP_ERR_CUDA;
     if (!r && K > 0) r = launch_scan_max(A, M, K, lda, inf_i, words, s);
     if (!r && K > 0) r = launch_scan_max(B, K, N, ldb, inf_i, words + 1, s);
   }
@@ -450,7 +524,34 @@ extern "C" int tropical_gemm(void *C, const void *A, const void *B, int64_t M, i
   p.status = status_word();
   p.wmax = words;
   p.wmult = 1;
+  // int32 with room for the packed copies: when the largest finite entries of A and B sum
+  // below 0x3FFF (checked by the pack kernels on the device), the product runs on 16-bit pairs,
+  // two (min,+) pairs per DPX operation; the plain launch then returns at once.
+  void *tev = nullptr;
+  const bool group = !r && dtype == APSP_I32 && K > 0 && ws_bytes >= kFlagBytes + packed16_bytes(M, N, K);
+  if (group && trace_on()) trace_begin(s, &tev);
+  if (group) {
+    const int64_t kw = (K + 1) >> 1, lda16 = round_up(kw, 4), ldb16 = round_up(N, 4);
+    int *A16 = reinterpret_cast<int *>(reinterpret_cast<uint8_t *>(ws) + kFlagBytes);
+    int *B16 = reinterpret_cast<int *>(reinterpret_cast<uint8_t *>(A16) + round_up(M * lda16 * 4, 256));
+    r = launch_pack16_a(reinterpret_cast<const int *>(A), lda, M, K, A16, lda16, inf_i, words, s);
+    if (!r) r = launch_pack16_b(reinterpret_cast<const int *>(B), ldb, K, N, B16, ldb16, inf_i, words, s);
+    CUtensorMap pA, pB;
+    if (!r) r = make_operand_maps(A16, M, kw, lda16, APSP_I32, &pA, nullptr, nullptr);
+    if (!r) r = make_operand_maps(B16, kw, N, ldb16, APSP_I32, nullptr, &pB, nullptr);
+    if (!r) {
+      TileProblem q = p;
+      q.K = kw;
+      q.arith16 = 1;
+      q.run_if = words + 4;
+      q.no_trace = 1;
+      r = launch_tgemm(kModeGemm, accumulate != 0, dtype, pA, pB, mC, q, s);
+    }
+    p.skip = words + 4;
+    p.no_trace = 1;
+  }
   if (!r) r = launch_tgemm(kModeGemm, accumulate != 0, dtype, mA, mB, mC, p, s);
+  if (tev) trace_end(s, tev, kModeGemm, (double)M * (double)N * (double)K);
   if (own) cudaFreeAsync(own, s);
   return r;
 }

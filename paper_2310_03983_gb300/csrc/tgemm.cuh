@@ -43,10 +43,27 @@ struct TileProblem {
   // largest finite entries of A and B).
   const int *wmax;
   int64_t wmult;
-  // Optional device word (may be null): when it holds a non-zero value at launch time every
-  // CTA returns at once, so a later kernel can take over the product (predecessors).
+  // Optional device words (may be null), read before any barrier exists: every CTA returns at
+  // once when *skip is non-zero, or when *run_if is zero.  They let a launch sequence that was
+  // enqueued up front choose between alternative launches on the device.
   const int *skip;
+  const int *run_if;
+  // int32 storage only: the operands are packed 16-bit pairs (ArithI16x2) -- A words
+  // {A[i][2w], A[i][2w+1]}, B words {B[2w][j], B[2w+1][j]}, K counted in words -- and C holds
+  // plain int32.
+  int arith16;
+  // Not traced by itself: the caller brackets a group of alternative launches with one
+  // trace record (only one of them does the work).
+  int no_trace;
 };
+
+// 16-bit packing of int32 operands for ArithI16x2 (tgemm.cu).  Entries >= inf (and the padding
+// past K) become kCap16.  They run only when words[0] + words[1] < kCap16 (the largest finite
+// entries of A and B, so every finite sum is exact in 16 bits), and then set words[4] = 1.
+int launch_pack16_a(const int *A, int64_t lda, int64_t M, int64_t K, int *A16, int64_t ld16, int inf, int *words,
+                    cudaStream_t s);
+int launch_pack16_b(const int *B, int64_t ldb, int64_t K, int64_t N, int *B16, int64_t ld16, int inf, int *words,
+                    cudaStream_t s);
 
 // Launch one tile pass.  acc: fold into the existing C (min) instead of overwriting it.
 // maps: A box 128 rows x 32 cols, B box 32 rows x 128 cols, C box 128 x 128.

@@ -128,10 +128,11 @@ def test_tropical_gemm_strided_and_unaligned(apsp, dtype):
     assert_dist_equal(C.cpu().numpy(), want, "unaligned")
 
 
-@pytest.mark.parametrize("hi", [1000, 2**23 - 1, 2**23, 2**24, 10**8])
+@pytest.mark.parametrize("hi", [1000, 8191, 8192, 2**23 - 1, 2**23, 2**24, 10**8])
 def test_tropical_gemm_int_paths(apsp, hi):
-    """Entries up to `hi`: below 2^23 + 2^23 the exact fp32 path runs, above it the int32
-    path; both must give the oracle's values, including sums right at the 2^24 boundary."""
+    """Entries up to `hi`: largest entries summing below 0x3FFF take the packed 16-bit path
+    (8191 + 8191 = 0x3FFE), below 2^24 the exact fp32 path, above it the int32 path; all must
+    give the oracle's values, including sums right at each boundary."""
     rng = np.random.default_rng(hi % 1000)
     M, N, K = 200, 160, 140
     a = np.where(rng.random((M, K)) < 0.8, rng.integers(hi // 2, hi, (M, K), endpoint=True), INF).astype(np.int32)
@@ -139,6 +140,31 @@ def test_tropical_gemm_int_paths(apsp, hi):
     C = torch.empty((M, N), dtype=torch.int32, device="cuda")
     apsp.tropical_gemm(C, torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda())
     assert_dist_equal(C.cpu().numpy(), oracle.minplus(a, b), f"hi={hi}")
+
+
+@pytest.mark.parametrize("M,N,K", [(129, 130, 1), (200, 160, 141), (64, 512, 256)])
+def test_tropical_gemm_16bit_path_equals_others(apsp, M, N, K):
+    """The same product with the full workspace (packed 16-bit path), with only the 256 bytes
+    of bound words (exact fp32 path), and in accumulate mode over a C with entries above the
+    16-bit cap: identical, and equal to the oracle."""
+    rng = np.random.default_rng(M + N + K)
+    a = np.where(rng.random((M, K)) < 0.7, rng.integers(0, 5000, (M, K)), INF).astype(np.int32)
+    b = np.where(rng.random((K, N)) < 0.7, rng.integers(0, 5000, (K, N)), INF).astype(np.int32)
+    c = np.where(rng.random((M, N)) < 0.7, rng.integers(0, 40000, (M, N)), INF).astype(np.int32)
+    A, B = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    full = torch.empty(apsp.tropical_gemm_workspace_bytes(M, N, K), dtype=torch.uint8, device="cuda")
+    small = torch.empty(256, dtype=torch.uint8, device="cuda")
+    outs = []
+    for ws in (full, small):
+        C = torch.from_numpy(c).cuda()
+        apsp.tropical_gemm(C, A, B, accumulate=True, ws=ws)
+        outs.append(C.cpu().numpy())
+        C = torch.empty((M, N), dtype=torch.int32, device="cuda")
+        apsp.tropical_gemm(C, A, B, ws=ws)
+        outs.append(C.cpu().numpy())
+    assert_dist_equal(outs[0], oracle.minplus(a, b, c), "16-bit accumulate")
+    assert_dist_equal(outs[1], oracle.minplus(a, b), "16-bit overwrite")
+    assert np.array_equal(outs[0], outs[2]) and np.array_equal(outs[1], outs[3])
 
 
 def test_tropical_gemm_identity_and_k0(apsp):
