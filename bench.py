@@ -126,6 +126,17 @@ class ClockSampler:
             self.t.start()
         except OSError:
             self.proc = None
+            return
+        # nvidia-smi's own start-up (NVML initialisation) stalls the GPU for a moment: wait until
+        # it is polling (two samples, at most 5 s) so that the stall falls before the timed region.
+        t0 = time.perf_counter()
+        while len(self.lines) < 2 and time.perf_counter() - t0 < 5.0 and self.proc.poll() is None:
+            time.sleep(0.05)
+        self.mark = len(self.lines)
+
+    def begin(self):
+        """Call right before the timed region: only later samples are reported."""
+        self.mark = len(self.lines)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -142,7 +153,9 @@ class ClockSampler:
         self.t.join(timeout=2)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        mark = getattr(self, "mark", 0)
+        lines = self.lines[mark:] if len(self.lines) > mark else self.lines[-1:]
+        for ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -328,7 +341,6 @@ def run_ours(args, w, rank, world, local_rank):
 
     sampler = ClockSampler(local_rank)
     sampler.start()
-    time.sleep(0.3)
     stream = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     apsp.apsp_trace_enable(True)
@@ -336,6 +348,7 @@ def run_ours(args, w, rank, world, local_rank):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    sampler.begin()
     e0.record(stream)
     for i in range(args.steps):
         if flush is not None:
@@ -394,16 +407,30 @@ def run_ours(args, w, rank, world, local_rank):
                    "algorithmic_bytes_per_launch": 8 * (n - 128) ** 2,
                    "source": "ncu dram bytes of one phase-3 launch at n=8192, scaled by (n-128)^2"}
     nb = -(-n // 128)
-    launches_per_step = {"fw": 1 + 3 * nb, "gemm": 2, "rkleene": None}[w["algo"]]
+    fw16 = w["algo"] == "fw" and w["dtype"] == "int32" and n >= 2048
+    # Every kernel of ours that is launched per step, including the alternative launches that
+    # return at once: FW with the 16-bit phase 3 launches normalise, the decision, per block
+    # (diagonal, panels, packing, 16-bit and plain phase 3), the certificate (2) and the three
+    # launches per block of the int32 pass that runs only when the certificate fails.
+    launches_per_step = {"fw": 4 + 8 * nb if fw16 else 1 + 3 * nb,
+                         "gemm": 6 if w["dtype"] == "int32" else 1, "rkleene": None}[w["algo"]]
+    if w["dtype"] != "int32":
+        arith = "fp32 packed add + 3-input min"
+    elif w["algo"] == "gemm":
+        arith = "packed 16-bit pairs, one DPX add-min per two pairs (exact: max A + max B < 0x3FFF)"
+    elif fw16:
+        arith = ("FW phase 3 on packed 16-bit pairs (one DPX add-min per two pairs), the closure truncated at "
+                 "0x3FFF and certified exact on the device (largest stored value below the cap + largest weight "
+                 "< cap; else an int32 pass); phases 1-2 exact in fp32 on int32 bit patterns")
+    else:
+        arith = "fp32 packed add + 3-input min on int32 bit patterns (exact: every distance < 2^24)"
+    dtype_tag = "f32" if w["dtype"] != "int32" else ("i16x2" if (fw16 or w["algo"] == "gemm") else "i32")
     line = {
         "metric": "(min,+) Gop/s (2n^3/s)", "value": round(value, 2), "unit": "Gop/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 2),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "i32" if w["dtype"] == "int32" else "f32",
-        "arith": (("packed 16-bit pairs, one DPX add-min per two pairs (exact: max A + max B < 0x3FFF)"
-                   if w["algo"] == "gemm" else
-                   "fp32 packed add + 3-input min on int32 bit patterns (exact: every distance < 2^24)")
-                  if w["dtype"] == "int32" else "fp32 packed add + 3-input min"),
+        "dtype": dtype_tag,
+        "arith": arith,
         "data": "synthetic", "config": config_of(args, w, world),
         "roofline": {"bound": "alu", "kernel": {0: "tgemm_kernel (product)", 2: "tgemm_kernel (FW phase 3)"}[dom_mode],
                      "achieved": round(achieved, 2) if achieved else None, "peak": round(peak_max, 2),
@@ -493,9 +520,9 @@ def run_batched(args, w, rank, world, local_rank):
         dist.barrier()
     sampler = ClockSampler(local_rank)
     sampler.start()
-    time.sleep(0.3)
     cur = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler.begin()
     e0.record(cur)
     for _ in range(args.steps):
         graph.replay()

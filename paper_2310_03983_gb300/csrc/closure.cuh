@@ -12,8 +12,14 @@ struct Bound {
   int64_t mult;
 };
 
-// Blocked Floyd-Warshall on an aligned, normalised block (fw.cu).
-int fw_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bound b, cudaStream_t s);
+// Blocked Floyd-Warshall on an aligned, normalised block (fw.cu).  panels16: scratch of
+// fw16_panel_bytes(n) for the packed 16-bit phase 3 of int32 closures, or null.
+int fw_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bound b, cudaStream_t s,
+               void *panels16 = nullptr);
+size_t fw16_panel_bytes(int64_t n);
+// Smallest n for which apsp_fw takes the packed 16-bit phase 3 (below it the extra launches
+// of the certificate cost more than the faster arithmetic saves).
+constexpr int64_t kFw16MinN = 2048;
 
 // R-Kleene on an aligned, normalised block, scratch of rkleene_scratch_bytes (rkleene.cu).
 int rkleene_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, int cutoff, Bound b, void *scratch,
@@ -23,7 +29,7 @@ size_t rkleene_scratch_bytes(int64_t n, int cutoff);
 // algo 0 = FW, 1 = R-Kleene; param = tile (FW) or cutoff (R-Kleene).
 int closure_entry(int algo, void *d, int64_t n, int64_t ld, int dtype, const void *inf, int param, void *ws,
                   size_t ws_bytes, void *stream);
-size_t closure_workspace_bytes(int algo, int64_t n, int64_t ld, int param);
+size_t closure_workspace_bytes(int algo, int64_t n, int64_t ld, int param, int dtype);
 
 // (min,+) product of aligned operands through the TMA engine (rkleene.cu).
 int gemm_aligned(void *C, int64_t ldc, const void *A, int64_t lda, const void *B, int64_t ldb, int64_t M, int64_t N,

@@ -32,6 +32,10 @@ __device__ __forceinline__ void flag_status(unsigned int *st, int code) {
 // with APSP_ERR_TIMEOUT instead of hanging the GPU.
 constexpr uint32_t kSpinLimit = 1u << 24;
 
+// Cap of the packed 16-bit (min,+) arithmetic: values at or above it mean "at least the cap";
+// two capped values still sum below 2^15.
+constexpr int kCap16 = 0x3FFF;
+
 // ---------------------------------------------------------------------------------------
 // (min,+) element operations.  int32 values live in [0, INF] with INF <= 0x3FFFFFFF, so
 // a + b never overflows and min() against an accumulator <= INF saturates for free.

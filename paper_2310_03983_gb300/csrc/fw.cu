@@ -20,7 +20,8 @@ namespace apsp {
 // Phase 1: Eq. 1 on the bk x bk diagonal tile, closed in registers by one 256-thread CTA
 // (diag.cuh).  int32 tiles are relaxed in int32 (exact for any weights), float32 in fp32.
 template <bool FLOAT>
-__global__ void __launch_bounds__(256) fw_diag_kernel(int *d, int64_t ld, int64_t n, int64_t kb) {
+__global__ void __launch_bounds__(256) fw_diag_kernel(int *d, int64_t ld, int64_t n, int64_t kb, const int *run_if) {
+  if (run_if && !*run_if) return;
   __shared__ __align__(16) int buf[512];
   const int64_t kb0 = kb * kBM;
   const int bk = (int)std::min<int64_t>(kBM, n - kb0);
@@ -33,17 +34,115 @@ __global__ void __launch_bounds__(256) fw_diag_kernel(int *d, int64_t ld, int64_
   store_tile_regs(r, T, ld, bk, tm, tn);
 }
 
-int launch_fw_diag(void *d, int64_t ld, int64_t n, int64_t kb, int dtype, cudaStream_t s) {
+int launch_fw_diag(void *d, int64_t ld, int64_t n, int64_t kb, int dtype, cudaStream_t s, const int *run_if) {
   if (dtype == APSP_I32)
-    fw_diag_kernel<false><<<1, 256, 0, s>>>(reinterpret_cast<int *>(d), ld, n, kb);
+    fw_diag_kernel<false><<<1, 256, 0, s>>>(reinterpret_cast<int *>(d), ld, n, kb, run_if);
   else
-    fw_diag_kernel<true><<<1, 256, 0, s>>>(reinterpret_cast<int *>(d), ld, n, kb);
+    fw_diag_kernel<true><<<1, 256, 0, s>>>(reinterpret_cast<int *>(d), ld, n, kb, run_if);
   APSP_LAUNCH_CHECK();
   return APSP_OK;
 }
 
+// ------------------------------------------------------------------------------------------
+// Phase 3 on packed 16-bit pairs (int32 matrices).
+//
+// The closure is computed in the (min,+) semiring truncated at CAP = 0x3FFF: values at or above
+// CAP all mean "CAP".  Truncation t(v) = min(v, CAP) is a homomorphism of (min,+) on [0, inf]
+// (t(min(a, b)) = min(t(a), t(b)), t(a + b) = t(t(a) + t(b))), so a computation that mixes
+// exact int32 steps (phases 1 and 2) with truncated ones (phase 3 on 16-bit pairs: operands
+// capped at CAP, a capped result discarded in favour of the old entry) keeps the invariant
+// t(stored) = t(exact Floyd-Warshall value) for every entry, and every finite stored value is
+// the length of a real path.  At the end, every pair whose distance is below CAP holds it
+// exactly.  A pair with CAP <= distance < infinity would need a vertex on its shortest path
+// whose distance lies in [CAP - w_max, CAP); so if the largest stored value below CAP plus the
+// largest weight stays below CAP, no such pair exists and the result is the exact closure.
+// Otherwise (checked on the device) the int32 Floyd-Warshall runs again over the stored
+// matrix, whose entries lie between the distances and the weights, and so closes it exactly.
+// Words of the bound block used here:
+//   [0] largest finite weight (a1), [4] 16-bit phase 3 in use, [5] largest stored value < CAP,
+//   [6] the int32 pass must run again.
+constexpr int kUse16MaxWeight = kCap16 / 4;
+
+__global__ void fw16_decide_kernel(int *words) {
+  words[4] = words[0] <= kUse16MaxWeight;
+  words[5] = 0;
+  words[6] = 0;
+}
+
+// Packs the column panel D[:, kb0 .. kb0+bk) into A16 (n rows x 64 words, ld 64) and the row
+// panel D[kb0 .. kb0+bk, :] into B16 (64 words x n, ld ldb16) as 16-bit pairs of consecutive
+// k, every value capped at CAP (the sentinel included).
+__global__ void __launch_bounds__(256) fw_pack16_kernel(const int *d, int64_t ld, int64_t n, int64_t kb, int *A16,
+                                                        int *B16, int64_t ldb16, const int *words) {
+  if (!words[4]) return;
+  const int64_t kb0 = kb * kBM;
+  const int bk = (int)std::min<int64_t>(kBM, n - kb0);
+  const int kw = (bk + 1) >> 1;
+  const int64_t na = n * kw, total = na + (int64_t)kw * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    if (e < na) {
+      const int64_t i = e / kw;
+      const int w = (int)(e - i * kw), k = 2 * w;
+      const int *row = d + i * ld + kb0;
+      const int lo = min(row[k], kCap16), hi = k + 1 < bk ? min(row[k + 1], kCap16) : kCap16;
+      A16[i * (kBK * 2) + w] = (hi << 16) | lo;
+    } else {
+      const int64_t f = e - na;
+      const int w = (int)(f / n);
+      const int64_t j = f - (int64_t)w * n;
+      const int k = 2 * w;
+      const int *r0 = d + (kb0 + k) * ld + j;
+      const int lo = min(r0[0], kCap16), hi = k + 1 < bk ? min(r0[ld], kCap16) : kCap16;
+      B16[w * ldb16 + j] = (hi << 16) | lo;
+    }
+  }
+}
+
+// words[5] = largest stored value below CAP; then words[6] = 1 when it plus the largest weight
+// reaches CAP (the truncated result cannot be certified).
+__global__ void __launch_bounds__(256) fw16_certify_kernel(const int *d, int64_t ld, int64_t n, int *words) {
+  if (!words[4]) return;
+  int m = 0;
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x)
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+      const int v = d[i * ld + j];
+      if (v < kCap16) m = max(m, v);
+    }
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(words + 5, m);
+}
+
+__global__ void fw16_verdict_kernel(int *words) {
+  if (words[4]) words[6] = (int64_t)words[5] + (int64_t)words[0] >= kCap16;
+}
+
+size_t fw16_panel_bytes(int64_t n) {
+  return (size_t)round_up(n * kBK * 2 * 4, 256) + (size_t)round_up(kBK * 2 * round_up(n, 4) * 4, 256);
+}
+
+// The plain three-phase loop; every launch returns at once unless *run_if (when given) is set.
+static int fw_loop(void *d, int64_t n, int64_t ld, int dtype, const CUtensorMap &mA, const CUtensorMap &mB,
+                   const CUtensorMap &mC, TileProblem p, const int *run_if, cudaStream_t s) {
+  int r;
+  const int64_t nb = p.nb;
+  p.run_if = run_if;
+  p.no_trace = run_if != nullptr;
+  for (int64_t kb = 0; kb < nb; ++kb) {
+    if ((r = launch_fw_diag(d, ld, n, kb, dtype, s, run_if))) return r;
+    if (nb == 1) break;
+    p.kb = kb;
+    p.ntiles = 2 * (nb - 1);
+    if ((r = launch_tgemm(kModeFwPanels, false, dtype, mA, mB, mC, p, s))) return r;
+    p.ntiles = (nb - 1) * (nb - 1);
+    if ((r = launch_tgemm(kModeFwRest, true, dtype, mA, mB, mC, p, s))) return r;
+  }
+  return APSP_OK;
+}
+
 // Closes the n x n block at d (16-byte aligned, ld % 4 == 0, already normalised) in place.
-int fw_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bound b, cudaStream_t s) {
+// panels16 (may be null): fw16_panel_bytes(n) of device scratch; with it, an int32 closure
+// whose largest weight is at most CAP / 4 runs phase 3 on packed 16-bit pairs (above).
+int fw_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bound b, cudaStream_t s, void *panels16) {
   if (n == 0) return APSP_OK;
   CUtensorMap mA, mB, mC;
   int r;
@@ -58,16 +157,55 @@ int fw_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bound b, cu
   p.status = status_word();
   p.wmax = b.w;
   p.wmult = b.mult;
+  if (!(panels16 && dtype == APSP_I32 && b.w && nb > 1)) return fw_loop(d, n, ld, dtype, mA, mB, mC, p, nullptr, s);
+
+  int *words = const_cast<int *>(b.w);
+  int *A16 = reinterpret_cast<int *>(panels16);
+  int *B16 = reinterpret_cast<int *>(reinterpret_cast<uint8_t *>(panels16) + round_up(n * kBK * 2 * 4, 256));
+  const int64_t ldb16 = round_up(n, 4);
+  CUtensorMap pA, pB;
+  if ((r = make_operand_maps(A16, n, kBK * 2, kBK * 2, APSP_I32, &pA, nullptr, nullptr))) return r;
+  if ((r = make_operand_maps(B16, kBK * 2, n, ldb16, APSP_I32, nullptr, &pB, nullptr))) return r;
+  fw16_decide_kernel<<<1, 1, 0, s>>>(words);
+  APSP_LAUNCH_CHECK();
+  const int64_t cap = (int64_t)sm_count() * 8;
   for (int64_t kb = 0; kb < nb; ++kb) {
-    if ((r = launch_fw_diag(d, ld, n, kb, dtype, s))) return r;
-    if (nb == 1) break;
+    if ((r = launch_fw_diag(d, ld, n, kb, dtype, s, nullptr))) return r;
     p.kb = kb;
     p.ntiles = 2 * (nb - 1);
+    p.run_if = nullptr;
+    p.skip = nullptr;
+    p.arith16 = 0;
+    p.no_trace = 0;
     if ((r = launch_tgemm(kModeFwPanels, false, dtype, mA, mB, mC, p, s))) return r;
+    const int64_t work = n * kBK * 2;
+    fw_pack16_kernel<<<(int)std::min<int64_t>(cap, cdiv(work, 256)), 256, 0, s>>>(
+        reinterpret_cast<const int *>(d), ld, n, kb, A16, B16, ldb16, words);
+    APSP_LAUNCH_CHECK();
+    // Phase 3: the 16-bit launch runs when words[4] is set, the plain one otherwise; one trace
+    // record covers the pair.
+    void *tev = nullptr;
+    if (trace_on()) trace_begin(s, &tev);
     p.ntiles = (nb - 1) * (nb - 1);
+    p.no_trace = 1;
+    TileProblem q = p;
+    q.arith16 = 1;
+    q.run_if = words + 4;
+    if ((r = launch_tgemm(kModeFwRest16, true, dtype, pA, pB, mC, q, s))) return r;
+    p.skip = words + 4;
     if ((r = launch_tgemm(kModeFwRest, true, dtype, mA, mB, mC, p, s))) return r;
+    if (tev) {
+      const double bk = (double)std::min<int64_t>(kBM, n - kb * kBM), rest = (double)n - bk;
+      trace_end(s, tev, kModeFwRest, rest * rest * bk);
+    }
   }
-  return APSP_OK;
+  fw16_certify_kernel<<<(int)std::min<int64_t>(n, cap), 256, 0, s>>>(reinterpret_cast<const int *>(d), ld, n, words);
+  APSP_LAUNCH_CHECK();
+  fw16_verdict_kernel<<<1, 1, 0, s>>>(words);
+  APSP_LAUNCH_CHECK();
+  p.skip = nullptr;
+  p.arith16 = 0;
+  return fw_loop(d, n, ld, dtype, mA, mB, mC, p, words + 6, s);
 }
 
 // Shared entry logic of apsp_fw and apsp_rkleene: validation, the workspace (caller's or
@@ -83,8 +221,12 @@ int closure_entry(int algo, void *d, int64_t n, int64_t ld, int dtype, const voi
   int inf_i = 0;
   float inf_f = 0.f;
   if (dtype == APSP_I32 ? resolve_inf_i32(inf, &inf_i) : resolve_inf_f32(inf, &inf_f)) return APSP_ERR_ARG;
-  const size_t need = closure_workspace_bytes(algo, n, ld, param);
-  if (ws && (ws_bytes < need || reinterpret_cast<uintptr_t>(ws) % 256 != 0)) return APSP_ERR_ARG;
+  // The full size includes the packed 16-bit panels of an int32 FW; a workspace of the base
+  // size is still accepted and closes with the plain phase 3.
+  const size_t need = closure_workspace_bytes(algo, n, ld, param, dtype);
+  const size_t panels = (algo == 0 && dtype == APSP_I32 && n >= kFw16MinN) ? fw16_panel_bytes(n) : 0;
+  const size_t base = need - panels;
+  if (ws && (ws_bytes < base || reinterpret_cast<uintptr_t>(ws) % 256 != 0)) return APSP_ERR_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   void *own = nullptr;
   if (!ws && need > 0) {
@@ -93,7 +235,9 @@ int closure_entry(int algo, void *d, int64_t n, int64_t ld, int dtype, const voi
       return APSP_ERR_NOMEM;
     }
     ws = own;
+    ws_bytes = need;
   }
+  void *panels16 = (panels && ws_bytes >= need) ? reinterpret_cast<uint8_t *>(ws) + base : nullptr;
   int r = APSP_OK;
   uint8_t *wsp = reinterpret_cast<uint8_t *>(ws);
   int *words = reinterpret_cast<int *>(wsp);  // [0]: largest finite weight, [1]: 0
@@ -109,26 +253,27 @@ int closure_entry(int algo, void *d, int64_t n, int64_t ld, int dtype, const voi
     if (!r) r = launch_copy2d(work, ldw, d, ld, n, n, s);
   }
   if (!r) r = launch_normalise(work, n, ldw, dtype, inf_i, inf_f, dtype == APSP_I32 ? words : nullptr, s);
-  if (!r) r = algo == 0 ? fw_closure(work, n, ldw, dtype, inf_i, bound, s)
+  if (!r) r = algo == 0 ? fw_closure(work, n, ldw, dtype, inf_i, bound, s, panels16)
                         : rkleene_closure(work, n, ldw, dtype, inf_i, param ? param : 256, bound, wsp, s);
   if (!r && work != d) r = launch_copy2d(d, ld, work, ldw, n, n, s);
   if (own) cudaFreeAsync(own, s);
   return r;
 }
 
-size_t closure_workspace_bytes(int algo, int64_t n, int64_t ld, int param) {
+size_t closure_workspace_bytes(int algo, int64_t n, int64_t ld, int param, int dtype) {
   if (n <= 0) return 0;
   size_t b = kFlagBytes;
   if (ld % 4 != 0) b += (size_t)round_up(n * round_up(n, 4) * 4, 256);
   if (algo == 1) b += rkleene_scratch_bytes(n, param ? param : 256);
+  if (algo == 0 && dtype == APSP_I32 && n >= kFw16MinN) b += fw16_panel_bytes(n);  // last: optional
   return b;
 }
 
 }  // namespace apsp
 
 extern "C" size_t apsp_fw_workspace_bytes(int64_t n, int64_t ld, int dtype, int tile) {
-  (void)dtype; (void)tile;
-  return apsp::closure_workspace_bytes(0, n, ld, 0);
+  (void)tile;
+  return apsp::closure_workspace_bytes(0, n, ld, 0, dtype);
 }
 
 extern "C" int apsp_fw(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int tile, void *ws,

@@ -78,8 +78,7 @@ int rkleene_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, int cu
 }  // namespace apsp
 
 extern "C" size_t apsp_rkleene_workspace_bytes(int64_t n, int64_t ld, int dtype, int cutoff) {
-  (void)dtype;
-  return apsp::closure_workspace_bytes(1, n, ld, cutoff);
+  return apsp::closure_workspace_bytes(1, n, ld, cutoff, dtype);
 }
 
 extern "C" int apsp_rkleene(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int cutoff, void *ws,

@@ -115,8 +115,6 @@ __device__ __forceinline__ void set_acc(float &d, int v) { d = __int_as_float(v)
 //   its high half, and the word-level loop is exactly the int32 loop over K / 2 "k" steps.
 //   Values are capped at kCap16 = 0x3FFF (sums stay below 2^15, no wrap); collapse() folds the
 //   halves and maps a capped result back to the int32 sentinel.
-constexpr int kCap16 = 0x3FFF;
-
 template <bool P16>
 struct ArithInt {
   typedef int T;

@@ -75,13 +75,14 @@ __device__ __forceinline__ TileCoords tile_coords(const TileProblem &p, int64_t 
       j = (int)(t - (int64_t)i * nb1);
       i += (i >= p.kb);
       j += (j >= p.kb);
-      tc.a_row = i * kBM; tc.a_col = kb0;
-      tc.b_row = kb0;     tc.b_col = j * kBN;
+      tc.a_row = i * kBM; tc.a_col = MODE == kModeFwRest16 ? 0 : kb0;
+      tc.b_row = MODE == kModeFwRest16 ? 0 : kb0;
+      tc.b_col = j * kBN;
       tc.c_row = i * kBM; tc.c_col = j * kBN;
     }
     tc.m_valid = (int)(p.n - tc.c_row < kBM ? p.n - tc.c_row : kBM);
     tc.n_valid = (int)(p.n - tc.c_col < kBN ? p.n - tc.c_col : kBN);
-    tc.k_len = bk;
+    tc.k_len = MODE == kModeFwRest16 ? (bk + 1) >> 1 : bk;
   }
   return tc;
 }
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // (min,+) pairs one launch performs by definition (Eq. 2: one add and one min per (i, j, k)).
 template <int MODE> static double algorithmic_pairs(const TileProblem &p) {
-  if (MODE == kModeGemm) return (double)p.M * (double)p.N * (double)p.K;
+  if (MODE == kModeGemm) return (double)p.M * (double)p.N * (double)p.K * (p.arith16 ? 2.0 : 1.0);
   const double bk = (double)(p.n - p.kb * kBM < kBM ? p.n - p.kb * kBM : kBM);
   const double rest = (double)p.n - bk;
   return MODE == kModeFwPanels ? 2.0 * bk * bk * rest : rest * rest * bk;
@@ -282,6 +283,7 @@ static int launch_t(int mode, bool acc, const CUtensorMap &mA, const CUtensorMap
     case 1: return launch_one<T, kModeGemm, true>(mA, mB, mC, p, s);
     case 2: return launch_one<T, kModeFwPanels, false>(mA, mB, mC, p, s);
     case 5: return launch_one<T, kModeFwRest, true>(mA, mB, mC, p, s);
+    case 7: return launch_one<T, kModeFwRest16, true>(mA, mB, mC, p, s);
     default: return APSP_ERR_ARG;
   }
 }

@@ -25,6 +25,8 @@ enum TileMode : int {
   kModeGemm = 0,      // C (M x N) = [min(C,)] A (M x K) (x) B (K x N)
   kModeFwPanels = 1,  // blocked-FW phase 2: row and column panels of block kb
   kModeFwRest = 2,    // blocked-FW phase 3: every tile outside block row/column kb
+  kModeFwRest16 = 3,  // phase 3 on packed 16-bit copies of the panels: A = the column panel
+                      // (n rows x 64 words), B = the row panel (64 words x n), C = the matrix
 };
 
 struct TileProblem {

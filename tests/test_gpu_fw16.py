@@ -1,0 +1,98 @@
+"""Blocked Floyd-Warshall with phase 3 on packed 16-bit pairs (int32 closures of at least 2048
+vertices whose largest weight is at most 0x3FFF / 4), against the CPU oracle, bit-exact.
+
+The 16-bit pass computes the closure truncated at 0x3FFF; a device-side certificate (largest
+stored value below the cap plus the largest weight stays below the cap) proves it exact, and
+otherwise the int32 pass runs again over the stored matrix.  Covered here: graphs that pass the
+certificate, graphs whose long paths fail it (the int32 pass must finish the job), weights too
+large for the 16-bit pass, and a workspace without room for the packed panels."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from test_gpu_parity import assert_dist_equal
+
+pytestmark = pytest.mark.gpu
+
+INF = workloads.INF_I32
+THREADS = os.cpu_count() or 4
+
+
+@pytest.fixture(scope="module")
+def apsp():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_2310_03983_gb300 as m
+    assert m.apsp_device_status() == 0
+    return m
+
+
+def _close(apsp, h, ws_bytes=None):
+    d = torch.from_numpy(h).cuda()
+    ws = None
+    if ws_bytes is not None:
+        ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    apsp.apsp_fw(d, ws=ws)
+    assert apsp.apsp_device_status() == 0
+    return d.cpu().numpy()
+
+
+@pytest.mark.parametrize("n,p,hi", [(2048, 0.01, 100), (2100, 0.3, 1000), (2179, 0.002, 4095)])
+def test_fw16_matches_oracle(apsp, n, p, hi):
+    h = workloads.er_graph(n, p, "int32", lo=1, hi=hi, seed=n + hi)
+    assert_dist_equal(_close(apsp, h), oracle.fw(h, threads=THREADS), f"n={n} p={p} hi={hi}")
+
+
+def _path_graph(n, w, extra=0, seed=0):
+    h = np.full((n, n), INF, np.int32)
+    np.fill_diagonal(h, 0)
+    idx = np.arange(n - 1)
+    h[idx, idx + 1] = w
+    if extra:  # a few random shortcuts
+        rng = np.random.default_rng(seed)
+        a, b = rng.integers(0, n, extra), rng.integers(0, n, extra)
+        h[a, b] = np.where(a != b, rng.integers(1, w + 1, extra), 0)
+    return h
+
+
+def test_long_paths_below_the_cap_certify(apsp):
+    """A directed path of 2048 vertices with weight 7: distances up to 14329, still below the
+    cap, so the certificate holds; every entry must be exact."""
+    n = 2048
+    h = _path_graph(n, 7)
+    i, j = np.indices((n, n))
+    want = np.where(j >= i, 7 * (j - i), INF)
+    assert np.array_equal(_close(apsp, h), want)
+
+
+@pytest.mark.parametrize("w,extra", [(100, 0), (1000, 300)])
+def test_long_paths_above_the_cap_rerun_in_int32(apsp, w, extra):
+    """Paths far longer than the cap: the truncated pass cannot be certified and the int32
+    pass must produce the exact closure."""
+    n = 2200
+    h = _path_graph(n, w, extra, seed=w)
+    assert_dist_equal(_close(apsp, h), oracle.fw(h, threads=THREADS), f"w={w}")
+
+
+def test_heavy_weights_skip_the_16bit_pass(apsp):
+    n = 2048
+    h = workloads.er_graph(n, 0.02, "int32", lo=1, hi=50000, seed=5)
+    assert_dist_equal(_close(apsp, h), oracle.fw(h, threads=THREADS), "heavy")
+
+
+def test_base_workspace_uses_the_plain_phase3(apsp):
+    """A workspace without room for the packed panels is accepted; the result is identical."""
+    n = 2304
+    h = workloads.er_graph(n, 0.01, "int32", lo=1, hi=100, seed=6)
+    full = apsp.apsp_fw_workspace_bytes(n, n)
+    assert full > 256
+    a = _close(apsp, h)
+    b = _close(apsp, h, ws_bytes=256)
+    c = _close(apsp, h, ws_bytes=full)
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+    rows = np.random.default_rng(7).choice(n, 16, replace=False)
+    assert_dist_equal(a[rows], oracle.dijkstra_rows(h, rows, threads=THREADS), "rows")
