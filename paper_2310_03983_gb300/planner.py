@@ -34,7 +34,8 @@ from . import (apsp_close_cta, apsp_fw, apsp_mlp_adam, apsp_mlp_backward, apsp_m
 CANDIDATES = (("fw", 0), ("rkleene", 128), ("rkleene", 256), ("rkleene", 512), ("rkleene", 1024), ("cta", 0),
               ("squaring", 0))
 CTA_MAX_N = 1024  # beyond this one SM is far too slow to be worth timing
-IN_DIM = 9
+IN_DIM = 10
+FW16_MIN_N = 2048  # apsp_fw runs phase 3 on packed 16-bit pairs for int32 graphs this large
 HIDDEN = 64
 
 
@@ -45,7 +46,8 @@ def features(n: int, density: float, dtype: str, algo: str, param: int) -> list[
             1.0 if algo == "fw" else 0.0, 1.0 if rk else 0.0, 1.0 if algo == "cta" else 0.0,
             math.log2(param) / 11.0 if rk else 0.0,
             (math.log2(max(n, 1)) - math.log2(param)) / 8.0 if rk and param else 0.0,
-            1.0 if algo == "squaring" else 0.0]
+            1.0 if algo == "squaring" else 0.0,
+            1.0 if algo == "fw" and dtype == "int32" and n >= FW16_MIN_N else 0.0]
 
 
 def applicable(n: int):
