@@ -407,7 +407,7 @@ def run_ours(args, w, rank, world, local_rank):
                    "algorithmic_bytes_per_launch": 8 * (n - 128) ** 2,
                    "source": "ncu dram bytes of one phase-3 launch at n=8192, scaled by (n-128)^2"}
     nb = -(-n // 128)
-    fw16 = w["algo"] == "fw" and w["dtype"] == "int32" and n >= 2048
+    fw16 = w["algo"] == "fw" and w["dtype"] == "int32" and n >= 4096
     # Every kernel of ours that is launched per step, including the alternative launches that
     # return at once: FW with the 16-bit phase 3 launches normalise, the decision, per block
     # (diagonal, panels, packing, 16-bit and plain phase 3), the certificate (2) and the three

@@ -19,7 +19,7 @@ int fw_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bound b, cu
 size_t fw16_panel_bytes(int64_t n);
 // Smallest n for which apsp_fw takes the packed 16-bit phase 3 (below it the extra launches
 // of the certificate cost more than the faster arithmetic saves).
-constexpr int64_t kFw16MinN = 2048;
+constexpr int64_t kFw16MinN = 4096;
 
 // R-Kleene on an aligned, normalised block, scratch of rkleene_scratch_bytes (rkleene.cu).
 int rkleene_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, int cutoff, Bound b, void *scratch,

@@ -35,7 +35,7 @@ CANDIDATES = (("fw", 0), ("rkleene", 128), ("rkleene", 256), ("rkleene", 512), (
               ("squaring", 0))
 CTA_MAX_N = 1024  # beyond this one SM is far too slow to be worth timing
 IN_DIM = 10
-FW16_MIN_N = 2048  # apsp_fw runs phase 3 on packed 16-bit pairs for int32 graphs this large
+FW16_MIN_N = 4096  # apsp_fw runs phase 3 on packed 16-bit pairs for int32 graphs this large
 HIDDEN = 64
 
 

@@ -1,4 +1,4 @@
-"""Blocked Floyd-Warshall with phase 3 on packed 16-bit pairs (int32 closures of at least 2048
+"""Blocked Floyd-Warshall with phase 3 on packed 16-bit pairs (int32 closures of at least 4096
 vertices whose largest weight is at most 0x3FFF / 4), against the CPU oracle, bit-exact.
 
 The 16-bit pass computes the closure truncated at 0x3FFF; a device-side certificate (largest
@@ -41,7 +41,7 @@ def _close(apsp, h, ws_bytes=None):
     return d.cpu().numpy()
 
 
-@pytest.mark.parametrize("n,p,hi", [(2048, 0.01, 100), (2100, 0.3, 1000), (2179, 0.002, 4095)])
+@pytest.mark.parametrize("n,p,hi", [(4096, 0.01, 100), (4100, 0.3, 1000), (4133, 0.002, 4095)])
 def test_fw16_matches_oracle(apsp, n, p, hi):
     h = workloads.er_graph(n, p, "int32", lo=1, hi=hi, seed=n + hi)
     assert_dist_equal(_close(apsp, h), oracle.fw(h, threads=THREADS), f"n={n} p={p} hi={hi}")
@@ -60,12 +60,12 @@ def _path_graph(n, w, extra=0, seed=0):
 
 
 def test_long_paths_below_the_cap_certify(apsp):
-    """A directed path of 2048 vertices with weight 7: distances up to 14329, still below the
+    """A directed path of 4096 vertices with weight 3: distances up to 12285, still below the
     cap, so the certificate holds; every entry must be exact."""
-    n = 2048
-    h = _path_graph(n, 7)
+    n = 4096
+    h = _path_graph(n, 3)
     i, j = np.indices((n, n))
-    want = np.where(j >= i, 7 * (j - i), INF)
+    want = np.where(j >= i, 3 * (j - i), INF)
     assert np.array_equal(_close(apsp, h), want)
 
 
@@ -73,20 +73,20 @@ def test_long_paths_below_the_cap_certify(apsp):
 def test_long_paths_above_the_cap_rerun_in_int32(apsp, w, extra):
     """Paths far longer than the cap: the truncated pass cannot be certified and the int32
     pass must produce the exact closure."""
-    n = 2200
+    n = 4200
     h = _path_graph(n, w, extra, seed=w)
     assert_dist_equal(_close(apsp, h), oracle.fw(h, threads=THREADS), f"w={w}")
 
 
 def test_heavy_weights_skip_the_16bit_pass(apsp):
-    n = 2048
+    n = 4096
     h = workloads.er_graph(n, 0.02, "int32", lo=1, hi=50000, seed=5)
     assert_dist_equal(_close(apsp, h), oracle.fw(h, threads=THREADS), "heavy")
 
 
 def test_base_workspace_uses_the_plain_phase3(apsp):
     """A workspace without room for the packed panels is accepted; the result is identical."""
-    n = 2304
+    n = 4352
     h = workloads.er_graph(n, 0.01, "int32", lo=1, hi=100, seed=6)
     full = apsp.apsp_fw_workspace_bytes(n, n)
     assert full > 256
