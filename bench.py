@@ -54,10 +54,10 @@ SMS_NOMINAL = 152
 LANES_PER_SM = 128
 MAX_SM_MHZ = 2070.0
 # DRAM traffic of one FW phase-3 launch per C element (dram__bytes_read.sum +
-# dram__bytes_write.sum from one ncu capture at n = 8192, block 50: 467.8 MB over 8064^2 C
-# elements), valid only for the kernel sources it was taken on (hash below).
-PHASE3_DRAM_BYTES_PER_C_ELEM = 7.197
-PHASE3_TRAFFIC_SRC_HASH = "028455458547e84a"
+# dram__bytes_write.sum from one ncu capture of the 16-bit phase-3 kernel at n = 8192, block
+# 37: 463.6 MB over 8064^2 C elements), valid only for the kernel sources it was taken on.
+PHASE3_DRAM_BYTES_PER_C_ELEM = 7.129
+PHASE3_TRAFFIC_SRC_HASH = "4f7333eca354027e"
 TGEMM_SOURCES = ("tgemm.cu", "tgemm.cuh", "slab.cuh", "common.cuh")
 
 
@@ -401,11 +401,11 @@ def run_ours(args, w, rank, world, local_rank):
     peak_max = 2.0 * sms * LANES_PER_SM * MAX_SM_MHZ * 1e6 / 1e12
     achieved = 2.0 * k_pairs / (k_ms * 1e-3) / 1e12 if k_ms > 0 else None
     sm_mhz = clocks.get("sm_mhz")
-    traffic = None
-    if dom_mode == 2 and tgemm_src_hash() == PHASE3_TRAFFIC_SRC_HASH:
-        traffic = {"bytes_per_launch": round(PHASE3_DRAM_BYTES_PER_C_ELEM * (n - 128) ** 2),
-                   "algorithmic_bytes_per_launch": 8 * (n - 128) ** 2,
-                   "source": "ncu dram bytes of one phase-3 launch at n=8192, scaled by (n-128)^2"}
+    traffic, traffic_note = None, None
+    if dom_mode == 2 and tgemm_src_hash() == PHASE3_TRAFFIC_SRC_HASH and w["dtype"] == "int32" and n >= 4096:
+        traffic = round(PHASE3_DRAM_BYTES_PER_C_ELEM * (n - 128) ** 2)
+        traffic_note = (f"dram bytes per launch from one ncu capture of the 16-bit phase-3 kernel at n=8192, scaled "
+                        f"by (n-128)^2; algorithmic {8 * (n - 128) ** 2} B (each C tile read and written once)")
     nb = -(-n // 128)
     fw16 = w["algo"] == "fw" and w["dtype"] == "int32" and n >= 4096
     # Every kernel of ours that is launched per step, including the alternative launches that
@@ -439,7 +439,7 @@ def run_ours(args, w, rank, world, local_rank):
                                                 if achieved and sm_mhz else None),
                      "peak_basis": f"{sms} SMs x {LANES_PER_SM} lanes x 1 pair/lane/clk x {MAX_SM_MHZ:.0f} MHz x 2 ops",
                      "launches": k_launches, "avg_launch_ms": round(k_ms / max(1, k_launches), 4),
-                     "traffic": traffic},
+                     "traffic": traffic, "traffic_note": traffic_note},
         "clocks": clocks,
         "e2e": {"value": round(e2e_val, 2) if e2e_val else None, "unit": "Gop/s",
                 "h2d_bytes_per_step": mat_bytes, "d2h_bytes_per_step": mat_bytes},
