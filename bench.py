@@ -418,13 +418,17 @@ def run_ours(args, w, rank, world, local_rank):
         arith = "fp32 packed add + 3-input min"
     elif w["algo"] == "gemm":
         arith = "packed 16-bit pairs, one DPX add-min per two pairs (exact: max A + max B < 0x3FFF)"
+    elif w["algo"] == "rkleene":
+        arith = ("products of >= 1e9 pairs on packed 16-bit pairs when their operands' largest finite entries sum "
+                 "below 0x3FFF (device-side scan, exact); other products and the FW leaves in fp32 on int32 bit "
+                 "patterns (exact: every distance < 2^24)")
     elif fw16:
         arith = ("FW phase 3 on packed 16-bit pairs (one DPX add-min per two pairs), the closure truncated at "
                  "0x3FFF and certified exact on the device (largest stored value below the cap + largest weight "
                  "< cap; else an int32 pass); phases 1-2 exact in fp32 on int32 bit patterns")
     else:
         arith = "fp32 packed add + 3-input min on int32 bit patterns (exact: every distance < 2^24)"
-    dtype_tag = "f32" if w["dtype"] != "int32" else ("i16x2" if (fw16 or w["algo"] == "gemm") else "i32")
+    dtype_tag = "f32" if w["dtype"] != "int32" else ("i16x2" if (fw16 or w["algo"] in ("gemm", "rkleene")) else "i32")
     line = {
         "metric": "(min,+) Gop/s (2n^3/s)", "value": round(value, 2), "unit": "Gop/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 2),

@@ -115,8 +115,14 @@ int tropical_gemm(void *C, const void *A, const void *B, int64_t M, int64_t N, i
  * tile: block size b; 0 selects the default (128).  Supported: 128.
  * d must be 16-byte aligned.  The workspace holds 256 bytes of bound words (int32 matrices
  * whose (n - 1) * largest finite weight < 2^24 run in exact fp32 arithmetic on their bit
- * patterns; others in int32) and, when ld is not a multiple of 4, an aligned copy of the
- * matrix (n x round_up(n, 4) elements). */
+ * patterns; others in int32), when ld is not a multiple of 4 an aligned copy of the matrix
+ * (n x round_up(n, 4) elements), and last, for int32 with n >= 4096, room for the two panels
+ * packed into 16-bit pairs (2 x 64 x round_up(n, 4) words).  With that room, and a largest
+ * weight of at most 0x0FFF, phase 3 runs on the packed pairs (two (min,+) pairs per DPX
+ * operation) in the (min,+) semiring truncated at 0x3FFF; a device-side certificate (largest
+ * stored value below 0x3FFF plus the largest weight stays below 0x3FFF) proves the result
+ * exact, and otherwise the int32 Floyd-Warshall runs again over it.  Results are bit-exact
+ * either way.  A workspace without the packed room is accepted and skips that path. */
 size_t apsp_fw_workspace_bytes(int64_t n, int64_t ld, int dtype, int tile);
 int apsp_fw(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int tile, void *ws,
             size_t ws_bytes, void *stream);
@@ -129,8 +135,12 @@ int apsp_fw(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int tile
  * multiple of 128.  cutoff: 0 selects the default (256); it must be >= 128.
  * d must be 16-byte aligned.  The workspace holds the 256 bytes of bound words (as for
  * apsp_fw), a copy of the block being overwritten (h x round_up(h, 4) elements,
- * h = ceil(n/2) rounded up to a multiple of 128, when n > cutoff) and, when ld is not a
- * multiple of 4, an aligned copy of the matrix. */
+ * h = ceil(n/2) rounded up to a multiple of 128, when n > cutoff), when ld is not a multiple
+ * of 4 an aligned copy of the matrix, and last, for int32, room for the operands of the
+ * largest product packed into 16-bit pairs (h x round_up(ceil(h/2), 4) + ceil(h/2) x
+ * round_up(h, 4) words).  With that room, a product of at least 10^9 pairs whose operands'
+ * largest finite entries sum below 0x3FFF (a device-side scan) runs on the packed pairs; the
+ * result is identical.  A workspace without the packed room is accepted. */
 size_t apsp_rkleene_workspace_bytes(int64_t n, int64_t ld, int dtype, int cutoff);
 int apsp_rkleene(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int cutoff,
                  void *ws, size_t ws_bytes, void *stream);

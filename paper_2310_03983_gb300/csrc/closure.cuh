@@ -21,18 +21,31 @@ size_t fw16_panel_bytes(int64_t n);
 // of the certificate cost more than the faster arithmetic saves).
 constexpr int64_t kFw16MinN = 4096;
 
+// Scratch for (min,+) products on packed 16-bit pairs: a block of 8 words (maxima of the
+// operands, the "packed" flag) and room for the packed copies of the largest product.
+struct Packed16 {
+  int *words;
+  void *scratch;
+  size_t bytes;
+};
+
 // R-Kleene on an aligned, normalised block, scratch of rkleene_scratch_bytes (rkleene.cu).
+// pk.scratch (may be null): rk16_scratch_bytes(n, cutoff) for 16-bit products (int32).
 int rkleene_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, int cutoff, Bound b, void *scratch,
-                    cudaStream_t s);
+                    cudaStream_t s, Packed16 pk = {nullptr, nullptr, 0});
 size_t rkleene_scratch_bytes(int64_t n, int cutoff);
+size_t rk16_scratch_bytes(int64_t n, int cutoff);
 
 // algo 0 = FW, 1 = R-Kleene; param = tile (FW) or cutoff (R-Kleene).
 int closure_entry(int algo, void *d, int64_t n, int64_t ld, int dtype, const void *inf, int param, void *ws,
                   size_t ws_bytes, void *stream);
 size_t closure_workspace_bytes(int algo, int64_t n, int64_t ld, int param, int dtype);
 
-// (min,+) product of aligned operands through the TMA engine (rkleene.cu).
+// (min,+) product of aligned operands through the TMA engine (rkleene.cu).  With pk.scratch
+// large enough, an int32 product whose largest finite operand entries sum below kCap16 (a
+// device-side scan) runs on packed 16-bit pairs; the plain launch returns at once then.
 int gemm_aligned(void *C, int64_t ldc, const void *A, int64_t lda, const void *B, int64_t ldb, int64_t M, int64_t N,
-                 int64_t K, int dtype, bool acc, int inf_i, Bound b, cudaStream_t s);
+                 int64_t K, int dtype, bool acc, int inf_i, Bound b, cudaStream_t s,
+                 Packed16 pk = {nullptr, nullptr, 0});
 
 }  // namespace apsp

@@ -36,13 +36,18 @@ def test_host_side_calls_without_gpu():
     assert lib.apsp_status_str(0) == b"ok"
     f = lib.apsp_rkleene_workspace_bytes
     f.restype, f.argtypes = ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int]
-    # n <= cutoff: no scratch; n = 32768: one 16384 x 16384 int32 block
+    # n <= cutoff: no scratch; n = 32768: one 16384 x 16384 block, plus (int32 only) the packed
+    # 16-bit copies of the largest product's operands (2 x 16384 x 8192 words)
     assert f(256, 256, 0, 256) == 256  # bound words only
-    assert f(32768, 32768, 0, 256) == 256 + 16384 * 16384 * 4
+    assert f(32768, 32768, 1, 256) == 256 + 16384 * 16384 * 4
+    assert f(32768, 32768, 0, 256) == 256 + 16384 * 16384 * 4 + 2 * 16384 * 8192 * 4
     g = lib.apsp_fw_workspace_bytes
     g.restype, g.argtypes = ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int]
     assert g(1000, 1000, 0, 0) == 256
     assert g(1001, 1001, 0, 0) >= 256 + 1001 * 1004 * 4
+    # int32 FW from 4096 vertices: room for the packed 16-bit panels (n x 64 + 64 x n words)
+    assert g(4096, 4096, 1, 0) == 256
+    assert g(4096, 4096, 0, 0) == 256 + 2 * 4096 * 64 * 4
     # argument errors return before any CUDA call: n < 0, bad dtype
     h = lib.apsp_fw
     h.restype = ctypes.c_int

@@ -96,3 +96,21 @@ def test_base_workspace_uses_the_plain_phase3(apsp):
     assert np.array_equal(a, b) and np.array_equal(a, c)
     rows = np.random.default_rng(7).choice(n, 16, replace=False)
     assert_dist_equal(a[rows], oracle.dijkstra_rows(h, rows, threads=THREADS), "rows")
+
+
+@pytest.mark.parametrize("n,hi", [(2600, 100), (2300, 3000)])
+def test_rkleene_packed_products_match_oracle(apsp, n, hi):
+    """R-Kleene with products of >= 10^9 pairs on packed 16-bit pairs (operand maxima summing
+    below 0x3FFF, checked per product on the device); with hi = 3000 some products exceed the
+    cap and take the plain path.  Bit-exact, and identical with a workspace without the packed
+    room."""
+    h = workloads.er_graph(n, 0.01, "int32", lo=1, hi=hi, seed=n)
+    d = torch.from_numpy(h).cuda()
+    apsp.apsp_rkleene(d, cutoff=256)
+    got = d.cpu().numpy()
+    assert apsp.apsp_device_status() == 0
+    assert_dist_equal(got, oracle.fw(h, threads=THREADS), f"rkleene n={n} hi={hi}")
+    base = apsp.apsp_rkleene_workspace_bytes(n, n, torch.float32, 256)  # same size minus the packed room
+    d2 = torch.from_numpy(h).cuda()
+    apsp.apsp_rkleene(d2, cutoff=256, ws=torch.empty(base, dtype=torch.uint8, device="cuda"))
+    assert np.array_equal(d2.cpu().numpy(), got)
