@@ -263,6 +263,7 @@ def config_of(args, w, world):
                 "weights": "even requests int32 uniform[1,100], odd float32 lognormal(0,1)",
                 "graphs": f"library of {w['library']} seeded graphs, request k carries graph k mod {w['library']}",
                 "admission": "HBM arena 16 GiB, first fit", "batching": "n <= 1024 continuously batched",
+                "plans": "n > 1024: the trained cost model (cost_model.json) picks FW, R-Kleene or squaring",
                 "parallelism": f"replicas{world}"}
     if w["algo"] == "batched" and w.get("gen") == "paper":
         return {"workload": args.workload, "graphs": w["count"],
@@ -673,13 +674,15 @@ def run_serve(args, w, rank, world, local_rank):
     ns, ps, lib = workloads.request_library(w["library"], w["n_lo"], w["n_hi"], seed=0)
     t_arr, _, _, _ = workloads.poisson_requests(w["rate"], args.serve_seconds, seed=0)
     # warm-up: every distinct size once through both paths (first-launch set-up)
-    srv = serve.Server(device=dev, arena_bytes=16 << 30, small_max=1024, slots=4)
-    srv.serve(serve.make_requests(np.linspace(0, 0.01, len(lib)), lib))
+    from paper_2310_03983_gb300 import planner as apsp_planner
+    model = apsp_planner.CostModel.load(apsp_planner.DEFAULT_MODEL, device=dev)
+    srv = serve.Server(device=dev, arena_bytes=16 << 30, small_max=1024, slots=4, planner=model)
+    srv.serve(serve.make_requests(np.linspace(0, 0.01, len(lib)), lib, density=list(ps)))
     if world > 1:
         dist.barrier()
     sampler = ClockSampler(local_rank)
     sampler.start()
-    reqs = serve.make_requests(t_arr, lib)
+    reqs = serve.make_requests(t_arr, lib, density=list(ps))
     st = srv.serve(reqs)
     clocks = sampler.stop()
     base = serve.serve_one_at_a_time(serve.make_requests(t_arr, lib), device=dev)

@@ -47,17 +47,18 @@ int launch_fw_diag(void *d, int64_t ld, int64_t n, int64_t kb, int dtype, cudaSt
 // Phase 3 on packed 16-bit pairs (int32 matrices).
 //
 // The closure is computed in the (min,+) semiring truncated at CAP = 0x3FFF: values at or above
-// CAP all mean "CAP".  Truncation t(v) = min(v, CAP) is a homomorphism of (min,+) on [0, inf]
-// (t(min(a, b)) = min(t(a), t(b)), t(a + b) = t(t(a) + t(b))), so a computation that mixes
-// exact int32 steps (phases 1 and 2) with truncated ones (phase 3 on 16-bit pairs: operands
-// capped at CAP, a capped result discarded in favour of the old entry) keeps the invariant
-// t(stored) = t(exact Floyd-Warshall value) for every entry, and every finite stored value is
-// the length of a real path.  At the end, every pair whose distance is below CAP holds it
-// exactly.  A pair with CAP <= distance < infinity would need a vertex on its shortest path
-// whose distance lies in [CAP - w_max, CAP); so if the largest stored value below CAP plus the
-// largest weight stays below CAP, no such pair exists and the result is the exact closure.
-// Otherwise (checked on the device) the int32 Floyd-Warshall runs again over the stored
-// matrix, whose entries lie between the distances and the weights, and so closes it exactly.
+// CAP all mean "at least CAP".  Truncation t(v) = min(v, CAP) is a homomorphism of (min,+) on
+// [0, inf] (t(min(a, b)) = min(t(a), t(b)), t(a + b) = t(t(a) + t(b))), so a computation that
+// mixes exact int32 steps (phases 1 and 2) with truncated ones (phase 3 on 16-bit pairs:
+// operands capped at CAP, the result min(old entry, capped minimum)) keeps the invariant
+// t(stored) = t(exact Floyd-Warshall value) for every entry.  Every stored value below CAP is
+// therefore an exact distance of the pass, and at the end every pair whose distance is below
+// CAP holds it exactly.  A pair with CAP <= distance < infinity would need a vertex on its
+// shortest path whose distance lies in [CAP - w_max, CAP); so if the largest stored value below
+// CAP plus the largest weight stays below CAP, no such pair exists: every entry at or above CAP
+// is unreachable and becomes the sentinel, which gives the exact closure.  Otherwise (checked
+// on the device) the same mapping leaves a matrix whose entries lie between the distances and
+// the weights (every edge is below CAP), and the int32 Floyd-Warshall runs again over it.
 // Words of the bound block used here:
 //   [0] largest finite weight (a1), [4] 16-bit phase 3 in use, [5] largest stored value < CAP,
 //   [6] the int32 pass must run again.
@@ -98,15 +99,18 @@ __global__ void __launch_bounds__(256) fw_pack16_kernel(const int *d, int64_t ld
   }
 }
 
-// words[5] = largest stored value below CAP; then words[6] = 1 when it plus the largest weight
-// reaches CAP (the truncated result cannot be certified).
-__global__ void __launch_bounds__(256) fw16_certify_kernel(const int *d, int64_t ld, int64_t n, int *words) {
+// words[5] = largest stored value below CAP, and every entry at or above CAP becomes the
+// sentinel; then words[6] = 1 when words[5] plus the largest weight reaches CAP (the truncated
+// result cannot be certified).
+__global__ void __launch_bounds__(256) fw16_certify_kernel(int *d, int64_t ld, int64_t n, int inf, int *words) {
   if (!words[4]) return;
   int m = 0;
   for (int64_t i = blockIdx.x; i < n; i += gridDim.x)
     for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
-      const int v = d[i * ld + j];
+      int *e = d + i * ld + j;
+      const int v = *e;
       if (v < kCap16) m = max(m, v);
+      else if (v != inf) *e = inf;
     }
   m = __reduce_max_sync(0xffffffffu, m);
   if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(words + 5, m);
@@ -157,7 +161,8 @@ int fw_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bound b, cu
   p.status = status_word();
   p.wmax = b.w;
   p.wmult = b.mult;
-  if (!(panels16 && dtype == APSP_I32 && b.w && nb > 1)) return fw_loop(d, n, ld, dtype, mA, mB, mC, p, nullptr, s);
+  if (!(panels16 && dtype == APSP_I32 && b.w && nb > 1 && inf_i > kCap16))
+    return fw_loop(d, n, ld, dtype, mA, mB, mC, p, nullptr, s);
 
   int *words = const_cast<int *>(b.w);
   int *A16 = reinterpret_cast<int *>(panels16);
@@ -199,7 +204,7 @@ int fw_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bound b, cu
       trace_end(s, tev, kModeFwRest, rest * rest * bk);
     }
   }
-  fw16_certify_kernel<<<(int)std::min<int64_t>(n, cap), 256, 0, s>>>(reinterpret_cast<const int *>(d), ld, n, words);
+  fw16_certify_kernel<<<(int)std::min<int64_t>(n, cap), 256, 0, s>>>(reinterpret_cast<int *>(d), ld, n, inf_i, words);
   APSP_LAUNCH_CHECK();
   fw16_verdict_kernel<<<1, 1, 0, s>>>(words);
   APSP_LAUNCH_CHECK();

@@ -43,6 +43,7 @@ struct ArithF32 {
   static __device__ __forceinline__ int to(T v) { return __float_as_int(v); }
   static __device__ __forceinline__ T mn(T a, T b) { return fminf(a, b); }
   static __device__ __forceinline__ T collapse(T v, int) { return v; }
+  static __device__ __forceinline__ T collapse_truncated(T v) { return v; }
   // Column pairs: {A[i][k], A[i][k]} + {B[k][c], B[k][c+1]} in one packed add (the B pair comes
   // straight from a 128-bit load, the duplicated A value is built once per row and k), the
   // four adds of one duplicated A value issued back to back so it stays in the operand reuse
@@ -125,10 +126,16 @@ struct ArithInt {
     if (P16) return (int)__viaddmin_s16x2((unsigned)a, (unsigned)b, (unsigned)c);
     return __viaddmin_s32(a, b, c);
   }
+  // Fold the two lanes; a result at the cap (or at a sentinel below it) means unreachable.
   static __device__ __forceinline__ T collapse(T v, int inf) {
     if (!P16) return v;
     const int m = min(v & 0xFFFF, (int)((unsigned)v >> 16));
-    return m >= kCap16 ? inf : m;
+    return m >= min(kCap16, inf) ? inf : m;
+  }
+  // Fold the two lanes only: the result stays in [0, kCap16] (truncated closures).
+  static __device__ __forceinline__ T collapse_truncated(T v) {
+    if (!P16) return v;
+    return min(v & 0xFFFF, (int)((unsigned)v >> 16));
   }
   template <typename A>
   static __device__ __forceinline__ void slab_full(const int *As, const int *Bs, int tm, int tn, A (&acc)[8][8]) {

@@ -125,7 +125,8 @@ __device__ __forceinline__ void consume(const TileProblem &p, const Smem &sm, in
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) acc[i][j] = AR::collapse(acc[i][j], p.inf_i);
+      for (int j = 0; j < 8; ++j)
+        acc[i][j] = MODE == kModeFwRest16 ? AR::collapse_truncated(acc[i][j]) : AR::collapse(acc[i][j], p.inf_i);
     if (ACC) {
       if (!mbar_wait(sm.cfull, cphase, p.status)) return;
 #pragma unroll

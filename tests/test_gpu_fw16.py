@@ -114,3 +114,19 @@ def test_rkleene_packed_products_match_oracle(apsp, n, hi):
     d2 = torch.from_numpy(h).cuda()
     apsp.apsp_rkleene(d2, cutoff=256, ws=torch.empty(base, dtype=torch.uint8, device="cuda"))
     assert np.array_equal(d2.cpu().numpy(), got)
+
+
+@pytest.mark.parametrize("inf", [1 << 20, 5000])
+def test_custom_sentinel(apsp, inf):
+    """A sentinel above the 16-bit cap keeps the packed phase 3 (unreachable pairs must come
+    back as exactly that sentinel); one below it takes the plain phase 3.  Bit-exact both ways."""
+    n = 4096
+    h = workloads.er_graph(n, 0.003, "int32", lo=1, hi=40, seed=inf % 97)
+    h[:, :64] = INF          # columns nobody reaches except themselves
+    np.fill_diagonal(h, 0)
+    hc = np.where(h >= INF, inf, h).astype(np.int32)
+    d = torch.from_numpy(hc).cuda()
+    apsp.apsp_fw(d, inf=inf)
+    assert apsp.apsp_device_status() == 0
+    want = oracle.fw(hc, inf=inf, threads=THREADS)
+    assert_dist_equal(d.cpu().numpy(), want, f"inf={inf}")

@@ -167,6 +167,19 @@ def test_tropical_gemm_16bit_path_equals_others(apsp, M, N, K):
     assert np.array_equal(outs[0], outs[2]) and np.array_equal(outs[1], outs[3])
 
 
+def test_tropical_gemm_16bit_small_sentinel(apsp):
+    """A sentinel below the 16-bit cap: finite sums that reach it must come back as the
+    sentinel, exactly as on the int32 path."""
+    rng = np.random.default_rng(17)
+    inf = 1000
+    M, N, K = 150, 140, 90
+    a = np.where(rng.random((M, K)) < 0.7, rng.integers(0, 900, (M, K)), inf).astype(np.int32)
+    b = np.where(rng.random((K, N)) < 0.7, rng.integers(0, 900, (K, N)), inf).astype(np.int32)
+    C = torch.empty((M, N), dtype=torch.int32, device="cuda")
+    apsp.tropical_gemm(C, torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), inf=inf)
+    assert_dist_equal(C.cpu().numpy(), oracle.minplus(a, b, inf=inf), "inf=1000")
+
+
 def test_tropical_gemm_identity_and_k0(apsp):
     n = 200
     eye = np.full((n, n), INF, np.int32)

@@ -27,8 +27,10 @@ def test_server_results_equal_alone_and_in_the_mix(apsp):
     from paper_2310_03983_gb300 import serve
     ns, ps, lib = workloads.request_library(24, n_lo=48, n_hi=1500, seed=3)
     t, _, _, _ = workloads.poisson_requests(rate=150.0, duration=0.8, seed=1)
-    reqs = serve.make_requests(t, lib)
-    srv = serve.Server(arena_bytes=256 << 20, small_max=512, slots=4, keep_results=True)
+    from paper_2310_03983_gb300 import planner
+    model = planner.CostModel.load(planner.DEFAULT_MODEL)
+    reqs = serve.make_requests(t, lib, density=list(ps))
+    srv = serve.Server(arena_bytes=256 << 20, small_max=512, slots=4, keep_results=True, planner=model)
     st = srv.serve(reqs)
     assert st["requests"] == len(reqs) > 50
     assert st["launches"]["batch"] > 0 and st["launches"]["solo"] > 0
@@ -36,10 +38,11 @@ def test_server_results_equal_alone_and_in_the_mix(apsp):
     assert st["p50"] <= st["p99"]
     for r in reqs:
         alone = torch.from_numpy(lib[r.rid % len(lib)]).cuda()
-        if r.plan[0] == "batched":
+        algo, param = r.plan
+        if algo == "batched":
             apsp.apsp_close_cta(alone)
-        else:
-            apsp.apsp_fw(alone)
+        else:  # the cost model's plan, run alone
+            planner.run_config(alone, algo, param)
         assert_dist_equal(r.result.numpy(), alone.cpu().numpy(), f"request {r.rid} n={r.n}")
     for g in (0, 1, 5):  # and the oracle, on a few distinct graphs
         r = next(r for r in reqs if r.rid % len(lib) == g)
