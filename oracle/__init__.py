@@ -24,6 +24,9 @@ What is here, each citing the passage it follows:
                          diagonal and unreachable pairs, a real last edge that is tight
                          (d[i, p] + w[p, j] = d[i, j]), and walks back to the source whose
                          edge costs re-sum to d[i, j] (the path recovery of Sec. 2).
+  * ``bellman_ford_rows`` -- single-source distances by Bellman-Ford, valid with negative
+                         weights, with negative-cycle detection: the independent check for
+                         signed graphs (Sec. 3.1 only excludes negative cycles).
   * ``reachability``  -- the transitive closure by breadth-first search (which pairs are
                          connected at all; needs no arithmetic).
   * ``check_invariants`` -- properties every closed distance matrix has: zero diagonal,
@@ -79,6 +82,11 @@ def _bind(lib):
     lib.oracle_dijkstra_rows_i64.argtypes = [i64p, I64, I64, i64p, I64, i64p, INT]
     lib.oracle_dijkstra_rows_f64.argtypes = [f64p, I64, i64p, I64, f64p, INT]
     f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+    i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+    lib.oracle_bellman_ford_rows_i64.argtypes = [i64p, I64, I64, i64p, I64, i64p, i32p, INT]
+    lib.oracle_bellman_ford_rows_f64.argtypes = [f64p, I64, i64p, I64, f64p, i32p, INT]
+    lib.oracle_bellman_ford_rows_i64.restype = None
+    lib.oracle_bellman_ford_rows_f64.restype = None
     lib.oracle_fw_pred_i64.argtypes = [i64p, i64p, I64, I64]
     lib.oracle_fw_pred_f64.argtypes = [f64p, i64p, I64]
     lib.oracle_last_hop_i64.argtypes = [i64p, i64p, i64p, I64, i64p, I64, I64, INT]
@@ -294,6 +302,24 @@ def check_predecessors(pred: np.ndarray, d: np.ndarray, h: np.ndarray, inf: int 
         elif not np.all(close(cost, D[i, js])):
             bad.append(f"row {i}: a walked path's cost differs from d[i,j]")
     return bad
+
+
+def bellman_ford_rows(w: np.ndarray, sources, inf: int = INF_I32, threads: int | None = None, lib=None):
+    """(distances from each source, negative-cycle flag per source) by Bellman-Ford.  Negative
+    weights allowed; int32/int64 -> exact int64 arithmetic, float -> fp64."""
+    lib = lib or load()
+    n = w.shape[0]
+    src = np.ascontiguousarray(sources, dtype=np.int64)
+    neg = np.zeros(len(src), np.int32)
+    if w.dtype.kind in "iu":
+        W = np.ascontiguousarray(np.minimum(w.astype(np.int64), inf))
+        out = np.empty((len(src), n), np.int64)
+        lib.oracle_bellman_ford_rows_i64(W, n, int(inf), src, len(src), out, neg, _threads(threads))
+        return (out.astype(np.int32) if w.dtype == np.int32 else out), neg.astype(bool)
+    W = np.ascontiguousarray(w, dtype=np.float64)
+    out = np.empty((len(src), n), np.float64)
+    lib.oracle_bellman_ford_rows_f64(W, n, src, len(src), out, neg, _threads(threads))
+    return out, neg.astype(bool)
 
 
 def edge_mask(h: np.ndarray, inf: int = INF_I32) -> np.ndarray:

@@ -24,6 +24,10 @@
  *     argmin of Sec. 3.1 restricted to the last edge), -1 on the diagonal and where the
  *     minimum is unreachable.  The float32 variant adds in float32 (one rounding per sum),
  *     the precision in which the library takes the same decision.
+ *   - oracle_bellman_ford_rows_i64 / _f64: single-source distances by Bellman-Ford (n - 1 rounds
+ *     relaxing every edge), valid with negative weights; a further round that still improves
+ *     a distance reports a negative cycle reachable from the source.  The independent check for
+ *     graphs with negative edges (Sec. 3.1 allows them as long as no cycle is negative).
  *   - oracle_dijkstra_rows_i64 / _f64: single-source shortest paths from selected sources by
  *     textbook O(n^2) array Dijkstra (valid because every weight is >= 0; Sec. 3.1 assumes
  *     no negative cycles and the generator draws costs >= 0, Sec. 3.4).  It is a second,
@@ -321,6 +325,76 @@ void oracle_last_hop_f32(const float *d, const float *w, int64_t *pred, int64_t 
           if (s < best) { best = s; arg = k; }
         }
       pred[r * n + j] = arg;
+    }
+  }
+}
+
+/* Bellman-Ford from each source in src[0..nsrc): out is nsrc x n, neg[s] = 1 when a negative
+ * cycle is reachable from src[s] (its row is then not meaningful).  int64, entries >= inf are
+ * missing edges; the diagonal of w is ignored. */
+void oracle_bellman_ford_rows_i64(const int64_t *w, int64_t n, int64_t inf, const int64_t *src, int64_t nsrc,
+                                  int64_t *out, int *neg, int threads) {
+  set_threads(threads);
+#pragma omp parallel for schedule(dynamic, 1) if (threads > 1)
+  for (int64_t s = 0; s < nsrc; ++s) {
+    int64_t *dist = out + s * n;
+    for (int64_t v = 0; v < n; ++v) dist[v] = inf;
+    dist[src[s]] = 0;
+#if ORACLE_PLANT == 7 /* plant 7: one relaxation round too few */
+    const int64_t rounds = n - 1 > 0 ? n - 2 : 0;
+#else
+    const int64_t rounds = n - 1;
+#endif
+    for (int64_t r = 0; r < rounds; ++r) {
+      int changed = 0;
+      for (int64_t u = 0; u < n; ++u) {
+        if (dist[u] >= inf) continue;
+        for (int64_t v = 0; v < n; ++v) {
+          const int64_t wuv = w[u * n + v];
+          if (v == u || wuv >= inf) continue;
+          if (dist[u] + wuv < dist[v]) { dist[v] = dist[u] + wuv; changed = 1; }
+        }
+      }
+      if (!changed) break;
+    }
+    neg[s] = 0;
+    for (int64_t u = 0; u < n && !neg[s]; ++u) {
+      if (dist[u] >= inf) continue;
+      for (int64_t v = 0; v < n; ++v) {
+        const int64_t wuv = w[u * n + v];
+        if (v != u && wuv < inf && dist[u] + wuv < dist[v]) { neg[s] = 1; break; }
+      }
+    }
+  }
+}
+
+void oracle_bellman_ford_rows_f64(const double *w, int64_t n, const int64_t *src, int64_t nsrc, double *out,
+                                  int *neg, int threads) {
+  set_threads(threads);
+#pragma omp parallel for schedule(dynamic, 1) if (threads > 1)
+  for (int64_t s = 0; s < nsrc; ++s) {
+    double *dist = out + s * n;
+    for (int64_t v = 0; v < n; ++v) dist[v] = INFINITY;
+    dist[src[s]] = 0.0;
+    for (int64_t r = 0; r < n - 1; ++r) {
+      int changed = 0;
+      for (int64_t u = 0; u < n; ++u) {
+        if (isinf(dist[u])) continue;
+        for (int64_t v = 0; v < n; ++v) {
+          const double wuv = w[u * n + v];
+          if (v == u || isinf(wuv)) continue;
+          if (dist[u] + wuv < dist[v]) { dist[v] = dist[u] + wuv; changed = 1; }
+        }
+      }
+      if (!changed) break;
+    }
+    neg[s] = 0;
+    for (int64_t u = 0; u < n && !neg[s]; ++u) {
+      if (isinf(dist[u])) continue;
+      for (int64_t v = 0; v < n; ++v) {
+        const double wuv = w[u * n + v];
+        if (v != u && !isinf(wuv) && dist[u] + wuv < dist[v]) { neg[s] = 1; break; }
+      }
     }
   }
 }

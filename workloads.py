@@ -94,6 +94,28 @@ def paper_graph(V: int, rho: float, alpha: int = 100, seed: int = 0, inf: int = 
     return H
 
 
+def signed_graph(n: int, p: float, dtype="int32", lo=1, hi=100, pot: float = 60, seed: int = 0,
+                 inf: int = INF_I32):
+    """A directed graph with negative edges and no negative cycle, by potentials: start from
+    er_graph(n, p) with non-negative weights w and draw a potential pi[v] uniform in [0, pot]
+    (integers for int32); the edge u -> v gets w(u, v) + pi[u] - pi[v].  Every cycle keeps its
+    (non-negative) weight, and every distance becomes d(u, v) + pi[u] - pi[v].
+    Returns (cost matrix, pi)."""
+    if np.dtype(dtype) == np.int32:
+        h = er_graph(n, p, "int32", lo=lo, hi=hi, seed=seed, inf=inf).astype(np.int64)
+        rng = np.random.Generator(np.random.PCG64([int(seed), 0x504F5445]))
+        pi = rng.integers(0, int(pot), size=n, endpoint=True).astype(np.int64)
+        out = np.where(h < inf, h + pi[:, None] - pi[None, :], inf)
+        np.fill_diagonal(out, 0)
+        return out.astype(np.int32), pi
+    h = er_graph(n, p, "float32", dist="uniform", lo=lo, hi=hi, seed=seed).astype(np.float64)
+    rng = np.random.Generator(np.random.PCG64([int(seed), 0x504F5445]))
+    pi = rng.uniform(0.0, float(pot), size=n)
+    out = h + pi[:, None] - pi[None, :]
+    np.fill_diagonal(out, 0.0)
+    return out.astype(np.float32), pi
+
+
 def paper_sweep(count: int = 1000, v_lo: int = 4, v_hi: int = 1000, rho_hi: float = 100.0, alpha: int = 100,
                 seed: int = 0, threads: int | None = None):
     """The paper's experiment inputs (Sec. 3.4 and Sec. 4): ``count`` graphs f(V, rho, alpha) with V
