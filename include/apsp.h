@@ -60,11 +60,12 @@ typedef enum apsp_dtype { APSP_I32 = 0, APSP_F32 = 1 } apsp_dtype;
 typedef enum apsp_status {
   APSP_OK = 0,
   APSP_ERR_ARG = 1,         /* invalid argument; nothing was launched */
-  APSP_ERR_DOMAIN = 2,      /* negative weight or NaN seen on the device */
+  APSP_ERR_DOMAIN = 2,      /* negative weight, NaN or out-of-range entry seen on the device */
   APSP_ERR_NOMEM = 3,       /* workspace allocation failed */
   APSP_ERR_CUDA = 4,        /* a CUDA call or launch failed */
   APSP_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
-  APSP_ERR_UNSUPPORTED = 6  /* no device of compute capability 10.3, or feature absent */
+  APSP_ERR_UNSUPPORTED = 6, /* no device of compute capability 10.3, or feature absent */
+  APSP_ERR_NEGATIVE_CYCLE = 7 /* apsp_fw_signed found a negative cycle on the device */
 } apsp_status;
 
 /* Library version (APSP_VERSION of the build). */
@@ -75,7 +76,8 @@ const char *apsp_status_str(int status);
 
 /* Synchronises `stream`, then reads and clears the current device's sticky data-status
  * word into *out: APSP_OK, or the most severe code a kernel flagged since the last read
- * (APSP_ERR_TIMEOUT, then APSP_ERR_ARG for a skipped batch entry, then APSP_ERR_DOMAIN).
+ * (APSP_ERR_TIMEOUT, then APSP_ERR_ARG for a skipped batch entry, then
+ * APSP_ERR_NEGATIVE_CYCLE, then APSP_ERR_DOMAIN).
  * Returns APSP_OK, or APSP_ERR_CUDA if the synchronisation failed. */
 int apsp_device_status(void *stream, int *out);
 
@@ -144,6 +146,25 @@ int apsp_fw(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int tile
 size_t apsp_rkleene_workspace_bytes(int64_t n, int64_t ld, int dtype, int cutoff);
 int apsp_rkleene(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int cutoff,
                  void *ws, size_t ws_bytes, void *stream);
+
+/* ---- negative weights (Sec. 3.1 assumes only that no cycle is negative) ----------------
+ * Closes d in place like apsp_fw (a1, then blocked Floyd-Warshall), for matrices whose finite
+ * entries may be negative.  The diagonal is set to 0; entries >= inf are missing edges.
+ *   int32: the sentinel must be >= 0x30000000 (NULL: APSP_INF_I32), and (n - 1) times the
+ *     largest |finite entry| must stay below 2^27, so that every distance lies in
+ *     (-2^27, 2^27); this is checked on the device after a1 (else APSP_ERR_DOMAIN and the
+ *     matrix is left normalised, not closed).  Sums that involve a missing edge are kept at or
+ *     above 2^29 and written back as exactly inf.  Arithmetic is int32 throughout.
+ *   float32: +infinity absorbs negative terms; NaN is a data error (APSP_ERR_DOMAIN).
+ * A negative cycle is detected on the device: the closure of the diagonal block that holds the
+ * cycle's largest vertex sees a negative d[v][v], sets APSP_ERR_NEGATIVE_CYCLE, and every later
+ * launch returns at once; the matrix is then unspecified.  A final scan of the diagonal reports
+ * any negative entry the same way.  d must be 16-byte aligned.  The workspace
+ * (apsp_fw_signed_workspace_bytes) holds the 256 bytes of bound words and, when ld is not a
+ * multiple of 4, an aligned copy of the matrix. */
+size_t apsp_fw_signed_workspace_bytes(int64_t n, int64_t ld, int dtype);
+int apsp_fw_signed(void *d, int64_t n, int64_t ld, int dtype, const void *inf, void *ws,
+                   size_t ws_bytes, void *stream);
 
 /* ---- the paper's "Floyd-Warshall on GPU" (Sec. 3.2): repeated (min,+) squaring ----------
  * Closes d in place by D <- D (x) D (Eq. 2) until no entry changes.  After t products D[i][j]

@@ -23,8 +23,8 @@ LIB_PATH = os.path.join(_HERE, "libapsp.so")
 
 APSP_I32, APSP_F32 = 0, 1
 APSP_INF_I32 = 0x3FFFFFFF
-STATUS = {0: "ok", 1: "invalid argument", 2: "negative weight or NaN", 3: "out of memory",
-          4: "CUDA error", 5: "device wait timed out", 6: "unsupported"}
+STATUS = {0: "ok", 1: "invalid argument", 2: "negative weight, NaN or out-of-range entry", 3: "out of memory",
+          4: "CUDA error", 5: "device wait timed out", 6: "unsupported", 7: "negative cycle"}
 
 
 class ApspError(RuntimeError):
@@ -51,6 +51,8 @@ def _load():
         "apsp_rkleene_workspace_bytes": ([i64, i64, i32, i32], sz),
         "apsp_rkleene": ([vp, i64, i64, i32, vp, i32, vp, sz, vp], i32),
         "apsp_probe_minplus": ([i32, i32, i32, i32, vp, vp], i32),
+        "apsp_fw_signed_workspace_bytes": ([i64, i64, i32], sz),
+        "apsp_fw_signed": ([vp, i64, i64, i32, vp, vp, sz, vp], i32),
         "apsp_squaring_workspace_bytes": ([i64, i64, i32], sz),
         "apsp_squaring": ([vp, i64, i64, i32, vp, i32, vp, sz, vp], i32),
         "apsp_predecessors_workspace_bytes": ([i64, i32], sz),
@@ -78,7 +80,7 @@ _lib = _load()
 EXPORTS = ("apsp_version", "apsp_status_str", "apsp_device_status", "apsp_normalise",
            "tropical_gemm_workspace_bytes", "tropical_gemm",
            "apsp_fw_workspace_bytes", "apsp_fw", "apsp_rkleene_workspace_bytes", "apsp_rkleene",
-           "apsp_squaring_workspace_bytes", "apsp_squaring", "apsp_predecessors_workspace_bytes", "apsp_predecessors",
+           "apsp_fw_signed_workspace_bytes", "apsp_fw_signed", "apsp_squaring_workspace_bytes", "apsp_squaring", "apsp_predecessors_workspace_bytes", "apsp_predecessors",
            "apsp_probe_minplus", "apsp_trace_enable", "apsp_trace_read", "apsp_batched_workspace_bytes",
            "apsp_batched", "apsp_mlp_param_count", "apsp_mlp_backward_workspace_bytes", "apsp_mlp_forward",
            "apsp_mlp_loss", "apsp_mlp_backward", "apsp_mlp_adam")
@@ -194,6 +196,20 @@ def apsp_rkleene(d: torch.Tensor, inf=None, cutoff: int = 0, ws: torch.Tensor | 
     """Close d in place by R-Kleene (Sec. 3.3) with blocked-FW leaves of <= cutoff vertices."""
     return _closure(_lib.apsp_rkleene, _lib.apsp_rkleene_workspace_bytes, d, inf, cutoff, ws, stream,
                     "apsp_rkleene")
+
+
+def apsp_fw_signed(d: torch.Tensor, inf=None, ws: torch.Tensor | None = None, stream=None):
+    """Close d in place by blocked Floyd-Warshall when finite entries may be negative (no
+    negative cycle, Sec. 3.1); a negative cycle is reported by apsp_device_status() as 7."""
+    n = d.shape[0]
+    if d.shape[1] != n:
+        raise ValueError("d must be square")
+    p, ld = _mat(d, "d")
+    code = _dtype_code(d)
+    ip, _keep = _inf_arg(inf, code)
+    wp, wb = (None, 0) if ws is None else (ws.data_ptr(), ws.numel() * ws.element_size())
+    _check(_lib.apsp_fw_signed(p, n, ld, code, ip, wp, wb, _stream(stream)), "apsp_fw_signed")
+    return d
 
 
 def apsp_squaring_workspace_bytes(n: int, ld: int, dtype=torch.int32) -> int:

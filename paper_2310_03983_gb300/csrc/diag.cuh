@@ -34,13 +34,29 @@ __device__ __forceinline__ void put_col(const int (&d)[8][8], int *cb, int tm) {
   for (int i = 0; i < 8; ++i) cb[tm + 16 * i] = d[i][J];
 }
 
-// Closes the bk x bk leading part of the register tile d in place.  buf: 512 ints of shared
-// memory.  Entries outside bk x bk are scratch (never read back by callers).
+// Signed closures (negative weights, int32): a published row or column value at or above
+// `thr` is an unreachable entry plus negative terms and is published as exactly `inf`, so no
+// such value can drift down into the finite range.  A negative d[k][k] means a negative cycle:
+// the closure stops (uniformly: every thread reads the same published value) and returns true.
+struct SignedCtl {
+  int inf, thr;
+};
+
 template <bool FLOAT>
-__device__ void close_tile_regs(int (&d)[8][8], int bk, int tm, int tn, int *buf) {
+__device__ __forceinline__ int canon(int v, const SignedCtl *sc) {
+  if (FLOAT || !sc) return v;
+  return v >= sc->thr ? sc->inf : v;
+}
+
+// Closes the bk x bk leading part of the register tile d in place.  buf: 512 ints of shared
+// memory.  Entries outside bk x bk are scratch (never read back by callers).  With sc (signed
+// closures) returns true when a negative cycle was found (the tile is then left partly closed).
+template <bool FLOAT>
+__device__ bool close_tile_regs(int (&d)[8][8], int bk, int tm, int tn, int *buf, const SignedCtl *sc = nullptr) {
+  bool negative = false;
 #pragma unroll
   for (int kh = 0; kh < 8; ++kh) {
-    if (16 * kh >= bk) break;
+    if (16 * kh >= bk || negative) break;
     for (int kl = 0; kl < 16; ++kl) {
       const int k = 16 * kh + kl;
       if (k >= bk) break;
@@ -72,13 +88,22 @@ __device__ void close_tile_regs(int (&d)[8][8], int bk, int tm, int tn, int *buf
         }
       }
       __syncthreads();
+      if (sc) {  // d[k][k] sits in the published row at column k
+        const int dkk = rb[k];
+        if (FLOAT ? __int_as_float(dkk) < 0.0f : dkk < 0) {
+          negative = true;
+          break;
+        }
+      }
       int c[8], r[8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) c[i] = cb[tm + 16 * i];
+      for (int i = 0; i < 8; ++i) c[i] = canon<FLOAT>(cb[tm + 16 * i], sc);
       const int4 r0 = *reinterpret_cast<const int4 *>(rb + 4 * tn);
       const int4 r1 = *reinterpret_cast<const int4 *>(rb + 4 * tn + 64);
-      r[0] = r0.x; r[1] = r0.y; r[2] = r0.z; r[3] = r0.w;
-      r[4] = r1.x; r[5] = r1.y; r[6] = r1.z; r[7] = r1.w;
+      r[0] = canon<FLOAT>(r0.x, sc); r[1] = canon<FLOAT>(r0.y, sc);
+      r[2] = canon<FLOAT>(r0.z, sc); r[3] = canon<FLOAT>(r0.w, sc);
+      r[4] = canon<FLOAT>(r1.x, sc); r[5] = canon<FLOAT>(r1.y, sc);
+      r[6] = canon<FLOAT>(r1.z, sc); r[7] = canon<FLOAT>(r1.w, sc);
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
@@ -86,6 +111,7 @@ __device__ void close_tile_regs(int (&d)[8][8], int bk, int tm, int tn, int *buf
     }
   }
   __syncthreads();  // buf is reused by the caller
+  return negative;
 }
 
 // Load / store the bk x bk tile at T (leading dimension ld, 16-byte aligned rows) into the

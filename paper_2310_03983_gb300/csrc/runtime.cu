@@ -148,11 +148,12 @@ extern "C" const char *apsp_status_str(int s) {
   switch (s) {
     case APSP_OK: return "ok";
     case APSP_ERR_ARG: return "invalid argument";
-    case APSP_ERR_DOMAIN: return "negative weight or NaN in the input";
+    case APSP_ERR_DOMAIN: return "negative weight, NaN or out-of-range entry in the input";
     case APSP_ERR_NOMEM: return "workspace allocation failed";
     case APSP_ERR_CUDA: return "CUDA error";
     case APSP_ERR_TIMEOUT: return "bounded device wait timed out";
     case APSP_ERR_UNSUPPORTED: return "unsupported device or feature";
+    case APSP_ERR_NEGATIVE_CYCLE: return "negative cycle";
     default: return "unknown status";
   }
 }
@@ -165,6 +166,7 @@ extern "C" int apsp_device_status(void *stream, int *out) {
   APSP_CUDA_TRY(cudaMemcpyToSymbol(apsp::g_status, &zero, sizeof(zero)));
   *out = (bits & (1u << APSP_ERR_TIMEOUT)) ? APSP_ERR_TIMEOUT
          : (bits & (1u << APSP_ERR_ARG))    ? APSP_ERR_ARG
+         : (bits & (1u << APSP_ERR_NEGATIVE_CYCLE)) ? APSP_ERR_NEGATIVE_CYCLE
          : (bits & (1u << APSP_ERR_DOMAIN)) ? APSP_ERR_DOMAIN
                                             : APSP_OK;
   return APSP_OK;

@@ -39,6 +39,7 @@ __device__ __forceinline__ int a_off(int r, int kq) { return r * kSlabK + ((kq ^
 // ---------------------------------------------------------------------------------------
 struct ArithF32 {
   typedef float T;
+  static constexpr bool kFloat = true;
   static __device__ __forceinline__ T from(int v) { return __int_as_float(v); }
   static __device__ __forceinline__ int to(T v) { return __float_as_int(v); }
   static __device__ __forceinline__ T mn(T a, T b) { return fminf(a, b); }
@@ -119,6 +120,7 @@ __device__ __forceinline__ void set_acc(float &d, int v) { d = __int_as_float(v)
 template <bool P16>
 struct ArithInt {
   typedef int T;
+  static constexpr bool kFloat = false;
   static __device__ __forceinline__ T from(int v) { return v; }
   static __device__ __forceinline__ int to(T v) { return v; }
   static __device__ __forceinline__ T mn(T a, T b) { return min(a, b); }

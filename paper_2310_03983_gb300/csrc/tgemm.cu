@@ -127,6 +127,12 @@ __device__ __forceinline__ void consume(const TileProblem &p, const Smem &sm, in
 #pragma unroll
       for (int j = 0; j < 8; ++j)
         acc[i][j] = MODE == kModeFwRest16 ? AR::collapse_truncated(acc[i][j]) : AR::collapse(acc[i][j], p.inf_i);
+    if (!AR::kFloat && p.sat) {  // uniform per launch
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = acc[i][j] >= p.sat ? AR::from(p.inf_i) : acc[i][j];
+    }
     if (ACC) {
       if (!mbar_wait(sm.cfull, cphase, p.status)) return;
 #pragma unroll

@@ -57,6 +57,9 @@ struct TileProblem {
   // Not traced by itself: the caller brackets a group of alternative launches with one
   // trace record (only one of them does the work).
   int no_trace;
+  // int32 signed closures (may be 0 = off): a result at or above sat is an unreachable entry
+  // plus negative terms and is written back as exactly inf_i.
+  int sat;
 };
 
 // 16-bit packing of int32 operands for ArithI16x2 (tgemm.cu).  Entries >= inf (and the padding
