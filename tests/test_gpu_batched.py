@@ -11,6 +11,7 @@ from test_gpu_parity import assert_dist_equal
 
 pytestmark = pytest.mark.gpu
 THREADS = os.cpu_count() or 4
+INF = workloads.INF_I32
 
 
 @pytest.fixture(scope="module")
@@ -110,3 +111,22 @@ def test_paper_sweep_through_batched(apsp):
         rows = rng.choice(int(ns[g]), 32, replace=False)
         got = batch.graph(int(g), out).numpy()[rows]
         assert_dist_equal(got, oracle.dijkstra_rows(mats[g], rows, threads=THREADS), f"graph {g}")
+
+
+def test_batched_long_paths(apsp):
+    """Directed paths (diameter n - 1, distances up to 8 * 10^5) mixed with ordinary graphs:
+    every phase-1 and phase-3 relaxation matters; all bit-exact."""
+    def path(n, w):
+        h = np.full((n, n), INF, np.int32)
+        np.fill_diagonal(h, 0)
+        idx = np.arange(n - 1)
+        h[idx, idx + 1] = w
+        return h
+    mats = [path(300, 100), path(400, 40), path(200, 4000), path(160, 1), path(129, 128)]
+    mats += [workloads.er_graph(n, 0.05, "int32", lo=1, hi=100, seed=600 + n) for n in (130, 257, 511)]
+    b = apsp.Batch(mats)
+    apsp.apsp_batched(b)
+    out = b.pool.cpu()
+    assert apsp.apsp_device_status() == 0
+    for g, m in enumerate(mats):
+        assert_dist_equal(b.graph(g, out).numpy(), oracle.fw(m, threads=THREADS), f"graph {g} n={m.shape[0]}")
