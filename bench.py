@@ -38,7 +38,7 @@ import workloads  # noqa: E402
 WORKLOADS = {
     "apsp_fw_n32768": dict(n=32768, p=0.05, dtype="int32", dist="uniform", lo=1, hi=100, algo="fw"),
     "apsp_rkleene_n32768": dict(n=32768, p=0.05, dtype="int32", dist="uniform", lo=1, hi=100, algo="rkleene",
-                                param=256),
+                                param=1024),
     "tgemm_n32768": dict(n=32768, p=0.05, dtype="int32", dist="uniform", lo=1, hi=100, algo="gemm"),
     "apsp_fw_n32768_f32": dict(n=32768, p=0.05, dtype="float32", dist="uniform01", lo=0, hi=1, algo="fw"),
     "apsp_fw_n4096": dict(n=4096, p=0.5, dtype="int32", dist="uniform", lo=1, hi=1000, algo="fw"),
@@ -421,8 +421,8 @@ def run_ours(args, w, rank, world, local_rank):
         arith = "packed 16-bit pairs, one DPX add-min per two pairs (exact: max A + max B < 0x3FFF)"
     elif w["algo"] == "rkleene":
         arith = ("products of >= 1e9 pairs on packed 16-bit pairs when their operands' largest finite entries sum "
-                 "below 0x3FFF (device-side scan, exact); other products and the FW leaves in fp32 on int32 bit "
-                 "patterns (exact: every distance < 2^24)")
+                 "below 0x3FFF (device-side scan, exact); leaves of >= 4096 vertices with the certified 16-bit FW; "
+                 "the rest in fp32 on int32 bit patterns (exact: every distance < 2^24)")
     elif fw16:
         arith = ("FW phase 3 on packed 16-bit pairs (one DPX add-min per two pairs), the closure truncated at "
                  "0x3FFF and certified exact on the device (largest stored value below the cap + largest weight "

@@ -84,7 +84,12 @@ int gemm_aligned(void *C, int64_t ldc, const void *A, int64_t lda, const void *B
 
 static int rk(uint8_t *d, int64_t m, int64_t ld, int dtype, int inf_i, int cutoff, Bound bd, uint8_t *W,
               cudaStream_t s, Packed16 pk) {
-  if (m <= cutoff) return fw_closure(d, m, ld, dtype, inf_i, bd, s);
+  // Leaves of at least kFw16MinN vertices close with the packed 16-bit phase 3 (certified per
+  // leaf: a leaf's closure is the closure of its induced subgraph); they reuse the product
+  // scratch, which is idle while a leaf runs.
+  if (m <= cutoff)
+    return fw_closure(d, m, ld, dtype, inf_i, bd, s,
+                      (m >= kFw16MinN && pk.scratch && pk.bytes >= fw16_panel_bytes(m)) ? pk.scratch : nullptr);
   const int64_t h = split_of(m), r2 = m - h;
   const int64_t es = 4;
   uint8_t *A = d, *B = d + h * es, *C = d + h * ld * es, *D = d + (h * ld + h) * es;

@@ -31,8 +31,8 @@ import torch
 from . import (apsp_close_cta, apsp_fw, apsp_mlp_adam, apsp_mlp_backward, apsp_mlp_forward, apsp_mlp_loss, apsp_mlp_param_count,
                apsp_rkleene, apsp_rkleene_workspace_bytes, apsp_squaring, apsp_squaring_workspace_bytes, lib)
 
-CANDIDATES = (("fw", 0), ("rkleene", 128), ("rkleene", 256), ("rkleene", 512), ("rkleene", 1024), ("cta", 0),
-              ("squaring", 0))
+CANDIDATES = (("fw", 0), ("rkleene", 128), ("rkleene", 256), ("rkleene", 512), ("rkleene", 1024), ("rkleene", 4096),
+              ("cta", 0), ("squaring", 0))
 CTA_MAX_N = 1024  # beyond this one SM is far too slow to be worth timing
 IN_DIM = 10
 FW16_MIN_N = 4096  # apsp_fw runs phase 3 on packed 16-bit pairs for int32 graphs this large
@@ -208,9 +208,9 @@ DEFAULT_LOG = os.path.join(os.path.dirname(os.path.abspath(__file__)), "timings_
 
 
 def sweep_graphs(seed: int = 0):
-    """The autotuning sweep: sizes 32..8192 (log-spaced), both dtypes, sparse and dense."""
+    """The autotuning sweep: sizes 32..16384 (log-spaced), both dtypes, sparse and dense."""
     import workloads
-    sizes = sorted({int(round(2 ** e)) for e in np.arange(5.0, 13.01, 0.5)})
+    sizes = sorted({int(round(2 ** e)) for e in np.arange(5.0, 14.01, 0.5)})
     for i, n in enumerate(sizes):
         for dt in ("int32", "float32"):
             for p in (0.02, 0.4):
