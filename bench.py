@@ -40,6 +40,7 @@ WORKLOADS = {
     "apsp_rkleene_n32768": dict(n=32768, p=0.05, dtype="int32", dist="uniform", lo=1, hi=100, algo="rkleene",
                                 param=1024),
     "tgemm_n32768": dict(n=32768, p=0.05, dtype="int32", dist="uniform", lo=1, hi=100, algo="gemm"),
+    "tgemm_n8192": dict(n=8192, p=0.05, dtype="int32", dist="uniform", lo=1, hi=100, algo="gemm"),
     "apsp_fw_n32768_f32": dict(n=32768, p=0.05, dtype="float32", dist="uniform01", lo=0, hi=1, algo="fw"),
     "apsp_fw_n4096": dict(n=4096, p=0.5, dtype="int32", dist="uniform", lo=1, hi=1000, algo="fw"),
     "apsp_fw_n8192": dict(n=8192, p=0.05, dtype="int32", dist="uniform", lo=1, hi=100, algo="fw"),
