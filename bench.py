@@ -242,6 +242,17 @@ def run_reference(args, w, rank, world):
     return 0
 
 
+def spin_up(fn, seconds: float = 1.0):
+    """Run fn (untimed) until `seconds` of wall time have passed: an idle GPU takes a while to
+    reach its full clocks, and a short warm-up would leave the start of the timed region slow."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        fn()
+        torch.cuda.synchronize()
+
+
 def aggregate(ms_local: float, work_local: float, device=None):
     """Whole-job throughput across ranks: the time is the max over ranks (the job ends when the
     slowest rank does), the work is summed.  Works with any torch.distributed backend; with no
@@ -326,6 +337,8 @@ def run_ours(args, w, rank, world, local_rank):
     copies = [host.to(dev) for _ in range(pool)]
     pristine = copies[0].clone() if pool < want else None
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev) if n < 32768 else None
+    if flush is not None:
+        flush.zero_()  # the first write to fresh memory is slow (hundreds of ms): keep it untimed
 
     def prepare(i):
         if i < pool and pristine is None:
@@ -334,6 +347,10 @@ def run_ours(args, w, rank, world, local_rank):
         buf.copy_(pristine)
         return buf
 
+    if n < 32768:  # a 4 GiB closure takes over a second: its warm-up steps already ramp the clocks
+        scratch = copies[0].clone()
+        spin_up(lambda: step_fn(scratch, gemm_out))
+        del scratch
     torch.cuda.synchronize()
     for i in range(args.warmup):
         step_fn(prepare(i), gemm_out)
@@ -410,11 +427,15 @@ def run_ours(args, w, rank, world, local_rank):
                         f"by (n-128)^2; algorithmic {8 * (n - 128) ** 2} B (each C tile read and written once)")
     nb = -(-n // 128)
     fw16 = w["algo"] == "fw" and w["dtype"] == "int32" and n >= 4096
-    # Every kernel of ours that is launched per step, including the alternative launches that
-    # return at once: FW with the 16-bit phase 3 launches normalise, the decision, per block
-    # (diagonal, panels, packing, 16-bit and plain phase 3), the certificate (2) and the three
-    # launches per block of the int32 pass that runs only when the certificate fails.
-    launches_per_step = {"fw": 4 + 8 * nb if fw16 else 1 + 3 * nb,
+    # Every kernel of ours that is launched per step, including launches that return at once
+    # (the int32 pass runs only when the certificate fails).
+    # FW with the 16-bit pass: normalise, decision, per block of the pass either 12 launches
+    # (256-vertex blocks from n = 16384: the block's own 2 x 3-phase closure, 2 panel copies,
+    # 2 panel products, packing, 16-bit phase 3) or 4 (128-vertex blocks: diagonal, panels,
+    # packing, 16-bit phase 3), the certificate (2) and the 3 launches per 128-vertex block of
+    # the int32 pass.
+    per_block16 = (12 * -(-n // 256)) if n >= 16384 else 4 * nb
+    launches_per_step = {"fw": 4 + per_block16 + 3 * nb if fw16 else 1 + 3 * nb,
                          "gemm": 6 if w["dtype"] == "int32" else 1, "rkleene": None}[w["algo"]]
     if w["dtype"] != "int32":
         arith = "fp32 packed add + 3-input min"
@@ -519,6 +540,7 @@ def run_batched(args, w, rank, world, local_rank):
     with torch.cuda.graph(graph, stream=stream):
         work.copy_(pristine)
         apsp.apsp_batched(batch)
+    spin_up(graph.replay)
     for _ in range(args.warmup):
         graph.replay()
     torch.cuda.synchronize()

@@ -118,13 +118,15 @@ int tropical_gemm(void *C, const void *A, const void *B, int64_t M, int64_t N, i
  * d must be 16-byte aligned.  The workspace holds 256 bytes of bound words (int32 matrices
  * whose (n - 1) * largest finite weight < 2^24 run in exact fp32 arithmetic on their bit
  * patterns; others in int32), when ld is not a multiple of 4 an aligned copy of the matrix
- * (n x round_up(n, 4) elements), and last, for int32 with n >= 4096, room for the two panels
- * packed into 16-bit pairs (2 x 64 x round_up(n, 4) words).  With that room, and a largest
- * weight of at most 0x0FFF, phase 3 runs on the packed pairs (two (min,+) pairs per DPX
- * operation) in the (min,+) semiring truncated at 0x3FFF; a device-side certificate (largest
- * stored value below 0x3FFF plus the largest weight stays below 0x3FFF) proves the result
- * exact, and otherwise the int32 Floyd-Warshall runs again over it.  Results are bit-exact
- * either way.  A workspace without the packed room is accepted and skips that path. */
+ * (n x round_up(n, 4) elements), and last, for int32 with n >= 4096, room for a 16-bit pass
+ * over 256-vertex diagonal blocks (the two panels packed into 16-bit pairs, 2 x 128 x
+ * round_up(n, 4) words, and copies of the two 256-wide panels, 2 x 256 x round_up(n, 4)
+ * elements).  With that room, and a largest weight of at most 0x0FFF, phase 3 runs on the
+ * packed pairs (two (min,+) pairs per DPX operation) in the (min,+) semiring truncated at
+ * 0x3FFF; a device-side certificate (largest stored value below 0x3FFF plus the largest weight
+ * stays below 0x3FFF) proves the result exact, and otherwise the int32 Floyd-Warshall runs
+ * again over it.  Results are bit-exact either way.  A workspace without that room is accepted
+ * and closes with the plain phase 3. */
 size_t apsp_fw_workspace_bytes(int64_t n, int64_t ld, int dtype, int tile);
 int apsp_fw(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int tile, void *ws,
             size_t ws_bytes, void *stream);

@@ -44,8 +44,10 @@ size_t closure_workspace_bytes(int algo, int64_t n, int64_t ld, int param, int d
 // (min,+) product of aligned operands through the TMA engine (rkleene.cu).  With pk.scratch
 // large enough, an int32 product whose largest finite operand entries sum below kCap16 (a
 // device-side scan) runs on packed 16-bit pairs; the plain launch returns at once then.
+// run_if (may be null): the launch returns at once unless *run_if is non-zero (then it is not
+// traced and never takes the packed path).
 int gemm_aligned(void *C, int64_t ldc, const void *A, int64_t lda, const void *B, int64_t ldb, int64_t M, int64_t N,
                  int64_t K, int dtype, bool acc, int inf_i, Bound b, cudaStream_t s,
-                 Packed16 pk = {nullptr, nullptr, 0});
+                 Packed16 pk = {nullptr, nullptr, 0}, const int *run_if = nullptr);
 
 }  // namespace apsp

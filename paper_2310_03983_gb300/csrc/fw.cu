@@ -63,37 +63,43 @@ int launch_fw_diag(void *d, int64_t ld, int64_t n, int64_t kb, int dtype, cudaSt
 //   [0] largest finite weight (a1), [4] 16-bit phase 3 in use, [5] largest stored value < CAP,
 //   [6] the int32 pass must run again.
 constexpr int kUse16MaxWeight = kCap16 / 4;
+// From kFw16WideN vertices the 16-bit pass works on diagonal blocks of two tiles (256 vertices):
+// phase 3 then has K = 256 (128 packed words) per launch, which halves the per-tile epilogue and
+// C traffic per pair, at the price of a heavier phase 1 and 2 per block (a 2 x 2-tile closure,
+// two panel copies and two panel products); below it the blocks are single tiles.
+constexpr int kFw16Tiles = 2;
+constexpr int64_t kFw16Block = kFw16Tiles * kBM;
+constexpr int kFw16Words = (int)(kFw16Block / 2);
+constexpr int64_t kFw16WideN = 16384;
 
 __global__ void fw16_decide_kernel(int *words) {
   words[4] = words[0] <= kUse16MaxWeight;
   words[5] = 0;
-  words[6] = 0;
+  words[6] = !words[4];  // without the 16-bit pass the int32 pass does all the work
 }
 
-// Packs the column panel D[:, kb0 .. kb0+bk) into A16 (n rows x 64 words, ld 64) and the row
-// panel D[kb0 .. kb0+bk, :] into B16 (64 words x n, ld ldb16) as 16-bit pairs of consecutive
+// Packs the column panel D[:, kb0 .. kb0+bw) into A16 (n rows x kFw16Words words) and the row
+// panel D[kb0 .. kb0+bw, :] into B16 (kFw16Words words x ldb16) as 16-bit pairs of consecutive
 // k, every value capped at CAP (the sentinel included).
-__global__ void __launch_bounds__(256) fw_pack16_kernel(const int *d, int64_t ld, int64_t n, int64_t kb, int *A16,
-                                                        int *B16, int64_t ldb16, const int *words) {
+__global__ void __launch_bounds__(256) fw_pack16_kernel(const int *d, int64_t ld, int64_t n, int64_t kb0, int bw,
+                                                        int *A16, int *B16, int64_t ldb16, const int *words) {
   if (!words[4]) return;
-  const int64_t kb0 = kb * kBM;
-  const int bk = (int)std::min<int64_t>(kBM, n - kb0);
-  const int kw = (bk + 1) >> 1;
+  const int kw = (bw + 1) >> 1;
   const int64_t na = n * kw, total = na + (int64_t)kw * n;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     if (e < na) {
       const int64_t i = e / kw;
       const int w = (int)(e - i * kw), k = 2 * w;
       const int *row = d + i * ld + kb0;
-      const int lo = min(row[k], kCap16), hi = k + 1 < bk ? min(row[k + 1], kCap16) : kCap16;
-      A16[i * (kBK * 2) + w] = (hi << 16) | lo;
+      const int lo = min(row[k], kCap16), hi = k + 1 < bw ? min(row[k + 1], kCap16) : kCap16;
+      A16[i * kFw16Words + w] = (hi << 16) | lo;
     } else {
       const int64_t f = e - na;
       const int w = (int)(f / n);
       const int64_t j = f - (int64_t)w * n;
       const int k = 2 * w;
       const int *r0 = d + (kb0 + k) * ld + j;
-      const int lo = min(r0[0], kCap16), hi = k + 1 < bk ? min(r0[ld], kCap16) : kCap16;
+      const int lo = min(r0[0], kCap16), hi = k + 1 < bw ? min(r0[ld], kCap16) : kCap16;
       B16[w * ldb16 + j] = (hi << 16) | lo;
     }
   }
@@ -120,8 +126,12 @@ __global__ void fw16_verdict_kernel(int *words) {
   if (words[4]) words[6] = (int64_t)words[5] + (int64_t)words[0] >= kCap16;
 }
 
+// Scratch of the 16-bit pass: the packed column and row panels, and copies of the int32 row and
+// column panels (the operands of the in-place panel products).
 size_t fw16_panel_bytes(int64_t n) {
-  return (size_t)round_up(n * kBK * 2 * 4, 256) + (size_t)round_up(kBK * 2 * round_up(n, 4) * 4, 256);
+  const int64_t ldp = round_up(n, 4);
+  return (size_t)round_up(n * kFw16Words * 4, 256) + (size_t)round_up(kFw16Words * ldp * 4, 256) +
+         (size_t)round_up(kFw16Block * ldp * 4, 256) + (size_t)round_up(n * kFw16Block * 4, 256);
 }
 
 // The plain three-phase loop; every launch returns at once unless *run_if (when given) is set.
@@ -164,52 +174,83 @@ int fw_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bound b, cu
   if (!(panels16 && dtype == APSP_I32 && b.w && nb > 1 && inf_i > kCap16))
     return fw_loop(d, n, ld, dtype, mA, mB, mC, p, nullptr, s);
 
+  // The 16-bit pass, over diagonal blocks of kFw16Block vertices; every launch returns at once
+  // unless words[4] (decided on the device from the largest weight) is set.
   int *words = const_cast<int *>(b.w);
-  int *A16 = reinterpret_cast<int *>(panels16);
-  int *B16 = reinterpret_cast<int *>(reinterpret_cast<uint8_t *>(panels16) + round_up(n * kBK * 2 * 4, 256));
-  const int64_t ldb16 = round_up(n, 4);
+  const int *use16 = words + 4;
+  const int64_t ldp = round_up(n, 4);
+  uint8_t *sp = reinterpret_cast<uint8_t *>(panels16);
+  int *A16 = reinterpret_cast<int *>(sp);
+  sp += round_up(n * kFw16Words * 4, 256);
+  int *B16 = reinterpret_cast<int *>(sp);
+  sp += round_up(kFw16Words * ldp * 4, 256);
+  int *Rc = reinterpret_cast<int *>(sp);
+  sp += round_up(kFw16Block * ldp * 4, 256);
+  int *Cc = reinterpret_cast<int *>(sp);
   CUtensorMap pA, pB;
-  if ((r = make_operand_maps(A16, n, kBK * 2, kBK * 2, APSP_I32, &pA, nullptr, nullptr))) return r;
-  if ((r = make_operand_maps(B16, kBK * 2, n, ldb16, APSP_I32, nullptr, &pB, nullptr))) return r;
+  if ((r = make_operand_maps(A16, n, kFw16Words, kFw16Words, APSP_I32, &pA, nullptr, nullptr))) return r;
+  if ((r = make_operand_maps(B16, kFw16Words, n, ldp, APSP_I32, nullptr, &pB, nullptr))) return r;
   fw16_decide_kernel<<<1, 1, 0, s>>>(words);
   APSP_LAUNCH_CHECK();
   const int64_t cap = (int64_t)sm_count() * 8;
-  for (int64_t kb = 0; kb < nb; ++kb) {
-    if ((r = launch_fw_diag(d, ld, n, kb, dtype, s, nullptr))) return r;
-    p.kb = kb;
-    p.ntiles = 2 * (nb - 1);
-    p.run_if = nullptr;
-    p.skip = nullptr;
-    p.arith16 = 0;
-    p.no_trace = 0;
-    if ((r = launch_tgemm(kModeFwPanels, false, dtype, mA, mB, mC, p, s))) return r;
-    const int64_t work = n * kBK * 2;
-    fw_pack16_kernel<<<(int)std::min<int64_t>(cap, cdiv(work, 256)), 256, 0, s>>>(
-        reinterpret_cast<const int *>(d), ld, n, kb, A16, B16, ldb16, words);
+  const int64_t bt = n >= kFw16WideN ? kFw16Tiles : 1, blk = bt * kBM;
+  const int64_t nbb = cdiv(n, blk), nt = cdiv(n, kBM);
+  int *D = reinterpret_cast<int *>(d);
+  for (int64_t kbb = 0; kbb < nbb; ++kbb) {
+    const int64_t kb0 = kbb * blk, bw = std::min<int64_t>(blk, n - kb0);
+    int *sub = D + kb0 * ld + kb0, *rowp = D + kb0 * ld, *colp = D + kb0;
+    if (bt == 1) {  // phases 1 and 2 of a single-tile block, in place (as in the plain loop)
+      if ((r = launch_fw_diag(d, ld, n, kbb, dtype, s, use16))) return r;
+      TileProblem pp = p;
+      pp.kb = kbb;
+      pp.ntiles = 2 * (nt - 1);
+      pp.run_if = use16;
+      pp.no_trace = 1;
+      if ((r = launch_tgemm(kModeFwPanels, false, dtype, mA, mB, mC, pp, s))) return r;
+    } else {
+      // Phase 1: close the diagonal block (itself a small blocked Floyd-Warshall, exact).
+      CUtensorMap dA, dB, dC;
+      if ((r = make_operand_maps(sub, bw, bw, ld, dtype, &dA, &dB, &dC))) return r;
+      TileProblem ps = p;
+      ps.n = bw;
+      ps.nb = cdiv(bw, kBM);
+      ps.C = sub;
+      if ((r = fw_loop(sub, bw, ld, dtype, dA, dB, dC, ps, use16, s))) return r;
+      // Phase 2: the row panel becomes D* (x) (row panel) and the column panel (column panel) (x)
+      // D*, each one exact product (D* is closed, so its zero diagonal keeps the old entry) read
+      // from a copy of the panel; the block's own entries are reproduced (D* (x) D* = D*).
+      if ((r = launch_copy2d(Rc, ldp, rowp, ld, bw, n, s, use16))) return r;
+      if ((r = gemm_aligned(rowp, ld, sub, ld, Rc, ldp, bw, n, bw, dtype, false, inf_i, b, s,
+                            {nullptr, nullptr, 0}, use16)))
+        return r;
+      if ((r = launch_copy2d(Cc, kFw16Block, colp, ld, n, bw, s, use16))) return r;
+      if ((r = gemm_aligned(colp, ld, Cc, kFw16Block, sub, ld, n, bw, bw, dtype, false, inf_i, b, s,
+                            {nullptr, nullptr, 0}, use16)))
+        return r;
+    }
+    // Phase 3 on the packed panels, K = bw.
+    const int64_t work = 2 * n * ((bw + 1) >> 1);
+    fw_pack16_kernel<<<(int)std::min<int64_t>(cap, cdiv(work, 256)), 256, 0, s>>>(D, ld, n, kb0, (int)bw, A16, B16,
+                                                                                  ldp, words);
     APSP_LAUNCH_CHECK();
-    // Phase 3: the 16-bit launch runs when words[4] is set, the plain one otherwise; one trace
-    // record covers the pair.
+    const int64_t ec = std::min<int64_t>(bt, nt - kbb * bt), rest = nt - ec;
+    if (rest == 0) continue;
+    TileProblem q = p;
+    q.kb = kbb;
+    q.bt = (int)bt;
+    q.ntiles = rest * rest;
+    q.arith16 = 1;
+    q.run_if = use16;
+    q.no_trace = 1;
     void *tev = nullptr;
     if (trace_on()) trace_begin(s, &tev);
-    p.ntiles = (nb - 1) * (nb - 1);
-    p.no_trace = 1;
-    TileProblem q = p;
-    q.arith16 = 1;
-    q.run_if = words + 4;
     if ((r = launch_tgemm(kModeFwRest16, true, dtype, pA, pB, mC, q, s))) return r;
-    p.skip = words + 4;
-    if ((r = launch_tgemm(kModeFwRest, true, dtype, mA, mB, mC, p, s))) return r;
-    if (tev) {
-      const double bk = (double)std::min<int64_t>(kBM, n - kb * kBM), rest = (double)n - bk;
-      trace_end(s, tev, kModeFwRest, rest * rest * bk);
-    }
+    if (tev) trace_end(s, tev, kModeFwRest, (double)(n - bw) * (double)(n - bw) * (double)bw);
   }
   fw16_certify_kernel<<<(int)std::min<int64_t>(n, cap), 256, 0, s>>>(reinterpret_cast<int *>(d), ld, n, inf_i, words);
   APSP_LAUNCH_CHECK();
   fw16_verdict_kernel<<<1, 1, 0, s>>>(words);
   APSP_LAUNCH_CHECK();
-  p.skip = nullptr;
-  p.arith16 = 0;
   return fw_loop(d, n, ld, dtype, mA, mB, mC, p, words + 6, s);
 }
 

@@ -32,7 +32,8 @@ static size_t packed_bytes(int64_t M, int64_t N, int64_t K) {
 constexpr double kPacked16MinPairs = 1.0e9;
 
 int gemm_aligned(void *C, int64_t ldc, const void *A, int64_t lda, const void *B, int64_t ldb, int64_t M, int64_t N,
-                 int64_t K, int dtype, bool acc, int inf_i, Bound b, cudaStream_t s, Packed16 pk) {
+                 int64_t K, int dtype, bool acc, int inf_i, Bound b, cudaStream_t s, Packed16 pk,
+                 const int *run_if) {
   if (M == 0 || N == 0) return APSP_OK;
   CUtensorMap mA, mB, mC;
   int r;
@@ -50,7 +51,9 @@ int gemm_aligned(void *C, int64_t ldc, const void *A, int64_t lda, const void *B
   p.status = status_word();
   p.wmax = b.w;
   p.wmult = b.mult;
-  const bool packed = dtype == APSP_I32 && pk.scratch && K > 0 && pk.bytes >= packed_bytes(M, N, K) &&
+  p.run_if = run_if;
+  p.no_trace = run_if != nullptr;
+  const bool packed = !run_if && dtype == APSP_I32 && pk.scratch && K > 0 && pk.bytes >= packed_bytes(M, N, K) &&
                       (double)M * (double)N * (double)K >= kPacked16MinPairs;
   if (!packed) return launch_tgemm(kModeGemm, acc, dtype, mA, mB, mC, p, s);
   // words[0], words[1]: largest finite entries of A and B; words[4]: set by the pack kernels

@@ -70,19 +70,34 @@ __device__ __forceinline__ TileCoords tile_coords(const TileProblem &p, int64_t 
         tc.b_row = kb0;     tc.b_col = kb0;
         tc.c_row = i * kBM; tc.c_col = kb0;
       }
+    } else if (MODE == kModeFwRest16) {  // as below, for a block of bt tiles, K in packed words
+      const int64_t bt = p.bt > 1 ? p.bt : 1;
+      const int64_t nt = (p.n + kBM - 1) / kBM, e0 = p.kb * bt;
+      const int64_t ec = nt - e0 < bt ? nt - e0 : bt, rest = nt - ec;
+      i = (int)(t / rest);
+      j = (int)(t - (int64_t)i * rest);
+      i += (i >= e0) ? (int)ec : 0;
+      j += (j >= e0) ? (int)ec : 0;
+      tc.a_row = i * kBM; tc.a_col = 0;
+      tc.b_row = 0;       tc.b_col = j * kBN;
+      tc.c_row = i * kBM; tc.c_col = j * kBN;
     } else {          // D[i][j] = min(D[i][j], D[i][kb] (x) D[kb][j]), i, j != kb
       i = (int)(t / nb1);
       j = (int)(t - (int64_t)i * nb1);
       i += (i >= p.kb);
       j += (j >= p.kb);
-      tc.a_row = i * kBM; tc.a_col = MODE == kModeFwRest16 ? 0 : kb0;
-      tc.b_row = MODE == kModeFwRest16 ? 0 : kb0;
-      tc.b_col = j * kBN;
+      tc.a_row = i * kBM; tc.a_col = kb0;
+      tc.b_row = kb0;     tc.b_col = j * kBN;
       tc.c_row = i * kBM; tc.c_col = j * kBN;
     }
     tc.m_valid = (int)(p.n - tc.c_row < kBM ? p.n - tc.c_row : kBM);
     tc.n_valid = (int)(p.n - tc.c_col < kBN ? p.n - tc.c_col : kBN);
-    tc.k_len = MODE == kModeFwRest16 ? (bk + 1) >> 1 : bk;
+    if (MODE == kModeFwRest16) {
+      const int64_t w = (p.bt > 1 ? p.bt : 1) * kBM, b0 = p.kb * w;
+      tc.k_len = (int)(((p.n - b0 < w ? p.n - b0 : w) + 1) >> 1);
+    } else {
+      tc.k_len = bk;
+    }
   }
   return tc;
 }
@@ -253,7 +268,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 // (min,+) pairs one launch performs by definition (Eq. 2: one add and one min per (i, j, k)).
 template <int MODE> static double algorithmic_pairs(const TileProblem &p) {
   if (MODE == kModeGemm) return (double)p.M * (double)p.N * (double)p.K * (p.arith16 ? 2.0 : 1.0);
-  const double bk = (double)(p.n - p.kb * kBM < kBM ? p.n - p.kb * kBM : kBM);
+  const int64_t w = (MODE == kModeFwRest16 && p.bt > 1 ? p.bt : 1) * kBM;
+  const double bk = (double)(p.n - p.kb * w < w ? p.n - p.kb * w : w);
   const double rest = (double)p.n - bk;
   return MODE == kModeFwPanels ? 2.0 * bk * bk * rest : rest * rest * bk;
 }
@@ -431,7 +447,8 @@ int launch_tgemm_generic(void *C, const void *A, const void *B, int64_t M, int64
 
 // ------------------------------------ copy --------------------------------------------
 __global__ void __launch_bounds__(256) copy2d_kernel(int *dst, int64_t ldd, const int *src, int64_t lds, int64_t rows,
-                                                     int64_t cols, bool vec) {
+                                                     int64_t cols, bool vec, const int *run_if) {
+  if (run_if && !*run_if) return;
   for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
     const int *s = src + r * lds;
     int *d = dst + r * ldd;
@@ -445,12 +462,14 @@ __global__ void __launch_bounds__(256) copy2d_kernel(int *dst, int64_t ldd, cons
   }
 }
 
-int launch_copy2d(void *dst, int64_t ldd, const void *src, int64_t lds, int64_t rows, int64_t cols, cudaStream_t s) {
+int launch_copy2d(void *dst, int64_t ldd, const void *src, int64_t lds, int64_t rows, int64_t cols, cudaStream_t s,
+                  const int *run_if) {
   if (rows == 0 || cols == 0) return APSP_OK;
   const bool vec = reinterpret_cast<uintptr_t>(dst) % 16 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0 &&
                    ldd % 4 == 0 && lds % 4 == 0;
   const int64_t cap = (int64_t)sm_count() * 8;
-  copy2d_kernel<<<(int)(rows < cap ? rows : cap), 256, 0, s>>>((int *)dst, ldd, (const int *)src, lds, rows, cols, vec);
+  copy2d_kernel<<<(int)(rows < cap ? rows : cap), 256, 0, s>>>((int *)dst, ldd, (const int *)src, lds, rows, cols, vec,
+                                                               run_if);
   APSP_LAUNCH_CHECK();
   return APSP_OK;
 }

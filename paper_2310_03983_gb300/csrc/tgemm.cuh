@@ -25,8 +25,9 @@ enum TileMode : int {
   kModeGemm = 0,      // C (M x N) = [min(C,)] A (M x K) (x) B (K x N)
   kModeFwPanels = 1,  // blocked-FW phase 2: row and column panels of block kb
   kModeFwRest = 2,    // blocked-FW phase 3: every tile outside block row/column kb
-  kModeFwRest16 = 3,  // phase 3 on packed 16-bit copies of the panels: A = the column panel
-                      // (n rows x 64 words), B = the row panel (64 words x n), C = the matrix
+  kModeFwRest16 = 3,  // phase 3 on packed 16-bit copies of the panels of a block of bt tiles:
+                      // A = the column panel (n rows x 64 bt words), B = the row panel
+                      // (64 bt words x n), C = the matrix; tiles of the block row/column skipped
 };
 
 struct TileProblem {
@@ -60,6 +61,8 @@ struct TileProblem {
   // int32 signed closures (may be 0 = off): a result at or above sat is an unreachable entry
   // plus negative terms and is written back as exactly inf_i.
   int sat;
+  // kModeFwRest16: tiles per diagonal block (0 or 1: 128-vertex blocks; 2: 256-vertex blocks).
+  int bt;
 };
 
 // 16-bit packing of int32 operands for ArithI16x2 (tgemm.cu).  Entries >= inf (and the padding
@@ -84,8 +87,10 @@ int launch_tgemm_generic(void *C, const void *A, const void *B, int64_t M, int64
 int make_operand_maps(const void *base, int64_t rows, int64_t cols, int64_t ld, int dtype, CUtensorMap *mA,
                       CUtensorMap *mB, CUtensorMap *mC);
 
-// Strided 2-D copy (rows x cols elements of 4 bytes), used for operand copies.
-int launch_copy2d(void *dst, int64_t ldd, const void *src, int64_t lds, int64_t rows, int64_t cols, cudaStream_t s);
+// Strided 2-D copy (rows x cols elements of 4 bytes), used for operand copies.  run_if (may be
+// null): the copy returns at once unless *run_if is non-zero.
+int launch_copy2d(void *dst, int64_t ldd, const void *src, int64_t lds, int64_t rows, int64_t cols, cudaStream_t s,
+                  const int *run_if = nullptr);
 
 // a1 launcher (normalise.cu).  For int32, atomically maxes the largest finite entry into
 // *wmax (device word, zeroed by the caller) when wmax is not null.

@@ -45,9 +45,10 @@ def test_host_side_calls_without_gpu():
     g.restype, g.argtypes = ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int]
     assert g(1000, 1000, 0, 0) == 256
     assert g(1001, 1001, 0, 0) >= 256 + 1001 * 1004 * 4
-    # int32 FW from 4096 vertices: room for the packed 16-bit panels (n x 64 + 64 x n words)
+    # int32 FW from 4096 vertices: room for the 16-bit pass over 256-vertex blocks (packed
+    # panels n x 128 + 128 x n words, and copies of the 256-wide row and column panels)
     assert g(4096, 4096, 1, 0) == 256
-    assert g(4096, 4096, 0, 0) == 256 + 2 * 4096 * 64 * 4
+    assert g(4096, 4096, 0, 0) == 256 + 2 * 4096 * 128 * 4 + 2 * 4096 * 256 * 4
     # argument errors return before any CUDA call: n < 0, bad dtype
     h = lib.apsp_fw
     h.restype = ctypes.c_int

@@ -130,3 +130,31 @@ def test_custom_sentinel(apsp, inf):
     assert apsp.apsp_device_status() == 0
     want = oracle.fw(hc, inf=inf, threads=THREADS)
     assert_dist_equal(d.cpu().numpy(), want, f"inf={inf}")
+
+
+def test_wide_blocks_rows(apsp):
+    """n = 16400: the 16-bit pass on 256-vertex blocks (a ragged last block of 16 vertices),
+    checked on 24 source rows by Dijkstra, bit-exact."""
+    n = 16400
+    h = workloads.er_graph(n, 0.004, "int32", lo=1, hi=100, seed=77)
+    d = torch.from_numpy(h).cuda()
+    apsp.apsp_fw(d)
+    assert apsp.apsp_device_status() == 0
+    rows = np.random.default_rng(78).choice(n, 24, replace=False)
+    got = d.cpu().numpy()[rows]
+    assert_dist_equal(got, oracle.dijkstra_rows(h, rows, threads=THREADS), "rows")
+
+
+def test_wide_blocks_long_path_reruns(apsp):
+    """A directed path of 16384 vertices with unit weights: distances reach the cap, the
+    certificate fails and the int32 pass must produce the closed form exactly."""
+    n = 16384
+    h = _path_graph(n, 1)
+    d = torch.from_numpy(h).cuda()
+    apsp.apsp_fw(d)
+    assert apsp.apsp_device_status() == 0
+    got = d.cpu().numpy()
+    for i in (0, 1, 255, 256, 8191, 16383):
+        row = got[i]
+        j = np.arange(n)
+        assert np.array_equal(row, np.where(j >= i, j - i, INF)), i
