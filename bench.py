@@ -394,22 +394,24 @@ def run_ours(args, w, rank, world, local_rank):
     if args.e2e_steps > 0:
         if w["algo"] == "gemm":
             e2e_ms = []
-            for _ in range(args.e2e_steps):
+            for it in range(args.e2e_steps + 1):  # the first, untimed, maps the buffers
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 a = host.to(dev, non_blocking=True)
                 apsp.tropical_gemm(gemm_out, a, a, ws=gemm_ws)
                 out_host.copy_(gemm_out, non_blocking=True)
                 torch.cuda.synchronize()
-                e2e_ms.append((time.perf_counter() - t0) * 1e3)
+                if it:
+                    e2e_ms.append((time.perf_counter() - t0) * 1e3)
                 del a
         else:
             e2e_ms = []
-            for _ in range(args.e2e_steps):
+            for it in range(args.e2e_steps + 1):  # the first, untimed, maps the buffers
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 apsp.solve(host, algo=w["algo"], param=w.get("param", 0), out=out_host)
-                e2e_ms.append((time.perf_counter() - t0) * 1e3)
+                if it:
+                    e2e_ms.append((time.perf_counter() - t0) * 1e3)
         te = torch.tensor([statistics.median(e2e_ms)], dtype=torch.float64, device=dev)
         if world > 1:
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
@@ -606,14 +608,15 @@ def run_batched(args, w, rank, world, local_rank):
     # End to end through the public API: pinned host pool in, closed pool back to pinned host.
     out_host = torch.empty_like(batch.host).pin_memory()
     e2e = []
-    for _ in range(max(1, args.e2e_steps)):
+    for it in range(max(1, args.e2e_steps) + 1):  # the first, untimed, maps the buffers
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         work.copy_(batch.host, non_blocking=True)
         apsp.apsp_batched(batch)
         out_host.copy_(work, non_blocking=True)
         torch.cuda.synchronize()
-        e2e.append(time.perf_counter() - t0)
+        if it:
+            e2e.append(time.perf_counter() - t0)
     e2e_val = world * len(batch) / statistics.median(e2e)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = 2.0 * sms * LANES_PER_SM * MAX_SM_MHZ * 1e6 / 1e12

@@ -29,8 +29,8 @@
  *    caller supplies the workspace (ws != NULL).
  *  - ws / ws_bytes: caller workspace in device memory (256-byte aligned, at least the size
  *    reported by the matching *_workspace_bytes function).  ws == NULL makes the library
- *    allocate it with cudaMallocAsync on `stream` and free it with cudaFreeAsync after the
- *    work, both stream-ordered.
+ *    allocate it on `stream` from its own stream-ordered pool and free it after the work
+ *    (apsp_workspace_pool_trim releases the pool's cached memory).
  *
  * Errors
  * ------
@@ -70,6 +70,12 @@ typedef enum apsp_status {
 
 /* Library version (APSP_VERSION of the build). */
 int apsp_version(void);
+
+/* Workspaces the library allocates for calls made with ws == NULL come from a stream-ordered
+ * memory pool per device that keeps freed memory for later calls (so a caller that
+ * synchronises between calls does not pay for mapping the memory again).  This releases the
+ * current device's cached pool memory.  Returns APSP_OK or APSP_ERR_CUDA. */
+int apsp_workspace_pool_trim(void);
 
 /* Static, human-readable name of a status code. */
 const char *apsp_status_str(int status);

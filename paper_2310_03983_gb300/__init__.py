@@ -41,6 +41,7 @@ def _load():
     vp, i64, i32, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_size_t
     sigs = {
         "apsp_version": ([], i32),
+        "apsp_workspace_pool_trim": ([], i32),
         "apsp_status_str": ([i32], ctypes.c_char_p),
         "apsp_device_status": ([vp, ctypes.POINTER(i32)], i32),
         "apsp_normalise": ([vp, i64, i64, i32, vp, vp], i32),
@@ -77,7 +78,7 @@ def _load():
 
 
 _lib = _load()
-EXPORTS = ("apsp_version", "apsp_status_str", "apsp_device_status", "apsp_normalise",
+EXPORTS = ("apsp_version", "apsp_workspace_pool_trim", "apsp_status_str", "apsp_device_status", "apsp_normalise",
            "tropical_gemm_workspace_bytes", "tropical_gemm",
            "apsp_fw_workspace_bytes", "apsp_fw", "apsp_rkleene_workspace_bytes", "apsp_rkleene",
            "apsp_fw_signed_workspace_bytes", "apsp_fw_signed", "apsp_squaring_workspace_bytes", "apsp_squaring", "apsp_predecessors_workspace_bytes", "apsp_predecessors",
@@ -123,6 +124,11 @@ def _inf_arg(inf, code):
 
 def apsp_version() -> int:
     return _lib.apsp_version()
+
+
+def apsp_workspace_pool_trim():
+    """Release the memory the library's workspace pool keeps for the current device."""
+    _check(_lib.apsp_workspace_pool_trim(), "apsp_workspace_pool_trim")
 
 
 def apsp_device_status(stream=None) -> int:

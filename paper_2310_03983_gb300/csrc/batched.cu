@@ -516,8 +516,7 @@ extern "C" int apsp_batched(void *pool, const int64_t *offsets, const int32_t *n
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   void *own = nullptr;
   if (!ws) {
-    if (cudaMallocAsync(&own, 256, s) != cudaSuccess) {
-      cudaGetLastError();
+    if (ws_alloc(&own, 256, s) != APSP_OK) {
       return APSP_ERR_NOMEM;
     }
     ws = own;
@@ -534,6 +533,6 @@ extern "C" int apsp_batched(void *pool, const int64_t *offsets, const int32_t *n
   if (cudaMemsetAsync(a.queue, 0, 2 * sizeof(int), s) != cudaSuccess) r = APSP_ERR_CUDA;
   const bool clusters = needs_clusters(ns_host, count);
   if (!r) r = dtype == APSP_I32 ? launch_batched<int>(a, clusters, s) : launch_batched<float>(a, clusters, s);
-  if (own) cudaFreeAsync(own, s);
+  ws_free(own, s);
   return r;
 }

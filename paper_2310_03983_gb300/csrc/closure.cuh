@@ -40,6 +40,9 @@ size_t rk16_scratch_bytes(int64_t n, int cutoff);
 int closure_entry(int algo, void *d, int64_t n, int64_t ld, int dtype, const void *inf, int param, void *ws,
                   size_t ws_bytes, void *stream);
 size_t closure_workspace_bytes(int algo, int64_t n, int64_t ld, int param, int dtype);
+// The part closure_entry cannot run without (bound words, aligned copy, R-Kleene scratch); the
+// rest of closure_workspace_bytes is the optional room for the packed 16-bit passes.
+size_t closure_required_bytes(int algo, int64_t n, int64_t ld, int param);
 
 // (min,+) product of aligned operands through the TMA engine (rkleene.cu).  With pk.scratch
 // large enough, an int32 product whose largest finite operand entries sum below kCap16 (a

@@ -195,6 +195,11 @@ inline int64_t round_up(int64_t a, int64_t b) { return cdiv(a, b) * b; }
 // Number of SMs of the current device (cached per device).
 int sm_count();
 
+// Workspace the library allocates for a call made without one: stream-ordered, from a
+// per-device pool that keeps freed memory for the next call (runtime.cu).
+int ws_alloc(void **p, size_t bytes, cudaStream_t s);
+void ws_free(void *p, cudaStream_t s);
+
 // Device address of the current device's status word (nullptr on failure).
 unsigned int *status_word();
 

@@ -270,17 +270,13 @@ int closure_entry(int algo, void *d, int64_t n, int64_t ld, int dtype, const voi
   // The full size includes the packed 16-bit panels of an int32 FW; a workspace of the base
   // size is still accepted and closes with the plain phase 3.
   const size_t need = closure_workspace_bytes(algo, n, ld, param, dtype);
-  const size_t panels = dtype != APSP_I32                     ? 0
-                        : (algo == 0 && n >= kFw16MinN) ? fw16_panel_bytes(n)
-                        : algo == 1                     ? rk16_scratch_bytes(n, param ? param : 256)
-                                                        : 0;
-  const size_t base = need - panels;
+  const size_t base = closure_required_bytes(algo, n, ld, param);
+  const size_t panels = need - base;
   if (ws && (ws_bytes < base || reinterpret_cast<uintptr_t>(ws) % 256 != 0)) return APSP_ERR_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   void *own = nullptr;
   if (!ws && need > 0) {
-    if (cudaMallocAsync(&own, need, s) != cudaSuccess) {
-      cudaGetLastError();
+    if (ws_alloc(&own, need, s) != APSP_OK) {
       return APSP_ERR_NOMEM;
     }
     ws = own;
@@ -306,15 +302,21 @@ int closure_entry(int algo, void *d, int64_t n, int64_t ld, int dtype, const voi
   if (!r) r = algo == 0 ? fw_closure(work, n, ldw, dtype, inf_i, bound, s, panels16)
                         : rkleene_closure(work, n, ldw, dtype, inf_i, param ? param : 256, bound, wsp, s, pk);
   if (!r && work != d) r = launch_copy2d(d, ld, work, ldw, n, n, s);
-  if (own) cudaFreeAsync(own, s);
+  ws_free(own, s);
   return r;
 }
 
-size_t closure_workspace_bytes(int algo, int64_t n, int64_t ld, int param, int dtype) {
+size_t closure_required_bytes(int algo, int64_t n, int64_t ld, int param) {
   if (n <= 0) return 0;
   size_t b = kFlagBytes;
   if (ld % 4 != 0) b += (size_t)round_up(n * round_up(n, 4) * 4, 256);
   if (algo == 1) b += rkleene_scratch_bytes(n, param ? param : 256);
+  return b;
+}
+
+size_t closure_workspace_bytes(int algo, int64_t n, int64_t ld, int param, int dtype) {
+  if (n <= 0) return 0;
+  size_t b = closure_required_bytes(algo, n, ld, param);
   // Last, and optional: room for the packed 16-bit panels (FW) or operands (R-Kleene).
   if (algo == 0 && dtype == APSP_I32 && n >= kFw16MinN) b += fw16_panel_bytes(n);
   if (algo == 1 && dtype == APSP_I32) b += rk16_scratch_bytes(n, param ? param : 256);

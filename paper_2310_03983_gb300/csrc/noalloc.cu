@@ -56,7 +56,9 @@ extern "C" int apsp_rkleene_noalloc(void *d, int64_t n, int64_t ld, int dtype, c
   using namespace apsp;
   if (n < 0 || n > kNoAllocMaxN) return APSP_ERR_ARG;   // larger graphs need apsp_rkleene
   if (n > 0 && ld % 4 != 0) return APSP_ERR_ARG;        // would need an aligned copy of the whole matrix
-  if (closure_workspace_bytes(1, n, ld, cutoff, dtype) > kNoAllocBytes) return APSP_ERR_ARG;
+  // The array holds the required scratch; the optional 16-bit room does not fit, so int32
+  // products run on the plain 32-bit path here.
+  if (closure_required_bytes(1, n, ld, cutoff) > kNoAllocBytes) return APSP_ERR_ARG;
   int err = APSP_OK;
   void *ws = noalloc_scratch(&err);
   if (!ws) return err;

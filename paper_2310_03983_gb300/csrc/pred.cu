@@ -316,8 +316,7 @@ extern "C" int apsp_predecessors(const void *d, int64_t ldd, const void *w, int6
   if (ws && ws_bytes < need) return APSP_ERR_ARG;
   void *own = nullptr;
   if (!ws) {
-    if (cudaMallocAsync(&own, need, s) != cudaSuccess) {
-      cudaGetLastError();
+    if (ws_alloc(&own, need, s) != APSP_OK) {
       return APSP_ERR_NOMEM;
     }
     ws = own;
@@ -365,6 +364,6 @@ extern "C" int apsp_predecessors(const void *d, int64_t ldd, const void *w, int6
     if (cudaGetLastError() != cudaSuccess) r = APSP_ERR_CUDA;
   }
   if (!r) r = launch_direct<int>(d, ldd, w, ldw, pred, ldp, n, inf_i, words + kWSkip, s);
-  if (own) cudaFreeAsync(own, s);
+  ws_free(own, s);
   return r;
 }

@@ -35,6 +35,53 @@ int sm_count() {
   return cached[dev];
 }
 
+// Library workspace pool: a stream-ordered memory pool per device that keeps freed blocks
+// (release threshold = the whole device), so a workspace the library allocates for a call
+// without one is reused by the next call instead of being unmapped and mapped again whenever
+// the caller synchronises (the default pool's behaviour), which costs far more than the
+// allocation itself for large workspaces.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pools[64];
+static bool g_have_pool[64];
+
+static cudaMemPool_t lib_pool() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_have_pool[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools[dev] = pool;
+    g_have_pool[dev] = true;
+  }
+  return g_pools[dev];
+}
+
+int ws_alloc(void **p, size_t bytes, cudaStream_t s) {
+  cudaMemPool_t pool = lib_pool();
+  const cudaError_t e = pool ? cudaMallocFromPoolAsync(p, bytes, pool, s) : cudaMallocAsync(p, bytes, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return APSP_ERR_NOMEM;
+  }
+  return APSP_OK;
+}
+
+void ws_free(void *p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -140,6 +187,14 @@ extern "C" int apsp_trace_read(int mode, double *total_ms, int64_t *launches, do
   *launches = cnt;
   *pairs = pr;
   return rc;
+}
+
+extern "C" int apsp_workspace_pool_trim(void) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return APSP_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(apsp::g_pool_mu);
+  if (apsp::g_have_pool[dev] && cudaMemPoolTrimTo(apsp::g_pools[dev], 0) != cudaSuccess) return APSP_ERR_CUDA;
+  return APSP_OK;
 }
 
 extern "C" int apsp_version(void) { return APSP_VERSION; }

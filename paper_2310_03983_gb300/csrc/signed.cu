@@ -169,8 +169,7 @@ extern "C" int apsp_fw_signed(void *d, int64_t n, int64_t ld, int dtype, const v
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   void *own = nullptr;
   if (!ws) {
-    if (cudaMallocAsync(&own, need, s) != cudaSuccess) {
-      cudaGetLastError();
+    if (ws_alloc(&own, need, s) != APSP_OK) {
       return APSP_ERR_NOMEM;
     }
     ws = own;
@@ -202,6 +201,6 @@ extern "C" int apsp_fw_signed(void *d, int64_t n, int64_t ld, int dtype, const v
   }
   if (!r) r = fw_signed(work, n, ldw, dtype, inf_i, words, s);
   if (!r && work != d) r = launch_copy2d(d, ld, work, ldw, n, n, s);
-  if (own) cudaFreeAsync(own, s);
+  ws_free(own, s);
   return r;
 }

@@ -70,8 +70,7 @@ extern "C" int apsp_squaring(void *d, int64_t n, int64_t ld, int dtype, const vo
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   void *own = nullptr;
   if (!ws) {
-    if (cudaMallocAsync(&own, need, s) != cudaSuccess) {
-      cudaGetLastError();
+    if (ws_alloc(&own, need, s) != APSP_OK) {
       return APSP_ERR_NOMEM;
     }
     ws = own;
@@ -120,6 +119,6 @@ extern "C" int apsp_squaring(void *d, int64_t n, int64_t ld, int dtype, const vo
     }
   }
   if (!r && work != d) r = launch_copy2d(d, ld, work, ldw, n, n, s);
-  if (own) cudaFreeAsync(own, s);
+  ws_free(own, s);
   return r;
 }

@@ -529,8 +529,7 @@ extern "C" int tropical_gemm(void *C, const void *A, const void *B, int64_t M, i
   if (dtype == APSP_I32) {  // largest finite entries of A and B decide the exact fp32 path
     if (!ws) {
       ws_bytes = tropical_gemm_workspace_bytes(M, N, K, dtype);
-      if (cudaMallocAsync(&own, ws_bytes, s) != cudaSuccess) {
-        cudaGetLastError();
+      if (ws_alloc(&own, ws_bytes, s) != APSP_OK) {
         return APSP_ERR_NOMEM;
       }
       ws = own;
@@ -580,6 +579,6 @@ extern "C" int tropical_gemm(void *C, const void *A, const void *B, int64_t M, i
   }
   if (!r) r = launch_tgemm(kModeGemm, accumulate != 0, dtype, mA, mB, mC, p, s);
   if (tev) trace_end(s, tev, kModeGemm, (double)M * (double)N * (double)K);
-  if (own) cudaFreeAsync(own, s);
+  ws_free(own, s);
   return r;
 }
