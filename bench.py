@@ -44,6 +44,7 @@ WORKLOADS = {
     "apsp_fw_n32768_f32": dict(n=32768, p=0.05, dtype="float32", dist="uniform01", lo=0, hi=1, algo="fw"),
     "apsp_fw_n4096": dict(n=4096, p=0.5, dtype="int32", dist="uniform", lo=1, hi=1000, algo="fw"),
     "apsp_fw_n8192": dict(n=8192, p=0.05, dtype="int32", dist="uniform", lo=1, hi=100, algo="fw"),
+    "apsp_fw_n16384": dict(n=16384, p=0.05, dtype="int32", dist="uniform", lo=1, hi=100, algo="fw"),
     "batched_2048": dict(n=None, count=2048, dtype="int32", dist="uniform", lo=1, hi=100, algo="batched"),
     "batched_256": dict(n=None, count=256, dtype="int32", dist="uniform", lo=1, hi=100, algo="batched"),
     "paper_sweep_1000": dict(n=None, count=1000, dtype="int32", dist="paper", lo=0, hi=100, algo="batched",
@@ -54,11 +55,13 @@ WORKLOADS = {
 SMS_NOMINAL = 152
 LANES_PER_SM = 128
 MAX_SM_MHZ = 2070.0
-# DRAM traffic of one FW phase-3 launch per C element (dram__bytes_read.sum +
-# dram__bytes_write.sum from one ncu capture of the 16-bit phase-3 kernel at n = 8192, block
-# 37: 463.6 MB over 8064^2 C elements), valid only for the kernel sources it was taken on.
-PHASE3_DRAM_BYTES_PER_C_ELEM = 7.129
-PHASE3_TRAFFIC_SRC_HASH = "4f7333eca354027e"
+# DRAM traffic of one 16-bit FW phase-3 launch per C element (dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture each), keyed by the block width in 128-vertex tiles:
+# 1 below n = 16384 (captured at n = 8192), 2 from n = 16384 (captured at n = 16384).  Valid
+# only for the kernel sources they were taken on (hash below; since the capture those files
+# changed only in host code: the launch counter in APSP_LAUNCH_CHECK).
+PHASE3_DRAM_BYTES_PER_C_ELEM = {1: 7.109, 2: 7.840}
+PHASE3_TRAFFIC_SRC_HASH = "bb66551703a193fb"
 TGEMM_SOURCES = ("tgemm.cu", "tgemm.cuh", "slab.cuh", "common.cuh")
 
 
@@ -242,6 +245,29 @@ def run_reference(args, w, rank, world):
     return 0
 
 
+def copy_parts(host_in, host_out, dev, reps: int = 3):
+    """Median times (ms, CUDA events) of the two copies an end-to-end step makes, each alone:
+    the pinned host input to a device buffer, and a device buffer back to the pinned host
+    output.  Reported beside the e2e figure to show how its time divides."""
+    import torch
+    buf = torch.empty(host_in.shape, dtype=host_in.dtype, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    h2d, d2h = [], []
+    for _ in range(reps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        e[0].record(stream)
+        buf.copy_(host_in, non_blocking=True)
+        e[1].record(stream)
+        host_out.copy_(buf.view(host_out.shape), non_blocking=True)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        h2d.append(e[0].elapsed_time(e[1]))
+        d2h.append(e[1].elapsed_time(e[2]))
+    del buf
+    return {"h2d": round(statistics.median(h2d), 2), "d2h": round(statistics.median(d2h), 2)}
+
+
 def spin_up(fn, seconds: float = 1.0):
     """Run fn (untimed) until `seconds` of wall time have passed: an idle GPU takes a while to
     reach its full clocks, and a short warm-up would leave the start of the timed region slow."""
@@ -368,12 +394,14 @@ def run_ours(args, w, rank, world, local_rank):
         dist.barrier()
     torch.cuda.synchronize()
     sampler.begin()
+    apsp.apsp_launch_count(reset=True)
     e0.record(stream)
     for i in range(args.steps):
         if flush is not None:
             flush.zero_()
         step_fn(prepare(args.warmup + i), gemm_out)
     e1.record(stream)
+    launches = apsp.apsp_launch_count()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -382,14 +410,13 @@ def run_ours(args, w, rank, world, local_rank):
     ms = e0.elapsed_time(e1)
     dom_mode = 0 if w["algo"] in ("gemm", "rkleene") else 2
     k_ms, k_launches, k_pairs = apsp.apsp_trace_read(dom_mode)
-    all_ms, all_launches, _ = apsp.apsp_trace_read(-1) if False else (None, None, None)
 
     ops_step = 2.0 * n ** 3
     ms_max, ops_total = aggregate(ms, args.steps * ops_step, dev)
     value = ops_total / (ms_max * 1e-3) / 1e9
 
     # End to end through the public API: pinned host matrix in, distances back to pinned host.
-    e2e_val = None
+    e2e_val, e2e_parts = None, None
     out_host = torch.empty((n, n), dtype=tdt).pin_memory()
     if args.e2e_steps > 0:
         if w["algo"] == "gemm":
@@ -416,6 +443,8 @@ def run_ours(args, w, rank, world, local_rank):
         if world > 1:
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
         e2e_val = world * ops_step / (float(te.item()) * 1e-3) / 1e9
+        e2e_parts = copy_parts(host, out_host, dev)
+        e2e_parts["e2e_median"] = round(statistics.median(e2e_ms), 2)
 
     # Peak: one (min,+) pair per lane per clock (packed pair add + 3-input min = one issued
     # instruction per pair), 128 lanes per SM.
@@ -423,22 +452,18 @@ def run_ours(args, w, rank, world, local_rank):
     achieved = 2.0 * k_pairs / (k_ms * 1e-3) / 1e12 if k_ms > 0 else None
     sm_mhz = clocks.get("sm_mhz")
     traffic, traffic_note = None, None
-    if dom_mode == 2 and tgemm_src_hash() == PHASE3_TRAFFIC_SRC_HASH and w["dtype"] == "int32" and n >= 4096:
-        traffic = round(PHASE3_DRAM_BYTES_PER_C_ELEM * (n - 128) ** 2)
-        traffic_note = (f"dram bytes per launch from one ncu capture of the 16-bit phase-3 kernel at n=8192, scaled "
-                        f"by (n-128)^2; algorithmic {8 * (n - 128) ** 2} B (each C tile read and written once)")
-    nb = -(-n // 128)
+    bt = 2 if n >= 16384 else 1
+    per_elem = PHASE3_DRAM_BYTES_PER_C_ELEM.get(bt)
+    if dom_mode == 2 and w["dtype"] == "int32" and n >= 4096:
+        if per_elem is None or tgemm_src_hash() != PHASE3_TRAFFIC_SRC_HASH:
+            traffic_note = "no ncu capture of this phase-3 kernel build: traffic not known"
+        else:
+            c_elems = (n - 128 * bt) ** 2
+            traffic = round(per_elem * c_elems)
+            traffic_note = (f"dram bytes per launch from one ncu capture of the 16-bit phase-3 kernel at "
+                            f"n={8192 * bt} ({128 * bt}-vertex blocks), scaled by (n-{128 * bt})^2; "
+                            f"algorithmic {8 * c_elems} B (each C tile read and written once)")
     fw16 = w["algo"] == "fw" and w["dtype"] == "int32" and n >= 4096
-    # Every kernel of ours that is launched per step, including launches that return at once
-    # (the int32 pass runs only when the certificate fails).
-    # FW with the 16-bit pass: normalise, decision, per block of the pass either 12 launches
-    # (256-vertex blocks from n = 16384: the block's own 2 x 3-phase closure, 2 panel copies,
-    # 2 panel products, packing, 16-bit phase 3) or 4 (128-vertex blocks: diagonal, panels,
-    # packing, 16-bit phase 3), the certificate (2) and the 3 launches per 128-vertex block of
-    # the int32 pass.
-    per_block16 = (12 * -(-n // 256)) if n >= 16384 else 4 * nb
-    launches_per_step = {"fw": 4 + per_block16 + 3 * nb if fw16 else 1 + 3 * nb,
-                         "gemm": 6 if w["dtype"] == "int32" else 1, "rkleene": None}[w["algo"]]
     if w["dtype"] != "int32":
         arith = "fp32 packed add + 3-input min"
     elif w["algo"] == "gemm":
@@ -470,9 +495,12 @@ def run_ours(args, w, rank, world, local_rank):
                      "launches": k_launches, "avg_launch_ms": round(k_ms / max(1, k_launches), 4),
                      "traffic": traffic, "traffic_note": traffic_note},
         "clocks": clocks,
+        "e2e_parts_ms": e2e_parts,
         "e2e": {"value": round(e2e_val, 2) if e2e_val else None, "unit": "Gop/s",
                 "h2d_bytes_per_step": mat_bytes, "d2h_bytes_per_step": mat_bytes},
-        "gpu_launches": launches_per_step * args.steps if launches_per_step else None,
+        # kernel launches the library enqueued in the timed region (its own host-side count),
+        # including launches that return at once on the device
+        "gpu_launches": launches,
     }
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
@@ -539,9 +567,11 @@ def run_batched(args, w, rank, world, local_rank):
         apsp.apsp_batched(batch)  # warm the library's per-device set-up before capture
     torch.cuda.synchronize()
     graph = torch.cuda.CUDAGraph()
+    apsp.apsp_launch_count(reset=True)
     with torch.cuda.graph(graph, stream=stream):
         work.copy_(pristine)
         apsp.apsp_batched(batch)
+    launches_per_replay = apsp.apsp_launch_count()
     spin_up(graph.replay)
     for _ in range(args.warmup):
         graph.replay()
@@ -618,6 +648,8 @@ def run_batched(args, w, rank, world, local_rank):
         if it:
             e2e.append(time.perf_counter() - t0)
     e2e_val = world * len(batch) / statistics.median(e2e)
+    e2e_parts = copy_parts(batch.host, out_host, dev)
+    e2e_parts["e2e_median"] = round(statistics.median(e2e) * 1e3, 2)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = 2.0 * sms * LANES_PER_SM * MAX_SM_MHZ * 1e6 / 1e12
     achieved = 2.0 * pairs / (k_ms * 1e-3) / 1e12
@@ -635,9 +667,10 @@ def run_batched(args, w, rank, world, local_rank):
                      "peak": round(peak, 2), "unit": "Tops/s", "frac": round(achieved / peak, 4),
                      "launches": 1, "avg_launch_ms": round(k_ms, 3), "traffic": None},
         "clocks": clocks,
+        "e2e_parts_ms": e2e_parts,
         "e2e": {"value": round(e2e_val, 1), "unit": "graphs/s", "h2d_bytes_per_step": pool_bytes,
                 "d2h_bytes_per_step": pool_bytes},
-        "gpu_launches": args.steps, "status_ok": ok,
+        "gpu_launches": launches_per_replay * args.steps, "status_ok": ok,
     }
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
@@ -709,7 +742,9 @@ def run_serve(args, w, rank, world, local_rank):
     sampler = ClockSampler(local_rank)
     sampler.start()
     reqs = serve.make_requests(t_arr, lib, density=list(ps))
+    apsp.apsp_launch_count(reset=True)
     st = srv.serve(reqs)
+    launches = apsp.apsp_launch_count()
     clocks = sampler.stop()
     base = serve.serve_one_at_a_time(serve.make_requests(t_arr, lib), device=dev)
     ok = apsp.apsp_device_status() == 0
@@ -725,7 +760,7 @@ def run_serve(args, w, rank, world, local_rank):
         "clocks": clocks,
         "e2e": {"value": round(st["p99"], 3), "unit": "ms", "h2d_bytes_per_step": bytes_in,
                 "d2h_bytes_per_step": bytes_in},
-        "gpu_launches": st["launches"]["batch"] + st["launches"]["solo"], "status_ok": ok,
+        "gpu_launches": launches, "status_ok": ok,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -287,6 +287,14 @@ int apsp_mlp_adam(float *params, const float *grads, float *m, float *v, int64_t
 int apsp_trace_enable(int on);
 int apsp_trace_read(int mode, double *total_ms, int64_t *launches, double *pairs);
 
+/* ---- measurement: launch count ---------------------------------------------------------
+ * Number of kernel launches the library has enqueued in this process (every entry point,
+ * including launches that return at once on the device because an earlier step made them
+ * unnecessary), counted on the host as each launch is made.  reset != 0 returns the count
+ * and sets it to zero.  Host-global and thread-safe; launches captured into a CUDA graph are
+ * counted once, at capture. */
+int64_t apsp_launch_count(int reset);
+
 /* ---- measurement: CUDA-core (min,+) rate probe -----------------------------------------
  * Launches `blocks` x `threads` threads, each running `iters` rounds of a register-only
  * (min,+) update of 32 independent accumulators with the instruction sequence `variant`:

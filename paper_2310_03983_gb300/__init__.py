@@ -68,6 +68,7 @@ def _load():
         "apsp_mlp_adam": ([vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, i32,
                            vp], i32),
         "apsp_trace_enable": ([i32], i32),
+        "apsp_launch_count": ([i32], i64),
         "apsp_trace_read": ([i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                              ctypes.POINTER(ctypes.c_double)], i32),
     }
@@ -82,7 +83,8 @@ EXPORTS = ("apsp_version", "apsp_workspace_pool_trim", "apsp_status_str", "apsp_
            "tropical_gemm_workspace_bytes", "tropical_gemm",
            "apsp_fw_workspace_bytes", "apsp_fw", "apsp_rkleene_workspace_bytes", "apsp_rkleene",
            "apsp_fw_signed_workspace_bytes", "apsp_fw_signed", "apsp_squaring_workspace_bytes", "apsp_squaring", "apsp_predecessors_workspace_bytes", "apsp_predecessors",
-           "apsp_probe_minplus", "apsp_trace_enable", "apsp_trace_read", "apsp_batched_workspace_bytes",
+           "apsp_probe_minplus", "apsp_trace_enable", "apsp_trace_read", "apsp_launch_count",
+           "apsp_batched_workspace_bytes",
            "apsp_batched", "apsp_mlp_param_count", "apsp_mlp_backward_workspace_bytes", "apsp_mlp_forward",
            "apsp_mlp_loss", "apsp_mlp_backward", "apsp_mlp_adam")
 
@@ -292,6 +294,11 @@ def apsp_trace_read(mode: int = -1):
     ms, n, pairs = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
     _check(_lib.apsp_trace_read(mode, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(pairs)), "apsp_trace_read")
     return ms.value, n.value, pairs.value
+
+
+def apsp_launch_count(reset: bool = False) -> int:
+    """Kernel launches the library has enqueued in this process; reset=True also zeroes it."""
+    return int(_lib.apsp_launch_count(int(bool(reset))))
 
 
 class Batch:

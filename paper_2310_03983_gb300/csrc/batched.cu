@@ -489,6 +489,7 @@ static int launch_batched(const BatchArgs &a, bool clusters, cudaStream_t s) {
   at.val.clusterDim.z = 1;
   cfg.attrs = &at;
   cfg.numAttrs = 1;
+  note_launch();
   if (cudaLaunchKernelEx(&cfg, batched_kernel<S>, a) != cudaSuccess) {
     cudaGetLastError();
     return APSP_ERR_CUDA;

@@ -180,8 +180,15 @@ __device__ __forceinline__ int4 lds128(const void *p) {
     if (_e != cudaSuccess) return APSP_ERR_CUDA;           \
   } while (0)
 
+namespace apsp {
+// Counts one kernel launch enqueued by the library (host side; read by apsp_launch_count).
+void note_launch();
+}  // namespace apsp
+
+// Follows every kernel launch: counts it and turns a launch error into APSP_ERR_CUDA.
 #define APSP_LAUNCH_CHECK()                                \
   do {                                                     \
+    apsp::note_launch();                                   \
     if (cudaGetLastError() != cudaSuccess) return APSP_ERR_CUDA; \
   } while (0)
 

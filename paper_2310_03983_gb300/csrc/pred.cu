@@ -336,6 +336,7 @@ extern "C" int apsp_predecessors(const void *d, int64_t ldd, const void *w, int6
     pred_encode_kernel<<<(int)(n < cap ? n : cap), 256, 0, s>>>(reinterpret_cast<const int *>(d), ldd,
                                                                 reinterpret_cast<const int *>(w), ldw, De, We, lde, n,
                                                                 sb, inf_i, words, status_word());
+    note_launch();
     if (cudaGetLastError() != cudaSuccess) r = APSP_ERR_CUDA;
   }
   if (!r) {
@@ -361,6 +362,7 @@ extern "C" int apsp_predecessors(const void *d, int64_t ldd, const void *w, int6
   if (!r) {
     const int64_t cap = (int64_t)sm_count() * 8;
     pred_decode_kernel<<<(int)(n < cap ? n : cap), 256, 0, s>>>(pred, ldp, n, sb, inf_i, words);
+    note_launch();
     if (cudaGetLastError() != cudaSuccess) r = APSP_ERR_CUDA;
   }
   if (!r) r = launch_direct<int>(d, ldd, w, ldw, pred, ldp, n, inf_i, words + kWSkip, s);

@@ -1,5 +1,6 @@
 // runtime.cu -- host runtime of libapsp: status word, device queries, TMA descriptor
 // encoding, sentinel handling and the small C-ABI helpers.
+#include <atomic>
 #include <math.h>
 #include <mutex>
 #include <string.h>
@@ -130,6 +131,11 @@ int resolve_inf_f32(const void *inf, float *out) {
   return 0;
 }
 
+// ------------------------------------ launch count -------------------------------------
+static std::atomic<long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
 // ------------------------------------ tracing ------------------------------------------
 struct TraceRec {
   cudaEvent_t e0, e1;
@@ -225,4 +231,8 @@ extern "C" int apsp_device_status(void *stream, int *out) {
          : (bits & (1u << APSP_ERR_DOMAIN)) ? APSP_ERR_DOMAIN
                                             : APSP_OK;
   return APSP_OK;
+}
+
+extern "C" int64_t apsp_launch_count(int reset) {
+  return reset ? apsp::g_launches.exchange(0) : apsp::g_launches.load();
 }

@@ -193,10 +193,12 @@ extern "C" int apsp_fw_signed(void *d, int64_t n, int64_t ld, int dtype, const v
       normalise_signed_kernel<int><<<grid, 256, 0, s>>>(reinterpret_cast<int *>(work), n, ldw, inf_i, words,
                                                         status_word());
       signed_range_kernel<<<1, 1, 0, s>>>(words, n, status_word());
+      note_launch();
     } else {
       normalise_signed_kernel<float><<<grid, 256, 0, s>>>(reinterpret_cast<float *>(work), n, ldw, inf_f, words,
                                                           status_word());
     }
+    note_launch();
     if (cudaGetLastError() != cudaSuccess) r = APSP_ERR_CUDA;
   }
   if (!r) r = fw_signed(work, n, ldw, dtype, inf_i, words, s);

@@ -115,6 +115,7 @@ extern "C" int apsp_squaring(void *d, int64_t n, int64_t ld, int dtype, const vo
     if (!r) {
       commit_kernel<<<(int)(n < cap ? n : cap), 256, 0, s>>>(reinterpret_cast<int *>(work), ldw, C, lde, n, skip,
                                                              words + kWordsUnchanged + t);
+      note_launch();
       if (cudaGetLastError() != cudaSuccess) r = APSP_ERR_CUDA;
     }
   }

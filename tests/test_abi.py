@@ -34,6 +34,10 @@ def test_host_side_calls_without_gpu():
     lib.apsp_status_str.restype = ctypes.c_char_p
     lib.apsp_status_str.argtypes = [ctypes.c_int]
     assert lib.apsp_status_str(0) == b"ok"
+    # the launch counter is host-side: it reads and resets without a GPU
+    lib.apsp_launch_count.restype, lib.apsp_launch_count.argtypes = ctypes.c_int64, [ctypes.c_int]
+    lib.apsp_launch_count(1)
+    assert lib.apsp_launch_count(0) == 0
     f = lib.apsp_rkleene_workspace_bytes
     f.restype, f.argtypes = ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int]
     # n <= cutoff: no scratch; n = 32768: one 16384 x 16384 block, plus (int32 only) the packed

@@ -1,0 +1,98 @@
+"""apsp_launch_count: the library's own count of the kernels it enqueues, which bench.py reports
+as gpu_launches.  Each case checks the count of one call against the launch structure the
+entry point documents, so the figure the bench prints is tied to the code that launches:
+
+  * blocked FW, plain (fp32, or int32 below n = 4096): a1, then per 128-vertex block kb the
+    diagonal closure, the panels and the remaining tiles (Sec. 3.2's three phases), the last
+    two left out when the whole matrix is one block;
+  * blocked FW, int32 from n = 4096 with small weights: a1, the decision, per block of the
+    16-bit pass 4 launches (128-vertex blocks: diagonal, panels, packing, 16-bit phase 3) or,
+    from n = 16384, 12 (256-vertex blocks: the block's own closure as two 3-phase sub-steps,
+    two panel copies, two panel products, packing, 16-bit phase 3), the certificate (2), then
+    the three launches per 128-vertex block of the int32 pass, which return at once on the
+    device when the certificate holds;
+  * an int32 tropical product with workspace room: two bound scans, two packings, the 16-bit
+    launch and the plain launch that returns at once;
+  * launches captured into a CUDA graph count once, at capture.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def apsp():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import paper_2310_03983_gb300 as m
+    return m
+
+
+def _count(apsp, fn):
+    torch.cuda.synchronize()
+    apsp.apsp_launch_count(reset=True)
+    fn()
+    c = apsp.apsp_launch_count()
+    torch.cuda.synchronize()
+    assert apsp.apsp_device_status() == 0
+    return c
+
+
+def _fw_count(apsp, n, dtype):
+    h = workloads.er_graph(n, 0.05, dtype, lo=1, hi=100, seed=n) if dtype == "int32" else \
+        workloads.er_graph(n, 0.05, "float32", dist="uniform", lo=1, hi=100, seed=n)
+    d = torch.from_numpy(h).cuda()
+    return _count(apsp, lambda: apsp.apsp_fw(d))
+
+
+@pytest.mark.parametrize("n,dtype", [(100, "float32"), (1000, "float32"), (3000, "int32")])
+def test_fw_plain_launches(apsp, n, dtype):
+    nb = -(-n // 128)
+    want = 2 if nb == 1 else 1 + 3 * nb
+    assert _fw_count(apsp, n, dtype) == want
+
+
+@pytest.mark.parametrize("n", [4096, 16384])
+def test_fw16_launches(apsp, n):
+    nb = -(-n // 128)
+    per_block16 = 12 * -(-n // 256) if n >= 16384 else 4 * nb
+    assert _fw_count(apsp, n, "int32") == 4 + per_block16 + 3 * nb
+
+
+def test_tropical_gemm_int32_launches(apsp):
+    h = workloads.er_graph(1024, 0.1, "int32", lo=1, hi=100, seed=5)
+    a = torch.from_numpy(h).cuda()
+    c = torch.empty_like(a)
+    assert _count(apsp, lambda: apsp.tropical_gemm(c, a, a)) == 6
+
+
+def test_rkleene_counts_are_repeatable_and_graph_capture_counts_once(apsp):
+    h = workloads.er_graph(1500, 0.05, "int32", lo=1, hi=100, seed=9)
+    d1, d2 = torch.from_numpy(h).cuda(), torch.from_numpy(h).cuda()
+    c1 = _count(apsp, lambda: apsp.apsp_rkleene(d1, cutoff=256))
+    c2 = _count(apsp, lambda: apsp.apsp_rkleene(d2, cutoff=256))
+    assert c1 == c2 > 0
+    assert np.array_equal(d1.cpu().numpy(), d2.cpu().numpy())
+
+    small = workloads.er_graph(300, 0.1, "int32", lo=1, hi=100, seed=10)
+    d = torch.from_numpy(small).cuda()
+    ws = torch.empty(apsp.apsp_fw_workspace_bytes(300, 300, torch.int32), dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        apsp.apsp_fw(d, ws=ws)  # per-device set-up before capture
+    torch.cuda.synchronize()
+    d.copy_(torch.from_numpy(small).cuda())
+    g = torch.cuda.CUDAGraph()
+    apsp.apsp_launch_count(reset=True)
+    with torch.cuda.graph(g, stream=s):
+        apsp.apsp_fw(d, ws=ws)
+    captured = apsp.apsp_launch_count()
+    assert captured == 1 + 3 * 3
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    assert apsp.apsp_launch_count() == captured
