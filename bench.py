@@ -445,6 +445,7 @@ def run_ours(args, w, rank, world, local_rank):
         e2e_val = world * ops_step / (float(te.item()) * 1e-3) / 1e9
         e2e_parts = copy_parts(host, out_host, dev)
         e2e_parts["e2e_median"] = round(statistics.median(e2e_ms), 2)
+        e2e_parts["e2e_samples"] = [round(x, 2) for x in e2e_ms]
 
     # Peak: one (min,+) pair per lane per clock (packed pair add + 3-input min = one issued
     # instruction per pair), 128 lanes per SM.

@@ -223,6 +223,18 @@ int apsp_rkleene_noalloc(void *d, int64_t n, int64_t ld, int dtype, const void *
  * in the device status word (the rest of the batch is still closed).  ns[g] <= 0 is skipped.
  * The workspace holds the work-queue counter (apsp_batched_workspace_bytes). */
 size_t apsp_batched_workspace_bytes(int64_t count);
+/* Workspace with which apsp_batched closes the larger graphs of an int32 batch in lockstep
+ * on the tropical-GEMM engine instead of one per CTA (same results).  ns_host: host copy of
+ * the sizes (the same values as the device ns passed to apsp_batched).  Graphs of 257..2048
+ * vertices are copied into a staging matrix in the workspace, each padded to whole 128-vertex
+ * tiles; per 128-vertex block, one launch per phase runs it for every such graph (phase 3 on
+ * packed 16-bit pairs, certified per graph as in apsp_fw, with an int32 pass for the graphs
+ * whose certificate fails).  Every other graph goes to the persistent kernel.  Returns
+ * apsp_batched_workspace_bytes(count) when no graph qualifies or dtype is APSP_F32.  The
+ * staged path runs only when apsp_batched gets ns_host, a caller workspace of at least this
+ * size and a sentinel above 0x3FFF; a staged graph whose device size, leading dimension or
+ * offset disagree with ns_host or the layout rules is left untouched and sets APSP_ERR_ARG. */
+size_t apsp_batched_staged_workspace_bytes(const int32_t *ns_host, int64_t count, int dtype);
 int apsp_batched(void *pool, const int64_t *offsets, const int32_t *ns, const int32_t *lds,
                  const int32_t *order, const int32_t *ns_host, int64_t count, int dtype,
                  const void *inf, void *ws, size_t ws_bytes, void *stream);

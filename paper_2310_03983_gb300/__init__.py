@@ -59,6 +59,7 @@ def _load():
         "apsp_predecessors_workspace_bytes": ([i64, i32], sz),
         "apsp_predecessors": ([vp, i64, vp, i64, vp, i64, i64, i32, vp, vp, sz, vp], i32),
         "apsp_batched_workspace_bytes": ([i64], sz),
+        "apsp_batched_staged_workspace_bytes": ([vp, i64, i32], sz),
         "apsp_batched": ([vp, vp, vp, vp, vp, vp, i64, i32, vp, vp, sz, vp], i32),
         "apsp_mlp_param_count": ([i32], i64),
         "apsp_mlp_backward_workspace_bytes": ([i32, i32], sz),
@@ -84,7 +85,7 @@ EXPORTS = ("apsp_version", "apsp_workspace_pool_trim", "apsp_status_str", "apsp_
            "apsp_fw_workspace_bytes", "apsp_fw", "apsp_rkleene_workspace_bytes", "apsp_rkleene",
            "apsp_fw_signed_workspace_bytes", "apsp_fw_signed", "apsp_squaring_workspace_bytes", "apsp_squaring", "apsp_predecessors_workspace_bytes", "apsp_predecessors",
            "apsp_probe_minplus", "apsp_trace_enable", "apsp_trace_read", "apsp_launch_count",
-           "apsp_batched_workspace_bytes",
+           "apsp_batched_workspace_bytes", "apsp_batched_staged_workspace_bytes",
            "apsp_batched", "apsp_mlp_param_count", "apsp_mlp_backward_workspace_bytes", "apsp_mlp_forward",
            "apsp_mlp_loss", "apsp_mlp_backward", "apsp_mlp_adam")
 
@@ -305,7 +306,7 @@ class Batch:
     """A batch of graphs packed into one device pool, in the layout apsp_batched expects:
     graph g at element offset offsets[g], leading dimension round_up(n_g, 4)."""
 
-    def __init__(self, mats, device=None, pin=True):
+    def __init__(self, mats, device=None, pin=True, staged=True):
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         mats = [np.asarray(m) for m in mats]
         if not mats:
@@ -331,7 +332,10 @@ class Batch:
         self.d_lds = torch.from_numpy(self.lds).to(dev)
         self.order = np.argsort(-self.ns, kind="stable").astype(np.int32)  # largest first
         self.d_order = torch.from_numpy(self.order).to(dev)
-        self.ws = torch.empty(_lib.apsp_batched_workspace_bytes(len(mats)), dtype=torch.uint8, device=dev)
+        # staged: room for closing the larger int32 graphs in lockstep on the GEMM engine
+        wsb = (apsp_batched_staged_workspace_bytes(self.ns, self.dtype) if staged
+               else _lib.apsp_batched_workspace_bytes(len(mats)))
+        self.ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
 
     def __len__(self):
         return len(self.ns)
@@ -356,6 +360,13 @@ class _OneGraph:
                                torch.tensor([ld], dtype=torch.int32, device=dev),
                                torch.empty(_lib.apsp_batched_workspace_bytes(1), dtype=torch.uint8, device=dev))
         return cls._cache[key]
+
+
+def apsp_batched_staged_workspace_bytes(ns_host, dtype=torch.int32) -> int:
+    """Workspace bytes with which apsp_batched runs the larger int32 graphs in lockstep."""
+    ns = np.ascontiguousarray(ns_host, dtype=np.int32)
+    code = APSP_I32 if dtype == torch.int32 else APSP_F32
+    return int(_lib.apsp_batched_staged_workspace_bytes(ns.ctypes.data_as(ctypes.c_void_p), len(ns), code))
 
 
 def apsp_close_cta(d: torch.Tensor, inf=None, stream=None):

@@ -18,7 +18,10 @@
 // inter-CTA synchronisation: there is no spin-wait anywhere in this kernel.
 #include <cooperative_groups.h>
 
+#include <vector>
+
 #include "diag.cuh"
+#include "grouped.cuh"
 #include "slab.cuh"
 #include "tgemm.cuh"
 
@@ -36,7 +39,8 @@ struct BatchArgs {
   int *pool;
   const int64_t *offsets;
   const int32_t *ns, *lds, *order;
-  int64_t count;
+  int64_t count;  // graphs in the arrays (valid indices are 0..count-1)
+  int64_t nq;     // queue entries: order[0..nq) (or 0..nq-1 without order)
   int inf_i;
   float inf_f;
   int *queue;
@@ -333,7 +337,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(const BatchArgs a
   if (csize > 1) {
     __shared__ double s_work[kBThreads / 32];
     double w = 0.0;
-    for (int k = threadIdx.x; k < a.count; k += kBThreads) {
+    for (int k = threadIdx.x; k < a.nq; k += kBThreads) {
       const int g = a.order ? a.order[k] : k;
       if (g >= 0 && g < a.count) {
         const double n = (double)max(a.ns[g], 0);
@@ -343,14 +347,14 @@ __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(const BatchArgs a
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
     if ((threadIdx.x & 31) == 0) s_work[threadIdx.x >> 5] = w;
-    if (threadIdx.x == 0) s_nbig = a.count;
+    if (threadIdx.x == 0) s_nbig = (int)a.nq;
     __syncthreads();
     double total = 0.0;
 #pragma unroll
     for (int i = 0; i < kBThreads / 32; ++i) total += s_work[i];
     const double big3 = fmax(0.5 * total / (double)gridDim.x, (double)(64 * csize) * (64 * csize) * (64 * csize));
-    int first_small = a.count;
-    for (int k = threadIdx.x; k < a.count; k += kBThreads) {
+    int first_small = (int)a.nq;
+    for (int k = threadIdx.x; k < a.nq; k += kBThreads) {
       const int g = a.order ? a.order[k] : k;
       const double n = (g >= 0 && g < a.count) ? (double)a.ns[g] : 0.0;
       if (!(n * n * n > big3)) {
@@ -394,7 +398,7 @@ __global__ void __launch_bounds__(kBThreads, 1) batched_kernel(const BatchArgs a
     __syncthreads();
     const int idx = s_idx;
     __syncthreads();
-    if (idx >= a.count) break;
+    if (idx >= a.nq) break;
     const int g = a.order ? a.order[idx] : idx;
     if (g < 0 || g >= a.count) {
       if (threadIdx.x == 0) flag_status(a.status, APSP_ERR_ARG);
@@ -499,9 +503,34 @@ static int launch_batched(const BatchArgs &a, bool clusters, cudaStream_t s) {
 
 }  // namespace apsp
 
+namespace {
+
+struct RestCtx {
+  apsp::BatchArgs a;
+  bool clusters;
+  cudaStream_t s;
+};
+
+// The persistent kernel over a sub-list of the batch (the graphs the staged path leaves out).
+int launch_rest_graphs(void *ctx, const int *order, int64_t nq) {
+  RestCtx *c = reinterpret_cast<RestCtx *>(ctx);
+  apsp::BatchArgs a = c->a;
+  a.order = order;
+  a.nq = nq;
+  return apsp::launch_batched<int>(a, c->clusters, c->s);
+}
+
+}  // namespace
+
 extern "C" size_t apsp_batched_workspace_bytes(int64_t count) {
   (void)count;
   return 256;
+}
+
+extern "C" size_t apsp_batched_staged_workspace_bytes(const int32_t *ns_host, int64_t count, int dtype) {
+  apsp::StagePlan pl;
+  if (dtype != APSP_I32 || !apsp::make_stage_plan(ns_host, count, pl)) return 256;
+  return apsp::staged_workspace_bytes(pl, count);
 }
 
 extern "C" int apsp_batched(void *pool, const int64_t *offsets, const int32_t *ns, const int32_t *lds,
@@ -528,10 +557,23 @@ extern "C" int apsp_batched(void *pool, const int64_t *offsets, const int32_t *n
   a.lds = lds;
   a.order = order;
   a.count = count;
+  a.nq = count;
   a.queue = reinterpret_cast<int *>(ws);
   a.status = status_word();
   int r = APSP_OK;
   if (cudaMemsetAsync(a.queue, 0, 2 * sizeof(int), s) != cudaSuccess) r = APSP_ERR_CUDA;
+  // Graphs of 257..2048 vertices go through the engine in lockstep when the workspace has room
+  // for the staging (int32, a sentinel above the 16-bit cap).
+  StagePlan pl;
+  if (!r && !own && dtype == APSP_I32 && a.inf_i > kCap16 && make_stage_plan(ns_host, count, pl) &&
+      ws_bytes >= staged_workspace_bytes(pl, count)) {
+    std::vector<int32_t> rest_ns;
+    rest_ns.reserve(pl.rest.size());
+    for (int g : pl.rest) rest_ns.push_back(ns_host[g]);
+    RestCtx ctx = {a, needs_clusters(rest_ns.data(), (int64_t)rest_ns.size()), s};
+    r = batched_staged(pl, a.pool, offsets, ns, lds, count, a.inf_i, ws, launch_rest_graphs, &ctx, s);
+    return r;
+  }
   const bool clusters = needs_clusters(ns_host, count);
   if (!r) r = dtype == APSP_I32 ? launch_batched<int>(a, clusters, s) : launch_batched<float>(a, clusters, s);
   ws_free(own, s);

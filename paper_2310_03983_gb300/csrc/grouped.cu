@@ -1,0 +1,532 @@
+// grouped.cu -- a7 for the larger graphs of a batch: blocked Floyd-Warshall over many graphs in
+// lockstep on the TMA engine.
+//
+// The persistent batched kernel closes each graph on one CTA with its own cp.async pipeline.
+// For graphs of a few hundred vertices and more, that per-CTA pipeline runs well below the
+// engine's rate, and those graphs carry nearly all of a batch's work (n^3).  Here they are
+// closed together instead: copied ("staged") one below the other into one tall matrix with a
+// common leading dimension, each padded to nb whole 128-tiles with isolated vertices (0 on the
+// diagonal, the sentinel elsewhere; they change no distance).  Graphs are grouped by nb, and
+// the groups are listed by decreasing nb, so the graphs still open at block kb (nb > kb) are a
+// prefix of the staged list.  Per block kb one launch runs a step for every open graph:
+//   phase 1  one CTA per graph closes its diagonal tile (Eq. 1, int32, in registers);
+//   packing  its column and row panels (the diagonal tile included) as 16-bit pairs;
+//   phase 2  the engine's panel mode on the packed panels (two (min,+) pairs per DPX op);
+//   packing  the updated panels;
+//   phase 3  the engine's 16-bit phase 3 over all graphs' remaining tiles.
+// Phases 2 and 3 compute the closure truncated at CAP = 0x3FFF (truncation is a homomorphism
+// of (min,+), so exact and truncated steps may be mixed), certified per graph exactly as
+// apsp_fw certifies one matrix: the largest stored value below CAP plus the graph's largest
+// weight must stay below CAP; then every entry at or above CAP is unreachable.
+// Graphs whose certificate fails, and graphs whose weights exceed CAP / 4, are finished by a
+// second lockstep pass in int32 (exact fp32 on the int32 bit patterns when every (n - 1) *
+// largest weight < 2^24) over the mapped matrix, which lies between the distances and the
+// weights; that pass's launches return at once when no graph needs it.  Results are identical
+// to closing each graph alone.
+//
+// The plan (which graphs, their order and rows) is made on the host from the host copy of the
+// sizes and reaches the device as kernel arguments, so the whole sequence can be captured in a
+// CUDA graph.  Graphs whose device size, leading dimension or offset disagree with the plan are
+// left untouched and flagged (APSP_ERR_ARG), as the persistent kernel does.
+#include <algorithm>
+#include <climits>
+#include <vector>
+
+#include "diag.cuh"
+#include "grouped.cuh"
+#include "tgemm.cuh"
+
+namespace apsp {
+
+namespace {
+
+constexpr int kGfUse16 = 1, kGfRerun = 2, kGfBad = 4;
+// Words of the 256-byte block at the front of the workspace (the persistent kernel's queue
+// counters are words 0 and 1): [8] largest (n - 1) * weight over the staged graphs, [9] 0,
+// [10] some graph needs the int32 pass.
+constexpr int kWBound = 8, kWRerun = 10;
+constexpr int kPlanChunk = 4096;
+
+struct GroupSet {
+  int ngroups;
+  GraphGroup groups[kMaxGroups];
+};
+
+struct PlanChunk {
+  int *dst;
+  int n;
+  int idx[kPlanChunk];
+};
+
+struct StageArgs {
+  GroupSet gs;
+  int *S;
+  int64_t ldS, R;
+  int *pool;
+  const int64_t *offsets;
+  const int32_t *ns, *lds;
+  const int *sidx;
+  int *gflags, *maxb, *wmaxg, *words;
+  int inf;
+  unsigned int *status;
+};
+
+// Staged graph holding staged row r: its index q, first row and nb.
+__device__ __forceinline__ bool row_graph(const GroupSet &gs, int64_t r, int &q, int64_t &base, int &nb) {
+  bool found = false;
+#pragma unroll
+  for (int k = 0; k < kMaxGroups; ++k) {
+    if (!found && k < gs.ngroups) {
+      const GraphGroup &g = gs.groups[k];
+      const int64_t rows = (int64_t)g.nb * kBM;
+      if (r >= g.row0 && r < g.row0 + rows * g.count) {
+        const int64_t ql = (r - g.row0) / rows;
+        q = g.first + (int)ql;
+        base = g.row0 + ql * rows;
+        nb = g.nb;
+        found = true;
+      }
+    }
+  }
+  return found;
+}
+
+// First row and nb of staged graph q.
+__device__ __forceinline__ void graph_rows(const GroupSet &gs, int q, int64_t &base, int &nb) {
+#pragma unroll
+  for (int k = 0; k < kMaxGroups; ++k) {
+    if (k < gs.ngroups) {
+      const GraphGroup &g = gs.groups[k];
+      if (q >= g.first && q < g.first + g.count) {
+        nb = g.nb;
+        base = g.row0 + (int64_t)(q - g.first) * g.nb * kBM;
+      }
+    }
+  }
+}
+
+__global__ void plan_kernel(const __grid_constant__ PlanChunk c) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < c.n; i += gridDim.x * blockDim.x) c.dst[i] = c.idx[i];
+}
+
+__device__ __forceinline__ bool graph_ok(const StageArgs &a, int g, int nb, int &n, int &ld, int64_t &off) {
+  n = a.ns[g];
+  ld = a.lds[g];
+  off = a.offsets[g];
+  return n > 0 && ld >= n && !(ld & 3) && !(off & 3) && off >= 0 && (n + kBM - 1) / kBM == nb;
+}
+
+// a1 into the staging matrix, one warp per staged row: zero diagonal, entries >= inf become
+// inf, negative entries flag APSP_ERR_DOMAIN; padding rows and columns are isolated vertices.
+// The largest finite weight of each graph is maxed into wmaxg[q].
+__global__ void __launch_bounds__(256) stage_in_kernel(const StageArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < a.R; r += warps) {
+    int q = 0, nb = 0;
+    int64_t base = 0;
+    if (!row_graph(a.gs, r, q, base, nb)) continue;
+    const int g = a.sidx[q];
+    int n = 0, ld = 0;
+    int64_t off = 0;
+    const bool ok = graph_ok(a, g, nb, n, ld, off);
+    const int i = (int)(r - base), w = nb * kBM;
+    int *dst = a.S + r * a.ldS;
+    if (!ok) {
+      if (i == 0 && lane == 0) {
+        atomicOr(a.gflags + q, kGfBad);
+        flag_status(a.status, APSP_ERR_ARG);
+      }
+      for (int c = lane * 4; c < w; c += 128) {
+        int4 v = make_int4(a.inf, a.inf, a.inf, a.inf);
+        if (i >= c && i < c + 4) (&v.x)[i - c] = 0;
+        *reinterpret_cast<int4 *>(dst + c) = v;
+      }
+      continue;
+    }
+    const int *src = a.pool + off + (int64_t)i * ld;
+    bool bad = false;
+    int m = 0;
+    for (int c = lane * 4; c < w; c += 128) {
+      int4 v = make_int4(a.inf, a.inf, a.inf, a.inf);
+      if (i < n) {
+        if (c + 3 < n) {
+          v = *reinterpret_cast<const int4 *>(src + c);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (c + e < n) (&v.x)[e] = src[c + e];
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        int x = (&v.x)[e];
+        if (c + e == i) {
+          x = 0;
+        } else {
+          bad |= x < 0;
+          x = x >= a.inf ? a.inf : x;
+          if (x < a.inf) m = max(m, x);
+        }
+        (&v.x)[e] = x;
+      }
+      *reinterpret_cast<int4 *>(dst + c) = v;
+    }
+    m = __reduce_max_sync(0xffffffffu, m);
+    if (__any_sync(0xffffffffu, bad) && lane == 0) flag_status(a.status, APSP_ERR_DOMAIN);
+    if (lane == 0 && m > 0) atomicMax(a.wmaxg + q, m);
+  }
+}
+
+// Per graph: the 16-bit pass is used when the largest weight is at most CAP / 4 (else the
+// int32 pass does all the work), and the bound word for exact fp32 arithmetic.
+__global__ void stage_decide_kernel(const StageArgs a, int64_t G) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < G; q += (int64_t)gridDim.x * blockDim.x) {
+    if (a.gflags[q] & kGfBad) continue;
+    const int w = a.wmaxg[q], n = a.ns[a.sidx[q]];
+    const int64_t prod = (int64_t)(n - 1) * (int64_t)w;
+    atomicMax(a.words + kWBound, (int)(prod < INT_MAX ? prod : INT_MAX));
+    if (w <= kCap16 / 4) {
+      a.gflags[q] |= kGfUse16;
+    } else {
+      a.gflags[q] |= kGfRerun;
+      a.words[kWRerun] = 1;
+    }
+  }
+}
+
+// Phase 1 for every graph with nb > kb (a prefix of the staged list: one CTA each) that the
+// mask admits.  run_if (may be null): every CTA returns at once unless *run_if is set.
+__global__ void __launch_bounds__(256) group_diag_kernel(int *S, int64_t ldS, GroupSet gs, int kb, const int *gflags,
+                                                         int mask, int want, const int *run_if) {
+  if (run_if && !*run_if) return;
+  const int q = blockIdx.x;
+  if ((gflags[q] & mask) != want) return;
+  int64_t base = 0;
+  int nb = 0;
+  graph_rows(gs, q, base, nb);
+  if (nb <= kb) return;
+  __shared__ __align__(16) int buf[512];
+  int *T = S + (base + (int64_t)kb * kBM) * ldS + (int64_t)kb * kBM;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tm = (warp & 3) * 4 + (lane >> 3), tn = (warp >> 2) * 8 + (lane & 7);
+  int r[8][8];
+  load_tile_regs(r, T, ldS, kBM, tm, tn);
+  close_tile_regs<false>(r, kBM, tm, tn, buf);
+  store_tile_regs(r, T, ldS, kBM, tm, tn);
+}
+
+// Packs, for graph blockIdx.x of the 16-bit pass (open at block kb), its column panel (its
+// rows x 64 words, at the same rows of A16) and its row panel (64 words x its columns, at rows
+// 64 q of B16) as 16-bit pairs of consecutive k, every value capped at CAP; the diagonal tile
+// is part of both.  blockIdx.y splits a graph's rows among gridDim.y CTAs.
+__device__ __forceinline__ int pack_pair(int lo, int hi) { return (min(hi, kCap16) << 16) | min(lo, kCap16); }
+
+__global__ void __launch_bounds__(256) group_pack16_kernel(const int *S, int64_t ldS, GroupSet gs, int kb,
+                                                           const int *gflags, int *A16, int *B16) {
+  const int q = blockIdx.x;
+  if ((gflags[q] & (kGfBad | kGfUse16)) != kGfUse16) return;
+  int64_t base = 0;
+  int nb = 0;
+  graph_rows(gs, q, base, nb);
+  if (nb <= kb) return;
+  const int W = nb * kBM, kb0 = kb * kBM, t = threadIdx.x;
+  const int *D = S + base * ldS;
+  // Column panel: row r, word w = t % 64 (a coalesced 512-byte row segment per 64 threads).
+  for (int r = blockIdx.y * 4 + (t >> 6); r < W; r += gridDim.y * 4) {
+    const int w = t & 63;
+    const int2 v = *reinterpret_cast<const int2 *>(D + (int64_t)r * ldS + kb0 + 2 * w);
+    A16[(base + r) * 64 + w] = pack_pair(v.x, v.y);
+  }
+  // Row panel: word row w, four columns per thread.
+  const int quads = W / 4;
+  for (int e = blockIdx.y * 256 + t; e < 64 * quads; e += gridDim.y * 256) {
+    const int w = e / quads, c = 4 * (e - w * quads);
+    const int4 lo = *reinterpret_cast<const int4 *>(D + (int64_t)(kb0 + 2 * w) * ldS + c);
+    const int4 hi = *reinterpret_cast<const int4 *>(D + (int64_t)(kb0 + 2 * w + 1) * ldS + c);
+    *reinterpret_cast<int4 *>(B16 + ((int64_t)q * 64 + w) * ldS + c) =
+        make_int4(pack_pair(lo.x, hi.x), pack_pair(lo.y, hi.y), pack_pair(lo.z, hi.z), pack_pair(lo.w, hi.w));
+  }
+}
+
+// For graphs of the 16-bit pass: maxb[q] = largest stored value below CAP, every entry at or
+// above CAP becomes the sentinel.  One warp per staged row.
+__global__ void __launch_bounds__(256) group_certify_kernel(const StageArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < a.R; r += warps) {
+    int q = 0, nb = 0;
+    int64_t base = 0;
+    if (!row_graph(a.gs, r, q, base, nb)) continue;
+    if ((a.gflags[q] & (kGfBad | kGfUse16)) != kGfUse16) continue;
+    int *row = a.S + r * a.ldS;
+    int m = 0;
+    for (int c = lane * 4; c < nb * kBM; c += 128) {
+      int4 v = *reinterpret_cast<const int4 *>(row + c);
+      bool changed = false;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int x = (&v.x)[e];
+        if (x < kCap16) {
+          m = max(m, x);
+        } else if (x != a.inf) {
+          (&v.x)[e] = a.inf;
+          changed = true;
+        }
+      }
+      if (changed) *reinterpret_cast<int4 *>(row + c) = v;
+    }
+    m = __reduce_max_sync(0xffffffffu, m);
+    if (lane == 0 && m > 0) atomicMax(a.maxb + q, m);
+  }
+}
+
+__global__ void group_verdict_kernel(const StageArgs a, int64_t G) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < G; q += (int64_t)gridDim.x * blockDim.x) {
+    if ((a.gflags[q] & (kGfBad | kGfUse16)) != kGfUse16) continue;
+    if ((int64_t)a.maxb[q] + (int64_t)a.wmaxg[q] >= kCap16) {
+      a.gflags[q] |= kGfRerun;
+      a.words[kWRerun] = 1;
+    }
+  }
+}
+
+// The closed n x n part of every staged graph back into the caller's pool.
+__global__ void __launch_bounds__(256) stage_out_kernel(const StageArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < a.R; r += warps) {
+    int q = 0, nb = 0;
+    int64_t base = 0;
+    if (!row_graph(a.gs, r, q, base, nb)) continue;
+    if (a.gflags[q] & kGfBad) continue;
+    const int g = a.sidx[q];
+    const int n = a.ns[g], ld = a.lds[g];
+    const int i = (int)(r - base);
+    if (i >= n) continue;
+    const int *src = a.S + r * a.ldS;
+    int *dst = a.pool + a.offsets[g] + (int64_t)i * ld;
+    for (int c = lane * 4; c < n; c += 128) {
+      const int4 v = *reinterpret_cast<const int4 *>(src + c);
+      if (c + 3 < n) {
+        *reinterpret_cast<int4 *>(dst + c) = v;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (c + e < n) dst[c + e] = (&v.x)[e];
+      }
+    }
+  }
+}
+
+struct Layout {
+  size_t gflags, maxb, wmaxg, lists, S, A16, B16, total;
+};
+
+Layout layout_of(const StagePlan &pl, int64_t count) {
+  Layout L;
+  size_t o = kFlagBytes;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o += (size_t)round_up((int64_t)bytes, 256);
+    return at;
+  };
+  L.gflags = take(pl.G * 4);
+  L.maxb = take(pl.G * 4);
+  L.wmaxg = take(pl.G * 4);
+  L.lists = take((size_t)count * 4);
+  L.S = take((size_t)pl.R * pl.NP * 4);
+  L.A16 = take((size_t)pl.R * 64 * 4);
+  L.B16 = take((size_t)pl.G * 64 * pl.NP * 4);
+  L.total = o;
+  return L;
+}
+
+int launch_plan_lists(int *dst, const std::vector<int> &idx, cudaStream_t s) {
+  for (size_t at = 0; at < idx.size(); at += kPlanChunk) {
+    PlanChunk c;
+    c.dst = dst + at;
+    c.n = (int)std::min<size_t>(kPlanChunk, idx.size() - at);
+    std::copy(idx.begin() + at, idx.begin() + at + c.n, c.idx);
+    plan_kernel<<<(c.n + 255) / 256, 256, 0, s>>>(c);
+    APSP_LAUNCH_CHECK();
+  }
+  return APSP_OK;
+}
+
+}  // namespace
+
+bool make_stage_plan(const int32_t *ns_host, int64_t count, StagePlan &pl) {
+  pl = StagePlan();
+  if (!ns_host || count <= 0 || count > (1 << 24)) return false;
+  std::vector<int64_t> per_nb(kGroupMaxNb + 1, 0);
+  for (int64_t g = 0; g < count; ++g) {
+    const int n = ns_host[g];
+    const int nb = n > 0 ? (n + kBM - 1) / kBM : 0;
+    if (nb >= kGroupMinNb && nb <= kGroupMaxNb) ++per_nb[nb];
+  }
+  std::vector<int> chosen;  // the kMaxGroups largest block counts present, decreasing
+  for (int nb = kGroupMaxNb; nb >= kGroupMinNb && (int)chosen.size() < kMaxGroups; --nb)
+    if (per_nb[nb] > 0) chosen.push_back(nb);
+  if (chosen.empty()) return false;
+  std::vector<int> order(count);
+  for (int64_t g = 0; g < count; ++g) order[g] = (int)g;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return ns_host[x] > ns_host[y]; });
+  std::vector<char> staged(count, 0);
+  int64_t row = 0;
+  for (int nb : chosen) {
+    GraphGroup gg = {};
+    gg.row0 = row;
+    gg.first = (int)pl.staged.size();
+    gg.nb = nb;
+    for (int g : order) {
+      const int n = ns_host[g];
+      if (n > 0 && (n + kBM - 1) / kBM == nb) {
+        pl.staged.push_back(g);
+        staged[g] = 1;
+        ++gg.count;
+      }
+    }
+    row += (int64_t)gg.count * nb * kBM;
+    pl.groups[pl.ngroups++] = gg;
+  }
+  for (int g : order)
+    if (!staged[g]) pl.rest.push_back(g);
+  pl.G = (int64_t)pl.staged.size();
+  pl.R = row;
+  pl.NP = chosen.front() * kBM;
+  if (pl.R > (int64_t)1 << 30) {  // keeps every staged row index an int
+    pl = StagePlan();
+    return false;
+  }
+  return true;
+}
+
+size_t staged_workspace_bytes(const StagePlan &pl, int64_t count) { return layout_of(pl, count).total; }
+
+int batched_staged(const StagePlan &pl, int *pool, const int64_t *offsets, const int32_t *ns, const int32_t *lds,
+                   int64_t count, int inf_i, void *ws, int (*launch_rest)(void *ctx, const int *order, int64_t nq),
+                   void *ctx, cudaStream_t s) {
+  const Layout L = layout_of(pl, count);
+  uint8_t *w = reinterpret_cast<uint8_t *>(ws);
+  int *words = reinterpret_cast<int *>(w);
+  StageArgs a = {};
+  a.gs.ngroups = pl.ngroups;
+  for (int k = 0; k < pl.ngroups; ++k) a.gs.groups[k] = pl.groups[k];
+  a.S = reinterpret_cast<int *>(w + L.S);
+  a.ldS = pl.NP;
+  a.R = pl.R;
+  a.pool = pool;
+  a.offsets = offsets;
+  a.ns = ns;
+  a.lds = lds;
+  int *lists = reinterpret_cast<int *>(w + L.lists);
+  a.sidx = lists;
+  a.gflags = reinterpret_cast<int *>(w + L.gflags);
+  a.maxb = reinterpret_cast<int *>(w + L.maxb);
+  a.wmaxg = reinterpret_cast<int *>(w + L.wmaxg);
+  a.words = words;
+  a.inf = inf_i;
+  a.status = status_word();
+  int *A16 = reinterpret_cast<int *>(w + L.A16);
+  int *B16 = reinterpret_cast<int *>(w + L.B16);
+
+  APSP_CUDA_TRY(cudaMemsetAsync(words + kWBound, 0, 4 * sizeof(int), s));
+  APSP_CUDA_TRY(cudaMemsetAsync(w + L.gflags, 0, L.lists - L.gflags, s));  // gflags, maxb, wmaxg
+  std::vector<int> all(pl.staged);
+  all.insert(all.end(), pl.rest.begin(), pl.rest.end());
+  int r;
+  if ((r = launch_plan_lists(lists, all, s))) return r;
+
+  // The graphs left out of the staging go to the persistent kernel first.
+  if (!pl.rest.empty() && (r = launch_rest(ctx, lists + pl.G, (int64_t)pl.rest.size()))) return r;
+
+  const int64_t cap = (int64_t)sm_count() * 8;
+  const int row_grid = (int)std::min<int64_t>(cap, cdiv(pl.R, 8));
+  const int g_grid = (int)std::min<int64_t>(cap, cdiv(pl.G, 256));
+  stage_in_kernel<<<row_grid, 256, 0, s>>>(a);
+  APSP_LAUNCH_CHECK();
+  stage_decide_kernel<<<g_grid, 256, 0, s>>>(a, pl.G);
+  APSP_LAUNCH_CHECK();
+
+  CUtensorMap mA, mB, mC, pA, pB;
+  if ((r = make_operand_maps(a.S, pl.R, pl.NP, pl.NP, APSP_I32, &mA, &mB, &mC))) return r;
+  if ((r = make_operand_maps(A16, pl.R, 64, 64, APSP_I32, &pA, nullptr, nullptr))) return r;
+  if ((r = make_operand_maps(B16, pl.G * 64, pl.NP, pl.NP, APSP_I32, nullptr, &pB, nullptr))) return r;
+
+  TileProblem p = {};
+  p.C = a.S;
+  p.ldc = pl.NP;
+  p.inf_i = inf_i;
+  p.status = status_word();
+  p.wmax = words + kWBound;  // (n - 1) * largest weight over every staged graph, then 0
+  p.wmult = 1;
+  p.no_trace = 1;
+  p.bt = 1;
+  p.ngroups = pl.ngroups;
+  for (int k = 0; k < pl.ngroups; ++k) p.groups[k] = pl.groups[k];
+  p.gflags = a.gflags;
+  const int max_nb = pl.groups[0].nb;
+
+  // Pass 1: graphs of the 16-bit pass.  Per block: the diagonal tile (exact), the packed
+  // panels, phase 2 on them (truncated), the panels packed again, phase 3 (truncated).
+  for (int kb = 0; kb < max_nb; ++kb) {
+    int64_t open = 0, panels = 0, rest = 0;
+    for (int k = 0; k < pl.ngroups; ++k) {
+      const int64_t nb = pl.groups[k].nb, c = pl.groups[k].count;
+      if (nb <= kb) continue;
+      open += c;
+      panels += c * 2 * (nb - 1);
+      rest += c * (nb - 1) * (nb - 1);
+    }
+    const dim3 pack_grid((unsigned)open, 4);
+    group_diag_kernel<<<(int)open, 256, 0, s>>>(a.S, pl.NP, a.gs, kb, a.gflags, kGfBad | kGfUse16, kGfUse16, nullptr);
+    APSP_LAUNCH_CHECK();
+    group_pack16_kernel<<<pack_grid, 256, 0, s>>>(a.S, pl.NP, a.gs, kb, a.gflags, A16, B16);
+    APSP_LAUNCH_CHECK();
+    TileProblem q16 = p;
+    q16.kb = kb;
+    q16.gmask = kGfBad | kGfUse16;
+    q16.gwant = kGfUse16;
+    q16.arith16 = 1;
+    q16.ntiles = panels;
+    if ((r = launch_tgemm(kModeFwPanels, false, APSP_I32, pA, pB, mC, q16, s))) return r;
+    group_pack16_kernel<<<pack_grid, 256, 0, s>>>(a.S, pl.NP, a.gs, kb, a.gflags, A16, B16);
+    APSP_LAUNCH_CHECK();
+    q16.ntiles = rest;
+    if ((r = launch_tgemm(kModeFwRest16, true, APSP_I32, pA, pB, mC, q16, s))) return r;
+  }
+  group_certify_kernel<<<row_grid, 256, 0, s>>>(a);
+  APSP_LAUNCH_CHECK();
+  group_verdict_kernel<<<g_grid, 256, 0, s>>>(a, pl.G);
+  APSP_LAUNCH_CHECK();
+
+  // Pass 2: the int32 closure of the graphs that need it (none: every launch returns at once).
+  p.run_if = words + kWRerun;
+  p.gmask = kGfBad | kGfRerun;
+  p.gwant = kGfRerun;
+  p.arith16 = 0;
+  for (int kb = 0; kb < max_nb; ++kb) {
+    int64_t open = 0, panels = 0, rest = 0;
+    for (int k = 0; k < pl.ngroups; ++k) {
+      const int64_t nb = pl.groups[k].nb, c = pl.groups[k].count;
+      if (nb <= kb) continue;
+      open += c;
+      panels += c * 2 * (nb - 1);
+      rest += c * (nb - 1) * (nb - 1);
+    }
+    group_diag_kernel<<<(int)open, 256, 0, s>>>(a.S, pl.NP, a.gs, kb, a.gflags, kGfBad | kGfRerun, kGfRerun,
+                                                words + kWRerun);
+    APSP_LAUNCH_CHECK();
+    p.kb = kb;
+    p.ntiles = panels;
+    if ((r = launch_tgemm(kModeFwPanels, false, APSP_I32, mA, mB, mC, p, s))) return r;
+    p.ntiles = rest;
+    if ((r = launch_tgemm(kModeFwRest, true, APSP_I32, mA, mB, mC, p, s))) return r;
+  }
+  stage_out_kernel<<<row_grid, 256, 0, s>>>(a);
+  APSP_LAUNCH_CHECK();
+  return APSP_OK;
+}
+
+}  // namespace apsp

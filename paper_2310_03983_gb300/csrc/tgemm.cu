@@ -31,11 +31,85 @@ namespace apsp {
 struct TileCoords {
   int a_row, a_col, b_row, b_col, c_row, c_col;
   int m_valid, n_valid, k_len;
+  bool skip;  // grouped FW: this graph does not take part in the launch
 };
+
+// Tile t of a grouped FW launch: find its group and graph (all tiles of one graph are
+// consecutive), then place the single-matrix tile of that graph at the graph's rows.
+template <int MODE>
+__device__ __forceinline__ TileCoords grouped_tile_coords(const TileProblem &p, int64_t t) {
+  TileCoords tc;
+  int64_t rem = t, per = 1, row0 = 0, gnb = 1;
+  int first = 0;
+  bool found = false;
+#pragma unroll
+  for (int k = 0; k < kMaxGroups; ++k) {
+    if (!found && k < p.ngroups) {
+      const int64_t nb = p.groups[k].nb;
+      const int64_t pg = nb <= p.kb ? 0 : (MODE == kModeFwPanels ? 2 * (nb - 1) : (nb - 1) * (nb - 1));
+      const int64_t tot = pg * p.groups[k].count;
+      if (rem < tot) {
+        found = true;
+        per = pg;
+        row0 = p.groups[k].row0;
+        first = p.groups[k].first;
+        gnb = nb;
+      } else {
+        rem -= tot;
+      }
+    }
+  }
+  const int64_t ql = rem / per, lt = rem - ql * per;
+  const int q = first + (int)ql;
+  const int base = (int)(row0 + ql * gnb * kBM);
+  const int64_t nb1 = gnb - 1;
+  const int kb0 = (int)(p.kb * kBM);
+  int i, j;
+  if (MODE == kModeFwPanels) {
+    // 16-bit operands: A = the packed column panel (A16, same rows), B = the packed row panel
+    // (B16, 64 rows per graph); both hold the diagonal tile as well.
+    const int a_col = p.arith16 ? 0 : kb0;
+    const int b_row = p.arith16 ? q * (kBM / 2) : base + kb0;
+    if (lt < nb1) {
+      j = (int)(lt + (lt >= p.kb));
+      tc.a_row = base + kb0; tc.a_col = a_col;
+      tc.b_row = b_row;      tc.b_col = j * kBN;
+      tc.c_row = base + kb0; tc.c_col = j * kBN;
+    } else {
+      i = (int)(lt - nb1);
+      i += (i >= p.kb);
+      tc.a_row = base + i * kBM; tc.a_col = a_col;
+      tc.b_row = b_row;          tc.b_col = kb0;
+      tc.c_row = base + i * kBM; tc.c_col = kb0;
+    }
+  } else {
+    i = (int)(lt / nb1);
+    j = (int)(lt - (int64_t)i * nb1);
+    i += (i >= p.kb);
+    j += (j >= p.kb);
+    tc.a_row = base + i * kBM;
+    tc.c_row = base + i * kBM; tc.c_col = j * kBN;
+    tc.b_col = j * kBN;
+    if (MODE == kModeFwRest16) {
+      tc.a_col = 0;
+      tc.b_row = q * (kBM / 2);
+    } else {
+      tc.a_col = kb0;
+      tc.b_row = base + kb0;
+    }
+  }
+  tc.m_valid = kBM;
+  tc.n_valid = kBN;
+  tc.k_len = (MODE == kModeFwRest16 || p.arith16) ? kBM / 2 : kBM;
+  tc.skip = !found || (p.gflags[q] & p.gmask) != p.gwant;
+  return tc;
+}
 
 template <int MODE>
 __device__ __forceinline__ TileCoords tile_coords(const TileProblem &p, int64_t t) {
+  if (MODE != kModeGemm && p.ngroups > 0) return grouped_tile_coords<MODE>(p, t);
   TileCoords tc;
+  tc.skip = false;
   if (MODE == kModeGemm) {
     // Grouped rasterisation: 8 tile-rows advance together so A slabs are reused from L2.
     const int64_t G = 8;
@@ -120,6 +194,7 @@ __device__ __forceinline__ void consume(const TileProblem &p, const Smem &sm, in
   const T init = AR::from(init_bits);
   for (int64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
     const TileCoords tc = tile_coords<MODE>(p, t);
+    if (tc.skip) continue;  // the producer skips the same tiles
     const int nk = (tc.k_len + kBK - 1) / kBK;
     T acc[8][8];
 #pragma unroll
@@ -141,7 +216,7 @@ __device__ __forceinline__ void consume(const TileProblem &p, const Smem &sm, in
     for (int i = 0; i < 8; ++i)
 #pragma unroll
       for (int j = 0; j < 8; ++j)
-        acc[i][j] = MODE == kModeFwRest16 ? AR::collapse_truncated(acc[i][j]) : AR::collapse(acc[i][j], p.inf_i);
+        acc[i][j] = MODE == kModeGemm ? AR::collapse(acc[i][j], p.inf_i) : AR::collapse_truncated(acc[i][j]);
     if (!AR::kFloat && p.sat) {  // uniform per launch
 #pragma unroll
       for (int i = 0; i < 8; ++i)
@@ -190,7 +265,7 @@ __device__ __forceinline__ void consume(const TileProblem &p, const Smem &sm, in
 template <typename S, int MODE, bool ACC>
 __global__ void __launch_bounds__(kThreads, 1)
     tgemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
-                 const __grid_constant__ CUtensorMap mC, const TileProblem p) {
+                 const __grid_constant__ CUtensorMap mC, const __grid_constant__ TileProblem p) {
   if ((p.skip && *p.skip) || (p.run_if && !*p.run_if)) return;  // uniform, before any barrier exists
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -225,6 +300,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t c_par = 0;
       for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
         const TileCoords tc = tile_coords<MODE>(p, t);
+        if (tc.skip) continue;  // the consumers skip the same tiles
         const int nk = (tc.k_len + kBK - 1) / kBK;
         for (int kt = 0; kt < nk; ++kt) {
           if (!mbar_wait(&empty[stage], phase ^ 1, p.status)) { ok = false; break; }

@@ -30,6 +30,16 @@ enum TileMode : int {
                       // (64 bt words x n), C = the matrix; tiles of the block row/column skipped
 };
 
+// Grouped FW (the batched closure of many graphs in lockstep): graphs staged one below the
+// other in one tall matrix, each padded to nb whole tiles with isolated vertices.  A group
+// holds `count` graphs of the same nb, the first at staged index `first` and row `row0`; graph
+// first + q starts at row row0 + q * nb * 128.  Groups are listed by decreasing nb.
+constexpr int kMaxGroups = 14;
+struct GraphGroup {
+  int64_t row0;
+  int first, count, nb, pad;
+};
+
 struct TileProblem {
   int64_t M, N, K;       // GEMM extents (kModeGemm)
   int64_t tiles_m, tiles_n;
@@ -63,6 +73,15 @@ struct TileProblem {
   int sat;
   // kModeFwRest16: tiles per diagonal block (0 or 1: 128-vertex blocks; 2: 256-vertex blocks).
   int bt;
+  // Grouped FW (modes 1, 2 and 3 with bt = 1; ngroups = 0: one matrix).  The launch visits the
+  // phase's tiles of every graph with nb > kb, group by group; a graph's tiles are skipped
+  // unless (gflags[staged index] & gmask) == gwant.  In mode 3, and in mode 1 with arith16, A
+  // is the packed column panels (the staged rows x 64 words) and B the packed row panels (64
+  // rows per staged graph); results are folded as truncated closures (capped at kCap16).
+  int ngroups;
+  GraphGroup groups[kMaxGroups];
+  const int *gflags;
+  int gmask, gwant;
 };
 
 // 16-bit packing of int32 operands for ArithI16x2 (tgemm.cu).  Entries >= inf (and the padding
