@@ -11,8 +11,8 @@
 // prefix of the staged list.  Per block kb one launch runs a step for every open graph:
 //   phase 1  one CTA per graph closes its diagonal tile (Eq. 1, int32, in registers);
 //   packing  its column and row panels (the diagonal tile included) as 16-bit pairs;
-//   phase 2  the engine's panel mode on the packed panels (two (min,+) pairs per DPX op);
-//   packing  the updated panels;
+//   phase 2  the engine's panel mode on the packed panels (two (min,+) pairs per DPX op),
+//            each tile also writing its result packed, as phase 3's operand;
 //   phase 3  the engine's 16-bit phase 3 over all graphs' remaining tiles.
 // Phases 2 and 3 compute the closure truncated at CAP = 0x3FFF (truncation is a homomorphism
 // of (min,+), so exact and truncated steps may be mixed), certified per graph exactly as
@@ -66,7 +66,7 @@ struct StageArgs {
   const int64_t *offsets;
   const int32_t *ns, *lds;
   const int *sidx;
-  int *gflags, *maxb, *wmaxg, *words;
+  int *gflags, *maxb, *wmaxg, *gsize, *words;
   int inf;
   unsigned int *status;
 };
@@ -184,6 +184,7 @@ __global__ void stage_decide_kernel(const StageArgs a, int64_t G) {
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < G; q += (int64_t)gridDim.x * blockDim.x) {
     if (a.gflags[q] & kGfBad) continue;
     const int w = a.wmaxg[q], n = a.ns[a.sidx[q]];
+    a.gsize[q] = n;
     const int64_t prod = (int64_t)(n - 1) * (int64_t)w;
     atomicMax(a.words + kWBound, (int)(prod < INT_MAX ? prod : INT_MAX));
     if (w <= kCap16 / 4) {
@@ -198,7 +199,7 @@ __global__ void stage_decide_kernel(const StageArgs a, int64_t G) {
 // Phase 1 for every graph with nb > kb (a prefix of the staged list: one CTA each) that the
 // mask admits.  run_if (may be null): every CTA returns at once unless *run_if is set.
 __global__ void __launch_bounds__(256) group_diag_kernel(int *S, int64_t ldS, GroupSet gs, int kb, const int *gflags,
-                                                         int mask, int want, const int *run_if) {
+                                                         const int *gsize, int mask, int want, const int *run_if) {
   if (run_if && !*run_if) return;
   const int q = blockIdx.x;
   if ((gflags[q] & mask) != want) return;
@@ -210,9 +211,11 @@ __global__ void __launch_bounds__(256) group_diag_kernel(int *S, int64_t ldS, Gr
   int *T = S + (base + (int64_t)kb * kBM) * ldS + (int64_t)kb * kBM;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tm = (warp & 3) * 4 + (lane >> 3), tn = (warp >> 2) * 8 + (lane & 7);
+  const int left = gsize[q] - kb * kBM;  // the padding vertices past the graph need no steps
+  const int bk = left < kBM ? (left > 0 ? left : 1) : kBM;
   int r[8][8];
   load_tile_regs(r, T, ldS, kBM, tm, tn);
-  close_tile_regs<false>(r, kBM, tm, tn, buf);
+  close_tile_regs<false>(r, bk, tm, tn, buf);
   store_tile_regs(r, T, ldS, kBM, tm, tn);
 }
 
@@ -320,7 +323,7 @@ __global__ void __launch_bounds__(256) stage_out_kernel(const StageArgs a) {
 }
 
 struct Layout {
-  size_t gflags, maxb, wmaxg, lists, S, A16, B16, total;
+  size_t gflags, maxb, wmaxg, gsize, lists, S, A16, B16, total;
 };
 
 Layout layout_of(const StagePlan &pl, int64_t count) {
@@ -334,6 +337,7 @@ Layout layout_of(const StagePlan &pl, int64_t count) {
   L.gflags = take(pl.G * 4);
   L.maxb = take(pl.G * 4);
   L.wmaxg = take(pl.G * 4);
+  L.gsize = take(pl.G * 4);
   L.lists = take((size_t)count * 4);
   L.S = take((size_t)pl.R * pl.NP * 4);
   L.A16 = take((size_t)pl.R * 64 * 4);
@@ -425,6 +429,7 @@ int batched_staged(const StagePlan &pl, int *pool, const int64_t *offsets, const
   a.gflags = reinterpret_cast<int *>(w + L.gflags);
   a.maxb = reinterpret_cast<int *>(w + L.maxb);
   a.wmaxg = reinterpret_cast<int *>(w + L.wmaxg);
+  a.gsize = reinterpret_cast<int *>(w + L.gsize);
   a.words = words;
   a.inf = inf_i;
   a.status = status_word();
@@ -432,7 +437,7 @@ int batched_staged(const StagePlan &pl, int *pool, const int64_t *offsets, const
   int *B16 = reinterpret_cast<int *>(w + L.B16);
 
   APSP_CUDA_TRY(cudaMemsetAsync(words + kWBound, 0, 4 * sizeof(int), s));
-  APSP_CUDA_TRY(cudaMemsetAsync(w + L.gflags, 0, L.lists - L.gflags, s));  // gflags, maxb, wmaxg
+  APSP_CUDA_TRY(cudaMemsetAsync(w + L.gflags, 0, L.lists - L.gflags, s));  // gflags, maxb, wmaxg, gsize
   std::vector<int> all(pl.staged);
   all.insert(all.end(), pl.rest.begin(), pl.rest.end());
   int r;
@@ -466,6 +471,7 @@ int batched_staged(const StagePlan &pl, int *pool, const int64_t *offsets, const
   p.ngroups = pl.ngroups;
   for (int k = 0; k < pl.ngroups; ++k) p.groups[k] = pl.groups[k];
   p.gflags = a.gflags;
+  p.gsize = a.gsize;
   const int max_nb = pl.groups[0].nb;
 
   // Pass 1: graphs of the 16-bit pass.  Per block: the diagonal tile (exact), the packed
@@ -480,7 +486,8 @@ int batched_staged(const StagePlan &pl, int *pool, const int64_t *offsets, const
       rest += c * (nb - 1) * (nb - 1);
     }
     const dim3 pack_grid((unsigned)open, 4);
-    group_diag_kernel<<<(int)open, 256, 0, s>>>(a.S, pl.NP, a.gs, kb, a.gflags, kGfBad | kGfUse16, kGfUse16, nullptr);
+    group_diag_kernel<<<(int)open, 256, 0, s>>>(a.S, pl.NP, a.gs, kb, a.gflags, a.gsize, kGfBad | kGfUse16, kGfUse16,
+                                                nullptr);
     APSP_LAUNCH_CHECK();
     group_pack16_kernel<<<pack_grid, 256, 0, s>>>(a.S, pl.NP, a.gs, kb, a.gflags, A16, B16);
     APSP_LAUNCH_CHECK();
@@ -490,9 +497,10 @@ int batched_staged(const StagePlan &pl, int *pool, const int64_t *offsets, const
     q16.gwant = kGfUse16;
     q16.arith16 = 1;
     q16.ntiles = panels;
+    q16.pack_a16 = A16;  // the panel tiles leave their results packed for phase 3
+    q16.pack_b16 = B16;
     if ((r = launch_tgemm(kModeFwPanels, false, APSP_I32, pA, pB, mC, q16, s))) return r;
-    group_pack16_kernel<<<pack_grid, 256, 0, s>>>(a.S, pl.NP, a.gs, kb, a.gflags, A16, B16);
-    APSP_LAUNCH_CHECK();
+    q16.pack_a16 = q16.pack_b16 = nullptr;
     q16.ntiles = rest;
     if ((r = launch_tgemm(kModeFwRest16, true, APSP_I32, pA, pB, mC, q16, s))) return r;
   }
@@ -515,8 +523,8 @@ int batched_staged(const StagePlan &pl, int *pool, const int64_t *offsets, const
       panels += c * 2 * (nb - 1);
       rest += c * (nb - 1) * (nb - 1);
     }
-    group_diag_kernel<<<(int)open, 256, 0, s>>>(a.S, pl.NP, a.gs, kb, a.gflags, kGfBad | kGfRerun, kGfRerun,
-                                                words + kWRerun);
+    group_diag_kernel<<<(int)open, 256, 0, s>>>(a.S, pl.NP, a.gs, kb, a.gflags, a.gsize, kGfBad | kGfRerun,
+                                                kGfRerun, words + kWRerun);
     APSP_LAUNCH_CHECK();
     p.kb = kb;
     p.ntiles = panels;

@@ -32,6 +32,7 @@ struct TileCoords {
   int a_row, a_col, b_row, b_col, c_row, c_col;
   int m_valid, n_valid, k_len;
   bool skip;  // grouped FW: this graph does not take part in the launch
+  int pk, pk_row;  // grouped FW panels: 1 column-panel tile, 2 row-panel tile; packed row base
 };
 
 // Tile t of a grouped FW launch: find its group and graph (all tiles of one graph are
@@ -75,14 +76,20 @@ __device__ __forceinline__ TileCoords grouped_tile_coords(const TileProblem &p, 
       tc.a_row = base + kb0; tc.a_col = a_col;
       tc.b_row = b_row;      tc.b_col = j * kBN;
       tc.c_row = base + kb0; tc.c_col = j * kBN;
+      tc.pk = 2;
+      tc.pk_row = q * (kBM / 2);
     } else {
       i = (int)(lt - nb1);
       i += (i >= p.kb);
       tc.a_row = base + i * kBM; tc.a_col = a_col;
       tc.b_row = b_row;          tc.b_col = kb0;
       tc.c_row = base + i * kBM; tc.c_col = kb0;
+      tc.pk = 1;
+      tc.pk_row = tc.c_row;
     }
   } else {
+    tc.pk = 0;
+    tc.pk_row = 0;
     i = (int)(lt / nb1);
     j = (int)(lt - (int64_t)i * nb1);
     i += (i >= p.kb);
@@ -100,8 +107,13 @@ __device__ __forceinline__ TileCoords grouped_tile_coords(const TileProblem &p, 
   }
   tc.m_valid = kBM;
   tc.n_valid = kBN;
-  tc.k_len = (MODE == kModeFwRest16 || p.arith16) ? kBM / 2 : kBM;
   tc.skip = !found || (p.gflags[q] & p.gmask) != p.gwant;
+  int bk = kBM;
+  if (p.gsize && !tc.skip) {
+    const int left = p.gsize[q] - kb0;
+    bk = left < kBM ? (left > 0 ? left : 1) : kBM;
+  }
+  tc.k_len = (MODE == kModeFwRest16 || p.arith16) ? (bk + 1) >> 1 : bk;
   return tc;
 }
 
@@ -110,6 +122,8 @@ __device__ __forceinline__ TileCoords tile_coords(const TileProblem &p, int64_t 
   if (MODE != kModeGemm && p.ngroups > 0) return grouped_tile_coords<MODE>(p, t);
   TileCoords tc;
   tc.skip = false;
+  tc.pk = 0;
+  tc.pk_row = 0;
   if (MODE == kModeGemm) {
     // Grouped rasterisation: 8 tile-rows advance together so A slabs are reused from L2.
     const int64_t G = 8;
@@ -255,6 +269,33 @@ __device__ __forceinline__ void consume(const TileProblem &p, const Smem &sm, in
           for (int q = 0; q < 4; ++q)
             if (cl + q < tc.n_valid) crow[cl + q] = AR::to(acc[i][4 * h + q]);
         }
+      }
+    }
+    if (MODE == kModeFwPanels && !AR::kFloat && p.arith16 && p.pack_a16 && tc.pk) {
+      // Truncated results are at most kCap16: the packed word is hi << 16 | lo.
+      if (tc.pk == 1) {  // column panel: columns 4 tn + 64 h + {0,1} and {2,3} form two words
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+            *reinterpret_cast<int2 *>(p.pack_a16 + (int64_t)(tc.pk_row + tm + 16 * i) * (kBM / 2) + 2 * tn + 32 * h) =
+                make_int2((AR::to(acc[i][4 * h + 1]) << 16) | AR::to(acc[i][4 * h]),
+                          (AR::to(acc[i][4 * h + 3]) << 16) | AR::to(acc[i][4 * h + 2]));
+      } else {  // row panel: rows tm and tm ^ 1 sit in lanes lane and lane ^ 8 of this warp
+        const bool even = ((lane >> 3) & 1) == 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            int o[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) o[q] = __shfl_xor_sync(0xffffffffu, AR::to(acc[i][4 * h + q]), 8);
+            if (even)
+              *reinterpret_cast<int4 *>(p.pack_b16 + (int64_t)(tc.pk_row + (tm + 16 * i) / 2) * p.ldc + tc.c_col +
+                                        4 * tn + 64 * h) =
+                  make_int4((o[0] << 16) | AR::to(acc[i][4 * h]), (o[1] << 16) | AR::to(acc[i][4 * h + 1]),
+                            (o[2] << 16) | AR::to(acc[i][4 * h + 2]), (o[3] << 16) | AR::to(acc[i][4 * h + 3]));
+          }
       }
     }
   }

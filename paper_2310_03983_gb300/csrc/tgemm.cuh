@@ -82,6 +82,15 @@ struct TileProblem {
   GraphGroup groups[kMaxGroups];
   const int *gflags;
   int gmask, gwant;
+  // Grouped mode 1 with arith16 (may be null): each panel tile also writes its result packed,
+  // as the next phase's operand -- a column-panel tile into pack_a16 (64 words per staged
+  // row, pairs of consecutive columns), a row-panel tile into pack_b16 (leading dimension
+  // ldc, 64 rows per staged graph, pairs of consecutive rows).  Each tile overwrites only the
+  // packed operand it has itself finished reading; the diagonal tile's words are not written.
+  int *pack_a16, *pack_b16;
+  // Grouped FW (may be null): vertices of each staged graph; the k range of a graph's last
+  // block stops there (the padding vertices are isolated and add nothing).
+  const int *gsize;
 };
 
 // 16-bit packing of int32 operands for ArithI16x2 (tgemm.cu).  Entries >= inf (and the padding
