@@ -197,8 +197,9 @@ __global__ void stage_decide_kernel(const StageArgs a, int64_t G) {
 }
 
 // Phase 1 for every graph with nb > kb (a prefix of the staged list: one CTA each) that the
-// mask admits.  run_if (may be null): every CTA returns at once unless *run_if is set.
-__global__ void __launch_bounds__(256) group_diag_kernel(int *S, int64_t ldS, GroupSet gs, int kb, const int *gflags,
+// mask admits.  A CTA is latency-bound (128 dependent steps, one barrier each); at 80
+// registers three fit on an SM, which hides more of that latency than two.  run_if (may be null): every CTA returns at once unless *run_if is set.
+__global__ void __launch_bounds__(256, 3) group_diag_kernel(int *S, int64_t ldS, GroupSet gs, int kb, const int *gflags,
                                                          const int *gsize, int mask, int want, const int *run_if) {
   if (run_if && !*run_if) return;
   const int q = blockIdx.x;
@@ -252,9 +253,11 @@ __global__ void __launch_bounds__(256) group_pack16_kernel(const int *S, int64_t
   }
 }
 
-// For graphs of the 16-bit pass: maxb[q] = largest stored value below CAP, every entry at or
-// above CAP becomes the sentinel.  One warp per staged row.
-__global__ void __launch_bounds__(256) group_certify_kernel(const StageArgs a) {
+// For graphs of the 16-bit pass, in one pass over each graph's n x n part: maxb[q] = the
+// largest stored value below CAP; every entry at or above CAP becomes the sentinel; the
+// results go to the caller's pool, and the mapped entries also back into the staging matrix
+// (the int32 pass starts from them if the certificate fails).  One warp per staged row.
+__global__ void __launch_bounds__(256) certify_out_kernel(const StageArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < a.R; r += warps) {
@@ -262,14 +265,20 @@ __global__ void __launch_bounds__(256) group_certify_kernel(const StageArgs a) {
     int64_t base = 0;
     if (!row_graph(a.gs, r, q, base, nb)) continue;
     if ((a.gflags[q] & (kGfBad | kGfUse16)) != kGfUse16) continue;
+    const int g = a.sidx[q];
+    const int n = a.ns[g], ld = a.lds[g];
+    const int i = (int)(r - base);
+    if (i >= n) continue;
     int *row = a.S + r * a.ldS;
+    int *dst = a.pool + a.offsets[g] + (int64_t)i * ld;
     int m = 0;
-    for (int c = lane * 4; c < nb * kBM; c += 128) {
+    for (int c = lane * 4; c < n; c += 128) {
       int4 v = *reinterpret_cast<const int4 *>(row + c);
       bool changed = false;
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int x = (&v.x)[e];
+        if (c + e >= n) continue;
         if (x < kCap16) {
           m = max(m, x);
         } else if (x != a.inf) {
@@ -278,6 +287,13 @@ __global__ void __launch_bounds__(256) group_certify_kernel(const StageArgs a) {
         }
       }
       if (changed) *reinterpret_cast<int4 *>(row + c) = v;
+      if (c + 3 < n) {
+        *reinterpret_cast<int4 *>(dst + c) = v;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (c + e < n) dst[c + e] = (&v.x)[e];
+      }
     }
     m = __reduce_max_sync(0xffffffffu, m);
     if (lane == 0 && m > 0) atomicMax(a.maxb + q, m);
@@ -294,15 +310,17 @@ __global__ void group_verdict_kernel(const StageArgs a, int64_t G) {
   }
 }
 
-// The closed n x n part of every staged graph back into the caller's pool.
+// The closed n x n part of every staged graph of the int32 pass back into the caller's pool
+// (the others went back with the certificate); returns at once when no graph needed the pass.
 __global__ void __launch_bounds__(256) stage_out_kernel(const StageArgs a) {
+  if (!a.words[kWRerun]) return;
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < a.R; r += warps) {
     int q = 0, nb = 0;
     int64_t base = 0;
     if (!row_graph(a.gs, r, q, base, nb)) continue;
-    if (a.gflags[q] & kGfBad) continue;
+    if ((a.gflags[q] & (kGfBad | kGfRerun)) != kGfRerun) continue;
     const int g = a.sidx[q];
     const int n = a.ns[g], ld = a.lds[g];
     const int i = (int)(r - base);
@@ -504,7 +522,7 @@ int batched_staged(const StagePlan &pl, int *pool, const int64_t *offsets, const
     q16.ntiles = rest;
     if ((r = launch_tgemm(kModeFwRest16, true, APSP_I32, pA, pB, mC, q16, s))) return r;
   }
-  group_certify_kernel<<<row_grid, 256, 0, s>>>(a);
+  certify_out_kernel<<<row_grid, 256, 0, s>>>(a);
   APSP_LAUNCH_CHECK();
   group_verdict_kernel<<<g_grid, 256, 0, s>>>(a, pl.G);
   APSP_LAUNCH_CHECK();

@@ -36,35 +36,37 @@ struct TileCoords {
 };
 
 // Tile t of a grouped FW launch: find its group and graph (all tiles of one graph are
-// consecutive), then place the single-matrix tile of that graph at the graph's rows.
+// consecutive), then place the single-matrix tile of that graph at the graph's rows.  Every
+// count here fits 32 bits (the staging keeps at most 2^30 rows, at least 384 per graph), and
+// 32-bit unsigned arithmetic keeps this per-tile work small next to the tile's DPX stream.
 template <int MODE>
 __device__ __forceinline__ TileCoords grouped_tile_coords(const TileProblem &p, int64_t t) {
   TileCoords tc;
-  int64_t rem = t, per = 1, row0 = 0, gnb = 1;
-  int first = 0;
+  unsigned rem = (unsigned)t, per = 1, row0 = 0, gnb = 1, first = 0;
+  const unsigned kb = (unsigned)p.kb;
   bool found = false;
 #pragma unroll
   for (int k = 0; k < kMaxGroups; ++k) {
     if (!found && k < p.ngroups) {
-      const int64_t nb = p.groups[k].nb;
-      const int64_t pg = nb <= p.kb ? 0 : (MODE == kModeFwPanels ? 2 * (nb - 1) : (nb - 1) * (nb - 1));
-      const int64_t tot = pg * p.groups[k].count;
+      const unsigned nb = (unsigned)p.groups[k].nb;
+      const unsigned pg = nb <= kb ? 0u : (MODE == kModeFwPanels ? 2u * (nb - 1) : (nb - 1) * (nb - 1));
+      const unsigned tot = pg * (unsigned)p.groups[k].count;
       if (rem < tot) {
         found = true;
         per = pg;
-        row0 = p.groups[k].row0;
-        first = p.groups[k].first;
+        row0 = (unsigned)p.groups[k].row0;
+        first = (unsigned)p.groups[k].first;
         gnb = nb;
       } else {
         rem -= tot;
       }
     }
   }
-  const int64_t ql = rem / per, lt = rem - ql * per;
-  const int q = first + (int)ql;
+  const unsigned ql = rem / per, lt = rem - ql * per;
+  const int q = (int)(first + ql);
   const int base = (int)(row0 + ql * gnb * kBM);
-  const int64_t nb1 = gnb - 1;
-  const int kb0 = (int)(p.kb * kBM);
+  const unsigned nb1 = gnb - 1;
+  const int kb0 = (int)(kb * kBM);
   int i, j;
   if (MODE == kModeFwPanels) {
     // 16-bit operands: A = the packed column panel (A16, same rows), B = the packed row panel
@@ -72,7 +74,7 @@ __device__ __forceinline__ TileCoords grouped_tile_coords(const TileProblem &p, 
     const int a_col = p.arith16 ? 0 : kb0;
     const int b_row = p.arith16 ? q * (kBM / 2) : base + kb0;
     if (lt < nb1) {
-      j = (int)(lt + (lt >= p.kb));
+      j = (int)(lt + (lt >= kb));
       tc.a_row = base + kb0; tc.a_col = a_col;
       tc.b_row = b_row;      tc.b_col = j * kBN;
       tc.c_row = base + kb0; tc.c_col = j * kBN;
@@ -80,7 +82,7 @@ __device__ __forceinline__ TileCoords grouped_tile_coords(const TileProblem &p, 
       tc.pk_row = q * (kBM / 2);
     } else {
       i = (int)(lt - nb1);
-      i += (i >= p.kb);
+      i += (i >= (int)kb);
       tc.a_row = base + i * kBM; tc.a_col = a_col;
       tc.b_row = b_row;          tc.b_col = kb0;
       tc.c_row = base + i * kBM; tc.c_col = kb0;
@@ -90,10 +92,11 @@ __device__ __forceinline__ TileCoords grouped_tile_coords(const TileProblem &p, 
   } else {
     tc.pk = 0;
     tc.pk_row = 0;
-    i = (int)(lt / nb1);
-    j = (int)(lt - (int64_t)i * nb1);
-    i += (i >= p.kb);
-    j += (j >= p.kb);
+    const unsigned iu = lt / nb1;
+    i = (int)iu;
+    j = (int)(lt - iu * nb1);
+    i += (i >= (int)kb);
+    j += (j >= (int)kb);
     tc.a_row = base + i * kBM;
     tc.c_row = base + i * kBM; tc.c_col = j * kBN;
     tc.b_col = j * kBN;
