@@ -289,6 +289,35 @@ int apsp_mlp_backward(const float *params, int in_dim, const float *x, const flo
 int apsp_mlp_adam(float *params, const float *grads, float *m, float *v, int64_t count, float lr,
                   float beta1, float beta2, float eps, int step, void *stream);
 
+/* ---- host buffers: copy in, close, copy back ------------------------------------------
+ * These calls take HOST memory (pinned for full copy speed; pageable works), run the device
+ * entry points above on `stream`, and return once the results are in the host buffer (they
+ * synchronize; not for CUDA-graph capture).  Status and data errors as for the device calls.
+ *
+ * apsp_solve_host: h_in / h_out are n x n host matrices with leading dimension ld_host (they
+ * may be the same buffer).  algo 0 = apsp_fw (param = tile), 1 = apsp_rkleene (param =
+ * cutoff), 2 = apsp_squaring (param = max_iters).  d: optional device matrix (n x ldd, 16-byte
+ * aligned rows) to work in; NULL takes it from the library's memory pool.  ws / ws_bytes as
+ * for the chosen algorithm.
+ *
+ * apsp_batched_host: h_in / h_out are host pools laid out exactly as the device pool `pool`
+ * (graph g at element offset offsets_host[g], ns_host[g] x ns_host[g], leading dimension
+ * lds_host[g]); offsets / ns / lds are the same descriptors in device memory.  The batch is
+ * split into `chunks` runs of consecutive graphs of about equal work (0 = 4; a layout whose
+ * graph ranges are not in pool order runs as one chunk).  Chunk c is closed by apsp_batched
+ * on `stream` while chunk c + 1 is copied in and chunk c - 1 copied out on two library copy
+ * streams.  ws: apsp_batched_host_workspace_bytes(...) bytes (the staged path's room for the
+ * largest chunk), or NULL for the library pool.  Graph sizes must satisfy ld >= n and
+ * offset >= 0 on the host copies (else APSP_ERR_ARG before any copy). */
+int apsp_solve_host(const void *h_in, void *h_out, int64_t n, int64_t ld_host, int dtype, int algo, int param,
+                    const void *inf, void *d, int64_t ldd, void *ws, size_t ws_bytes, void *stream);
+size_t apsp_batched_host_workspace_bytes(const int32_t *ns_host, const int64_t *offsets_host,
+                                         const int32_t *lds_host, int64_t count, int dtype, int chunks);
+int apsp_batched_host(const void *h_in, void *h_out, void *pool, const int64_t *offsets_host,
+                      const int32_t *ns_host, const int32_t *lds_host, const int64_t *offsets,
+                      const int32_t *ns, const int32_t *lds, int64_t count, int dtype, const void *inf,
+                      int chunks, void *ws, size_t ws_bytes, void *stream);
+
 /* ---- measurement: launch tracing ------------------------------------------------------
  * apsp_trace_enable(1) makes every launch of the tropical GEMM engine (the standalone
  * product and blocked-FW phases 2 and 3) record a CUDA event before and after itself on its

@@ -60,6 +60,9 @@ def _load():
         "apsp_predecessors": ([vp, i64, vp, i64, vp, i64, i64, i32, vp, vp, sz, vp], i32),
         "apsp_batched_workspace_bytes": ([i64], sz),
         "apsp_batched_staged_workspace_bytes": ([vp, i64, i32], sz),
+        "apsp_solve_host": ([vp, vp, i64, i64, i32, i32, i32, vp, vp, i64, vp, sz, vp], i32),
+        "apsp_batched_host_workspace_bytes": ([vp, vp, vp, i64, i32, i32], sz),
+        "apsp_batched_host": ([vp, vp, vp, vp, vp, vp, vp, vp, vp, i64, i32, vp, i32, vp, sz, vp], i32),
         "apsp_batched": ([vp, vp, vp, vp, vp, vp, i64, i32, vp, vp, sz, vp], i32),
         "apsp_mlp_param_count": ([i32], i64),
         "apsp_mlp_backward_workspace_bytes": ([i32, i32], sz),
@@ -85,7 +88,8 @@ EXPORTS = ("apsp_version", "apsp_workspace_pool_trim", "apsp_status_str", "apsp_
            "apsp_fw_workspace_bytes", "apsp_fw", "apsp_rkleene_workspace_bytes", "apsp_rkleene",
            "apsp_fw_signed_workspace_bytes", "apsp_fw_signed", "apsp_squaring_workspace_bytes", "apsp_squaring", "apsp_predecessors_workspace_bytes", "apsp_predecessors",
            "apsp_probe_minplus", "apsp_trace_enable", "apsp_trace_read", "apsp_launch_count",
-           "apsp_batched_workspace_bytes", "apsp_batched_staged_workspace_bytes",
+           "apsp_batched_workspace_bytes", "apsp_batched_staged_workspace_bytes", "apsp_solve_host",
+           "apsp_batched_host_workspace_bytes", "apsp_batched_host",
            "apsp_batched", "apsp_mlp_param_count", "apsp_mlp_backward_workspace_bytes", "apsp_mlp_forward",
            "apsp_mlp_loss", "apsp_mlp_backward", "apsp_mlp_adam")
 
@@ -413,6 +417,27 @@ def apsp_batched(batch: Batch, inf=None, stream=None, pool=None):
     return batch
 
 
+def apsp_batched_host(batch: Batch, host_in=None, host_out=None, chunks: int = 4, inf=None, stream=None):
+    """Close a batch given in HOST memory, laid out like batch.host (the default input): the
+    batch is copied to the device pool chunk by chunk, each chunk closed while the next is
+    copied in and the previous copied out (apsp_batched_host).  Returns the host result
+    (host_out, or a new pinned tensor); the call returns once it is written."""
+    src = batch.host if host_in is None else host_in
+    if src.is_cuda or src.numel() < batch.pool.numel() or not src.is_contiguous():
+        raise ValueError("host_in must be a contiguous CPU tensor laid out like batch.host")
+    out = torch.empty_like(src).pin_memory() if host_out is None else host_out
+    if out.is_cuda or out.numel() < batch.pool.numel() or not out.is_contiguous():
+        raise ValueError("host_out must be a contiguous CPU tensor laid out like batch.host")
+    code = _dtype_code(batch.pool)
+    ip, _keep = _inf_arg(inf, code)
+    vpp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    _check(_lib.apsp_batched_host(src.data_ptr(), out.data_ptr(), batch.pool.data_ptr(), vpp(batch.offsets),
+                                  vpp(batch.ns), vpp(batch.lds), batch.d_offsets.data_ptr(), batch.d_ns.data_ptr(),
+                                  batch.d_lds.data_ptr(), len(batch), code, ip, chunks, batch.ws.data_ptr(),
+                                  batch.ws.numel(), _stream(stream)), "apsp_batched_host")
+    return out
+
+
 def _fptr(t):
     if t is None:
         return None
@@ -462,22 +487,30 @@ def solve(h, algo: str = "fw", inf=None, param: int = 0, device=None, out=None, 
     device, close it there, copy the distances back.  Returns a CPU tensor (``out`` if given,
     pinned memory recommended); with predecessors=True, a pair (distances, pred) where pred is
     the int32 predecessor matrix of apsp_predecessors (walk it with ``path``)."""
-    t = torch.as_tensor(h)
-    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
-    d = t.to(dev, non_blocking=True)
-    w = d.clone() if predecessors else None
-    if algo == "fw":
-        apsp_fw(d, inf=inf, tile=param)
-    elif algo == "rkleene":
-        apsp_rkleene(d, inf=inf, cutoff=param)
-    elif algo == "squaring":
-        apsp_squaring(d, inf=inf, max_iters=param)
-    else:
+    algos = {"fw": 0, "rkleene": 1, "squaring": 2}
+    if algo not in algos:
         raise ValueError(f"unknown algorithm {algo!r}")
-    pred = apsp_predecessors(d, w, inf=inf).cpu() if predecessors else None
+    t = torch.as_tensor(h)
+    if t.is_cuda or t.dim() != 2 or t.shape[0] != t.shape[1]:
+        raise ValueError("h must be a square host matrix")
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    if predecessors:  # the weights stay on the device for the predecessor pass
+        d = t.to(dev, non_blocking=True)
+        w = d.clone()
+        {"fw": lambda: apsp_fw(d, inf=inf, tile=param), "rkleene": lambda: apsp_rkleene(d, inf=inf, cutoff=param),
+         "squaring": lambda: apsp_squaring(d, inf=inf, max_iters=param)}[algo]()
+        pred = apsp_predecessors(d, w, inf=inf).cpu()
+        out = d.cpu() if out is None else out.copy_(d)
+        return out, pred
+    t = t.contiguous()
+    n = t.shape[0]
+    code = _dtype_code(t)
     if out is None:
-        out = d.cpu()
-    else:
-        out.copy_(d, non_blocking=True)
-        torch.cuda.current_stream(dev).synchronize()
-    return (out, pred) if predecessors else out
+        out = torch.empty_like(t)
+    elif out.is_cuda or out.dtype != t.dtype or tuple(out.shape) != (n, n) or not out.is_contiguous():
+        raise ValueError("out must be a contiguous host tensor of h's shape and dtype")
+    ip, _keep = _inf_arg(inf, code)
+    with torch.cuda.device(dev):
+        _check(_lib.apsp_solve_host(t.data_ptr(), out.data_ptr(), n, max(n, 1), code, algos[algo], param, ip, None,
+                                    0, None, 0, _stream(None)), "apsp_solve_host")
+    return out

@@ -405,6 +405,7 @@ bool make_stage_plan(const int32_t *ns_host, int64_t count, StagePlan &pl) {
       const int n = ns_host[g];
       if (n > 0 && (n + kBM - 1) / kBM == nb) {
         pl.staged.push_back(g);
+        pl.sizes.push_back(n);
         staged[g] = 1;
         ++gg.count;
       }
@@ -484,7 +485,6 @@ int batched_staged(const StagePlan &pl, int *pool, const int64_t *offsets, const
   p.status = status_word();
   p.wmax = words + kWBound;  // (n - 1) * largest weight over every staged graph, then 0
   p.wmult = 1;
-  p.no_trace = 1;
   p.bt = 1;
   p.ngroups = pl.ngroups;
   for (int k = 0; k < pl.ngroups; ++k) p.groups[k] = pl.groups[k];
@@ -496,12 +496,18 @@ int batched_staged(const StagePlan &pl, int *pool, const int64_t *offsets, const
   // panels, phase 2 on them (truncated), the panels packed again, phase 3 (truncated).
   for (int kb = 0; kb < max_nb; ++kb) {
     int64_t open = 0, panels = 0, rest = 0;
+    double panel_pairs = 0.0, rest_pairs = 0.0;  // (min,+) pairs by definition, k to each graph's size
     for (int k = 0; k < pl.ngroups; ++k) {
       const int64_t nb = pl.groups[k].nb, c = pl.groups[k].count;
       if (nb <= kb) continue;
       open += c;
       panels += c * 2 * (nb - 1);
       rest += c * (nb - 1) * (nb - 1);
+      for (int64_t g = pl.groups[k].first; g < pl.groups[k].first + c; ++g) {
+        const double bk = (double)std::min<int64_t>(kBM, pl.sizes[g] - (int64_t)kb * kBM);
+        panel_pairs += 2.0 * (nb - 1) * kBM * kBM * bk;
+        rest_pairs += (double)(nb - 1) * (nb - 1) * kBM * kBM * bk;
+      }
     }
     const dim3 pack_grid((unsigned)open, 4);
     group_diag_kernel<<<(int)open, 256, 0, s>>>(a.S, pl.NP, a.gs, kb, a.gflags, a.gsize, kGfBad | kGfUse16, kGfUse16,
@@ -515,11 +521,13 @@ int batched_staged(const StagePlan &pl, int *pool, const int64_t *offsets, const
     q16.gwant = kGfUse16;
     q16.arith16 = 1;
     q16.ntiles = panels;
+    q16.trace_pairs = panel_pairs;
     q16.pack_a16 = A16;  // the panel tiles leave their results packed for phase 3
     q16.pack_b16 = B16;
     if ((r = launch_tgemm(kModeFwPanels, false, APSP_I32, pA, pB, mC, q16, s))) return r;
     q16.pack_a16 = q16.pack_b16 = nullptr;
     q16.ntiles = rest;
+    q16.trace_pairs = rest_pairs;
     if ((r = launch_tgemm(kModeFwRest16, true, APSP_I32, pA, pB, mC, q16, s))) return r;
   }
   certify_out_kernel<<<row_grid, 256, 0, s>>>(a);
@@ -528,6 +536,7 @@ int batched_staged(const StagePlan &pl, int *pool, const int64_t *offsets, const
   APSP_LAUNCH_CHECK();
 
   // Pass 2: the int32 closure of the graphs that need it (none: every launch returns at once).
+  p.no_trace = 1;
   p.run_if = words + kWRerun;
   p.gmask = kGfBad | kGfRerun;
   p.gwant = kGfRerun;

@@ -18,6 +18,7 @@ struct StagePlan {
   int ngroups = 0;
   GraphGroup groups[kMaxGroups] = {};
   std::vector<int> staged;  // graph indices in staged order (groups by decreasing nb)
+  std::vector<int> sizes;   // their host sizes
   std::vector<int> rest;    // every other graph, largest first (for the persistent kernel)
 };
 

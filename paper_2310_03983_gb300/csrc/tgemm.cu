@@ -387,6 +387,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // (min,+) pairs one launch performs by definition (Eq. 2: one add and one min per (i, j, k)).
 template <int MODE> static double algorithmic_pairs(const TileProblem &p) {
+  if (p.trace_pairs > 0) return p.trace_pairs;
   if (MODE == kModeGemm) return (double)p.M * (double)p.N * (double)p.K * (p.arith16 ? 2.0 : 1.0);
   const int64_t w = (MODE == kModeFwRest16 && p.bt > 1 ? p.bt : 1) * kBM;
   const double bk = (double)(p.n - p.kb * w < w ? p.n - p.kb * w : w);

@@ -91,6 +91,9 @@ struct TileProblem {
   // Grouped FW (may be null): vertices of each staged graph; the k range of a graph's last
   // block stops there (the padding vertices are isolated and add nothing).
   const int *gsize;
+  // Host only, for tracing: when > 0, the launch's algorithmic pairs (grouped launches, whose
+  // work the host sums over the graphs of the launch).
+  double trace_pairs;
 };
 
 // 16-bit packing of int32 operands for ArithI16x2 (tgemm.cu).  Entries >= inf (and the padding
