@@ -224,8 +224,8 @@ class Server:
             self._staging[key] = torch.empty((r.n, r.n), dtype=dt).pin_memory()
         return self._staging[key]
 
-    def _launch(self, work, stream, ws):
-        from . import apsp_batched_raw, apsp_fw, apsp_rkleene
+    def _launch(self, work, stream, slot):
+        from . import apsp_batched_raw, apsp_batched_staged_workspace_bytes, apsp_fw, apsp_rkleene
         torch = self.torch
         with torch.cuda.stream(stream):
             stream.wait_stream(self.copy_in)
@@ -234,6 +234,12 @@ class Server:
                 offs = np.array([r.off for r in group], np.int64)
                 ns = np.array([r.n for r in group], np.int32)
                 lds = np.array([r.ld for r in group], np.int32)
+                # room for the staged path (int32 graphs of 257..2048 vertices closed in lockstep
+                # on the GEMM engine); grown per slot, allocated on the slot's own stream
+                need = apsp_batched_staged_workspace_bytes(ns, torch.int32 if work[1] == "int32" else torch.float32)
+                if self.ws[slot].numel() < need:
+                    self.ws[slot] = torch.empty(need + need // 4, dtype=torch.uint8, device=self.dev)
+                ws = self.ws[slot]
                 order = np.argsort(-ns, kind="stable").astype(np.int32)
                 meta = torch.from_numpy(np.concatenate([offs.view(np.int32), ns, lds, order])).pin_memory()
                 dmeta = meta.to(self.dev, non_blocking=True)
@@ -298,7 +304,7 @@ class Server:
                 if work is None:
                     break
                 slot = free_slots.pop()
-                ev, rs, keep = self._launch(work, self.streams[slot], self.ws[slot])
+                ev, rs, keep = self._launch(work, self.streams[slot], slot)
                 inflight.append((ev, rs, keep, slot))
                 launches[work[0]] += 1
                 progressed = True
