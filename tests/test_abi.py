@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -61,3 +63,46 @@ def test_host_side_calls_without_gpu():
     assert h(None, -1, 0, 0, None, 0, None, 0, None) == 1
     assert h(None, 4, 4, 7, None, 0, None, 0, None) == 1
     assert h(None, 0, 0, 0, None, 0, None, 0, None) == 0
+
+
+def _staged_model(ns, count):
+    """The staging plan of apsp_batched, restated: int32 graphs of 3..16 blocks of 128 vertices
+    (the 14 largest block counts present), grouped by block count; workspace = 256 bytes of
+    words, four per-graph int arrays, the index lists of the whole batch, the staging matrix
+    (staged rows x the largest padded size), the packed column panels (staged rows x 64) and
+    the packed row panels (64 rows per staged graph x the largest padded size)."""
+    r256 = lambda b: -(-b // 256) * 256
+    nbs = [-(-n // 128) if n > 0 else 0 for n in ns]
+    present = sorted({nb for nb in nbs if 3 <= nb <= 16}, reverse=True)[:14]
+    if not present:
+        return 256
+    staged = [nb for nb in nbs if nb in present]
+    G, R, NP = len(staged), sum(nb * 128 for nb in staged), present[0] * 128
+    return (256 + 4 * r256(4 * G) + r256(4 * count) + r256(4 * R * NP) + r256(4 * R * 64)
+            + r256(4 * G * 64 * NP))
+
+
+def test_staged_plan_and_chunking_on_the_host():
+    """apsp_batched's staging plan and apsp_batched_host's chunking are host code: their
+    workspace sizes, checked here without a GPU against the plan restated in Python."""
+    lib = ctypes.CDLL(_builder().build())
+    f = lib.apsp_batched_staged_workspace_bytes
+    f.restype, f.argtypes = ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int]
+    h = lib.apsp_batched_host_workspace_bytes
+    h.restype = ctypes.c_size_t
+    h.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int]
+    rng = np.random.default_rng(3)
+    cases = [[300], [256, 128, 5], [2048, 2049, 257, 0, -3], list(rng.integers(1, 1100, 300)),
+             list(rng.integers(200, 2300, 40)), [384 * k for k in range(1, 6)] * 3]
+    for ns in cases:
+        arr = np.asarray(ns, np.int32)
+        ptr = arr.ctypes.data_as(ctypes.c_void_p)
+        assert f(ptr, len(arr), 0) == _staged_model(ns, len(arr)), ns
+        assert f(ptr, len(arr), 1) == 256  # float32 batches are never staged
+        # chunking: consecutive runs of about equal n^3, each run's staged room; the largest
+        lds = ((np.maximum(arr, 1) + 3) // 4 * 4).astype(np.int32)
+        offs = np.concatenate([[0], np.cumsum(np.maximum(arr, 0).astype(np.int64) * lds)[:-1]]).astype(np.int64)
+        one = h(ptr, offs.ctypes.data_as(ctypes.c_void_p), lds.ctypes.data_as(ctypes.c_void_p), len(arr), 0, 1)
+        assert one == f(ptr, len(arr), 0)
+        four = h(ptr, offs.ctypes.data_as(ctypes.c_void_p), lds.ctypes.data_as(ctypes.c_void_p), len(arr), 0, 4)
+        assert 256 <= four <= one
