@@ -208,7 +208,7 @@ int apsp_squaring(void *d, int64_t n, int64_t ld, int dtype, const void *inf, in
 int apsp_rkleene_noalloc(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int cutoff,
                          void *stream);
 
-/* ---- a7: batched closure of many independent graphs in one persistent launch ----------
+/* ---- a7: batched closure of many independent graphs --------------------------------------
  * Closes `count` graphs in place.  Graph g is an ns[g] x ns[g] matrix stored row-major at
  * element offset offsets[g] of `pool` with leading dimension lds[g]; it is closed exactly as
  * apsp_fw would close it (a1 normalisation, then blocked Floyd-Warshall), so results are
@@ -221,7 +221,12 @@ int apsp_rkleene_noalloc(void *d, int64_t n, int64_t ld, int dtype, const void *
  * aligned; every lds[g] and offsets[g] must be a multiple of 4 and lds[g] >= ns[g]: a graph
  * that breaks this, or an order entry outside [0, count), is skipped and sets APSP_ERR_ARG
  * in the device status word (the rest of the batch is still closed).  ns[g] <= 0 is skipped.
- * The workspace holds the work-queue counter (apsp_batched_workspace_bytes). */
+ * The workspace holds the work-queue counter (apsp_batched_workspace_bytes); with the room
+ * reported by apsp_batched_staged_workspace_bytes (and ns_host), the larger int32 graphs are
+ * closed in lockstep on the tropical-GEMM engine instead (below), the others by the persistent
+ * launch in the library's own largest-first order (`order` is then not used).  Either way
+ * the call is asynchronous, allocates nothing when ws is given, and can be captured in a CUDA
+ * graph. */
 size_t apsp_batched_workspace_bytes(int64_t count);
 /* Workspace with which apsp_batched closes the larger graphs of an int32 batch in lockstep
  * on the tropical-GEMM engine instead of one per CTA (same results).  ns_host: host copy of
