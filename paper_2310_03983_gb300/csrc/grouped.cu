@@ -196,11 +196,82 @@ __global__ void stage_decide_kernel(const StageArgs a, int64_t G) {
   }
 }
 
+// Phase 1 of the truncated pass on packed 16-bit pairs.  The thread owning rows tm + 16 i and
+// columns 4 tn + 64 h + q (the layout of diag.cuh) keeps w[i][2 h + p] = {d[i][4 tn + 64 h +
+// 2 p], d[i][... + 1]}, values capped at CAP.  Step k: the owner of row k publishes its four
+// words (the row, packed), the owners of column k publish d[i][k] in both lanes; then one DPX
+// add-min per word relaxes two entries: w = min(w, {c, c} + {r0, r1}).
+template <int KH>
+__device__ __forceinline__ void put_row16(const int (&w)[8][4], int *rb, int tn) {
+  *reinterpret_cast<int2 *>(rb + 2 * tn) = make_int2(w[KH][0], w[KH][1]);
+  *reinterpret_cast<int2 *>(rb + 2 * tn + 32) = make_int2(w[KH][2], w[KH][3]);
+}
+
+template <int WJ, int HI>
+__device__ __forceinline__ void put_col16(const int (&w)[8][4], int *cb, int tm) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int v = HI ? (int)((unsigned)w[i][WJ] >> 16) : (w[i][WJ] & 0xFFFF);
+    cb[tm + 16 * i] = (v << 16) | v;
+  }
+}
+
+__device__ void close_tile_regs16(int (&w)[8][4], int bk, int tm, int tn, int *buf) {
+#pragma unroll
+  for (int kh = 0; kh < 8; ++kh) {
+    if (16 * kh >= bk) break;
+    for (int kl = 0; kl < 16; ++kl) {
+      const int k = 16 * kh + kl;
+      if (k >= bk) break;
+      int *rb = buf + (k & 1) * 256;
+      int *cb = rb + 128;
+      if (tm == kl) {
+        switch (kh) {
+          case 0: put_row16<0>(w, rb, tn); break;
+          case 1: put_row16<1>(w, rb, tn); break;
+          case 2: put_row16<2>(w, rb, tn); break;
+          case 3: put_row16<3>(w, rb, tn); break;
+          case 4: put_row16<4>(w, rb, tn); break;
+          case 5: put_row16<5>(w, rb, tn); break;
+          case 6: put_row16<6>(w, rb, tn); break;
+          default: put_row16<7>(w, rb, tn); break;
+        }
+      }
+      if (tn == ((k >> 2) & 15)) {  // column k = 4 tn + q + 64 h: word 2 h + q / 2, lane q % 2
+        switch (2 * (k >> 6) + ((k >> 1) & 1) + 4 * (k & 1)) {
+          case 0: put_col16<0, 0>(w, cb, tm); break;
+          case 1: put_col16<1, 0>(w, cb, tm); break;
+          case 2: put_col16<2, 0>(w, cb, tm); break;
+          case 3: put_col16<3, 0>(w, cb, tm); break;
+          case 4: put_col16<0, 1>(w, cb, tm); break;
+          case 5: put_col16<1, 1>(w, cb, tm); break;
+          case 6: put_col16<2, 1>(w, cb, tm); break;
+          default: put_col16<3, 1>(w, cb, tm); break;
+        }
+      }
+      __syncthreads();
+      int c[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) c[i] = cb[tm + 16 * i];
+      const int2 r0 = *reinterpret_cast<const int2 *>(rb + 2 * tn);
+      const int2 r1 = *reinterpret_cast<const int2 *>(rb + 2 * tn + 32);
+      const int r[4] = {r0.x, r0.y, r1.x, r1.y};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          w[i][j] = (int)__viaddmin_s16x2((unsigned)c[i], (unsigned)r[j], (unsigned)w[i][j]);
+    }
+  }
+  __syncthreads();  // buf is reused by the caller
+}
+
 // Phase 1 for every graph with nb > kb (a prefix of the staged list: one CTA each) that the
 // mask admits.  A CTA is latency-bound (128 dependent steps, one barrier each); at 80
 // registers three fit on an SM, which hides more of that latency than two.  run_if (may be null): every CTA returns at once unless *run_if is set.
 __global__ void __launch_bounds__(256, 3) group_diag_kernel(int *S, int64_t ldS, GroupSet gs, int kb, const int *gflags,
-                                                         const int *gsize, int mask, int want, const int *run_if) {
+                                                         const int *gsize, int mask, int want, const int *run_if,
+                                                         bool truncated) {
   if (run_if && !*run_if) return;
   const int q = blockIdx.x;
   if ((gflags[q] & mask) != want) return;
@@ -216,7 +287,23 @@ __global__ void __launch_bounds__(256, 3) group_diag_kernel(int *S, int64_t ldS,
   const int bk = left < kBM ? (left > 0 ? left : 1) : kBM;
   int r[8][8];
   load_tile_regs(r, T, ldS, kBM, tm, tn);
-  close_tile_regs<false>(r, bk, tm, tn, buf);
+  if (truncated) {  // the 16-bit pass: packed pairs, values capped at CAP
+    int w[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) w[i][j] = (min(r[i][2 * j + 1], kCap16) << 16) | min(r[i][2 * j], kCap16);
+    close_tile_regs16(w, bk, tm, tn, buf);
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        r[i][2 * j] = w[i][j] & 0xFFFF;
+        r[i][2 * j + 1] = (int)((unsigned)w[i][j] >> 16);
+      }
+  } else {
+    close_tile_regs<false>(r, bk, tm, tn, buf);
+  }
   store_tile_regs(r, T, ldS, kBM, tm, tn);
 }
 
@@ -511,7 +598,7 @@ int batched_staged(const StagePlan &pl, int *pool, const int64_t *offsets, const
     }
     const dim3 pack_grid((unsigned)open, 4);
     group_diag_kernel<<<(int)open, 256, 0, s>>>(a.S, pl.NP, a.gs, kb, a.gflags, a.gsize, kGfBad | kGfUse16, kGfUse16,
-                                                nullptr);
+                                                nullptr, true);
     APSP_LAUNCH_CHECK();
     group_pack16_kernel<<<pack_grid, 256, 0, s>>>(a.S, pl.NP, a.gs, kb, a.gflags, A16, B16);
     APSP_LAUNCH_CHECK();
@@ -551,7 +638,7 @@ int batched_staged(const StagePlan &pl, int *pool, const int64_t *offsets, const
       rest += c * (nb - 1) * (nb - 1);
     }
     group_diag_kernel<<<(int)open, 256, 0, s>>>(a.S, pl.NP, a.gs, kb, a.gflags, a.gsize, kGfBad | kGfRerun,
-                                                kGfRerun, words + kWRerun);
+                                                kGfRerun, words + kWRerun, false);
     APSP_LAUNCH_CHECK();
     p.kb = kb;
     p.ntiles = panels;
