@@ -9,13 +9,14 @@
 // diagonal, the sentinel elsewhere; they change no distance).  Graphs are grouped by nb, and
 // the groups are listed by decreasing nb, so the graphs still open at block kb (nb > kb) are a
 // prefix of the staged list.  Per block kb one launch runs a step for every open graph:
-//   phase 1  one CTA per graph closes its diagonal tile (Eq. 1, int32, in registers);
+//   phase 1  one CTA per graph closes its diagonal tile (Eq. 1, in registers, on packed
+//            16-bit pairs: two entries per DPX add-min);
 //   packing  its column and row panels (the diagonal tile included) as 16-bit pairs;
 //   phase 2  the engine's panel mode on the packed panels (two (min,+) pairs per DPX op),
 //            each tile also writing its result packed, as phase 3's operand;
 //   phase 3  the engine's 16-bit phase 3 over all graphs' remaining tiles.
-// Phases 2 and 3 compute the closure truncated at CAP = 0x3FFF (truncation is a homomorphism
-// of (min,+), so exact and truncated steps may be mixed), certified per graph exactly as
+// All three compute the closure truncated at CAP = 0x3FFF (truncation is a homomorphism of
+// (min,+), so exact and truncated steps could even be mixed), certified per graph exactly as
 // apsp_fw certifies one matrix: the largest stored value below CAP plus the graph's largest
 // weight must stay below CAP; then every entry at or above CAP is unreachable.
 // Graphs whose certificate fails, and graphs whose weights exceed CAP / 4, are finished by a
