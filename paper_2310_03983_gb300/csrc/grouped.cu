@@ -11,10 +11,12 @@
 // prefix of the staged list.  Per block kb one launch runs a step for every open graph:
 //   phase 1  one CTA per graph closes its diagonal tile (Eq. 1, in registers, on packed
 //            16-bit pairs: two entries per DPX add-min);
-//   packing  its column and row panels (the diagonal tile included) as 16-bit pairs;
 //   phase 2  the engine's panel mode on the packed panels (two (min,+) pairs per DPX op),
 //            each tile also writing its result packed, as phase 3's operand;
 //   phase 3  the engine's 16-bit phase 3 over all graphs' remaining tiles.
+// The packed panels a step reads are written, already packed, by the kernels that produce the
+// values: the diagonal kernel for its tile, and the previous step's phase-2 and phase-3 tiles
+// of block row and column kb (two alternating buffer sets); only step 0 packs them in a pass.
 // All three compute the closure truncated at CAP = 0x3FFF (truncation is a homomorphism of
 // (min,+), so exact and truncated steps could even be mixed), certified per graph exactly as
 // apsp_fw certifies one matrix: the largest stored value below CAP plus the graph's largest
@@ -268,11 +270,12 @@ __device__ void close_tile_regs16(int (&w)[8][4], int bk, int tm, int tn, int *b
 }
 
 // Phase 1 for every graph with nb > kb (a prefix of the staged list: one CTA each) that the
-// mask admits.  A CTA is latency-bound (128 dependent steps, one barrier each); at 80
-// registers three fit on an SM, which hides more of that latency than two.  run_if (may be null): every CTA returns at once unless *run_if is set.
-__global__ void __launch_bounds__(256, 3) group_diag_kernel(int *S, int64_t ldS, GroupSet gs, int kb, const int *gflags,
+// mask admits.  run_if (may be null): every CTA returns at once unless *run_if is set.  With
+// truncated (the 16-bit pass), the tile is closed on packed 16-bit pairs and its part of the
+// step's packed column and row panels is written to pa / pb.
+__global__ void __launch_bounds__(256, 2) group_diag_kernel(int *S, int64_t ldS, GroupSet gs, int kb, const int *gflags,
                                                          const int *gsize, int mask, int want, const int *run_if,
-                                                         bool truncated) {
+                                                         bool truncated, int *pa, int *pb) {
   if (run_if && !*run_if) return;
   const int q = blockIdx.x;
   if ((gflags[q] & mask) != want) return;
@@ -306,6 +309,10 @@ __global__ void __launch_bounds__(256, 3) group_diag_kernel(int *S, int64_t ldS,
     close_tile_regs<false>(r, bk, tm, tn, buf);
   }
   store_tile_regs(r, T, ldS, kBM, tm, tn);
+  if (pa) {  // the closed tile's part of this step's packed column and row panels
+    store_col_pairs16(r, tm, tn, pa + (base + (int64_t)kb * kBM) * 64);
+    store_row_pairs16(r, tm, tn, lane, pb + (int64_t)q * 64 * ldS + (int64_t)kb * kBM, ldS);
+  }
 }
 
 // Packs, for graph blockIdx.x of the 16-bit pass (open at block kb), its column panel (its
@@ -429,7 +436,7 @@ __global__ void __launch_bounds__(256) stage_out_kernel(const StageArgs a) {
 }
 
 struct Layout {
-  size_t gflags, maxb, wmaxg, gsize, lists, S, A16, B16, total;
+  size_t gflags, maxb, wmaxg, gsize, lists, S, A16[2], B16[2], total;
 };
 
 Layout layout_of(const StagePlan &pl, int64_t count) {
@@ -446,8 +453,10 @@ Layout layout_of(const StagePlan &pl, int64_t count) {
   L.gsize = take(pl.G * 4);
   L.lists = take((size_t)count * 4);
   L.S = take((size_t)pl.R * pl.NP * 4);
-  L.A16 = take((size_t)pl.R * 64 * 4);
-  L.B16 = take((size_t)pl.G * 64 * pl.NP * 4);
+  for (int k = 0; k < 2; ++k) {  // two sets: block step kb reads set kb & 1, writes the other
+    L.A16[k] = take((size_t)pl.R * 64 * 4);
+    L.B16[k] = take((size_t)pl.G * 64 * pl.NP * 4);
+  }
   L.total = o;
   return L;
 }
@@ -540,8 +549,8 @@ int batched_staged(const StagePlan &pl, int *pool, const int64_t *offsets, const
   a.words = words;
   a.inf = inf_i;
   a.status = status_word();
-  int *A16 = reinterpret_cast<int *>(w + L.A16);
-  int *B16 = reinterpret_cast<int *>(w + L.B16);
+  int *A16[2] = {reinterpret_cast<int *>(w + L.A16[0]), reinterpret_cast<int *>(w + L.A16[1])};
+  int *B16[2] = {reinterpret_cast<int *>(w + L.B16[0]), reinterpret_cast<int *>(w + L.B16[1])};
 
   APSP_CUDA_TRY(cudaMemsetAsync(words + kWBound, 0, 4 * sizeof(int), s));
   APSP_CUDA_TRY(cudaMemsetAsync(w + L.gflags, 0, L.lists - L.gflags, s));  // gflags, maxb, wmaxg, gsize
@@ -561,10 +570,12 @@ int batched_staged(const StagePlan &pl, int *pool, const int64_t *offsets, const
   stage_decide_kernel<<<g_grid, 256, 0, s>>>(a, pl.G);
   APSP_LAUNCH_CHECK();
 
-  CUtensorMap mA, mB, mC, pA, pB;
+  CUtensorMap mA, mB, mC, pA[2], pB[2];
   if ((r = make_operand_maps(a.S, pl.R, pl.NP, pl.NP, APSP_I32, &mA, &mB, &mC))) return r;
-  if ((r = make_operand_maps(A16, pl.R, 64, 64, APSP_I32, &pA, nullptr, nullptr))) return r;
-  if ((r = make_operand_maps(B16, pl.G * 64, pl.NP, pl.NP, APSP_I32, nullptr, &pB, nullptr))) return r;
+  for (int k = 0; k < 2; ++k) {
+    if ((r = make_operand_maps(A16[k], pl.R, 64, 64, APSP_I32, &pA[k], nullptr, nullptr))) return r;
+    if ((r = make_operand_maps(B16[k], pl.G * 64, pl.NP, pl.NP, APSP_I32, nullptr, &pB[k], nullptr))) return r;
+  }
 
   TileProblem p = {};
   p.C = a.S;
@@ -597,12 +608,17 @@ int batched_staged(const StagePlan &pl, int *pool, const int64_t *offsets, const
         rest_pairs += (double)(nb - 1) * (nb - 1) * kBM * kBM * bk;
       }
     }
-    const dim3 pack_grid((unsigned)open, 4);
+    // The packed panels of step kb (set kb & 1): the diagonal kernel writes its tile's part; the
+    // rest came from step kb - 1 (its phase-2 and phase-3 tiles of block row / column kb),
+    // except at kb = 0, where one packing pass writes them.
+    const int cur = kb & 1;
     group_diag_kernel<<<(int)open, 256, 0, s>>>(a.S, pl.NP, a.gs, kb, a.gflags, a.gsize, kGfBad | kGfUse16, kGfUse16,
-                                                nullptr, true);
+                                                nullptr, true, A16[cur], B16[cur]);
     APSP_LAUNCH_CHECK();
-    group_pack16_kernel<<<pack_grid, 256, 0, s>>>(a.S, pl.NP, a.gs, kb, a.gflags, A16, B16);
-    APSP_LAUNCH_CHECK();
+    if (kb == 0) {
+      group_pack16_kernel<<<dim3((unsigned)open, 4), 256, 0, s>>>(a.S, pl.NP, a.gs, kb, a.gflags, A16[0], B16[0]);
+      APSP_LAUNCH_CHECK();
+    }
     TileProblem q16 = p;
     q16.kb = kb;
     q16.gmask = kGfBad | kGfUse16;
@@ -610,13 +626,14 @@ int batched_staged(const StagePlan &pl, int *pool, const int64_t *offsets, const
     q16.arith16 = 1;
     q16.ntiles = panels;
     q16.trace_pairs = panel_pairs;
-    q16.pack_a16 = A16;  // the panel tiles leave their results packed for phase 3
-    q16.pack_b16 = B16;
-    if ((r = launch_tgemm(kModeFwPanels, false, APSP_I32, pA, pB, mC, q16, s))) return r;
-    q16.pack_a16 = q16.pack_b16 = nullptr;
+    q16.pk_a[0] = A16[0];  // the tiles leave their results packed: phase 3's operands and the
+    q16.pk_a[1] = A16[1];  // next step's panels
+    q16.pk_b[0] = B16[0];
+    q16.pk_b[1] = B16[1];
+    if ((r = launch_tgemm(kModeFwPanels, false, APSP_I32, pA[cur], pB[cur], mC, q16, s))) return r;
     q16.ntiles = rest;
     q16.trace_pairs = rest_pairs;
-    if ((r = launch_tgemm(kModeFwRest16, true, APSP_I32, pA, pB, mC, q16, s))) return r;
+    if ((r = launch_tgemm(kModeFwRest16, true, APSP_I32, pA[cur], pB[cur], mC, q16, s))) return r;
   }
   certify_out_kernel<<<row_grid, 256, 0, s>>>(a);
   APSP_LAUNCH_CHECK();
@@ -639,7 +656,7 @@ int batched_staged(const StagePlan &pl, int *pool, const int64_t *offsets, const
       rest += c * (nb - 1) * (nb - 1);
     }
     group_diag_kernel<<<(int)open, 256, 0, s>>>(a.S, pl.NP, a.gs, kb, a.gflags, a.gsize, kGfBad | kGfRerun,
-                                                kGfRerun, words + kWRerun, false);
+                                                kGfRerun, words + kWRerun, false, nullptr, nullptr);
     APSP_LAUNCH_CHECK();
     p.kb = kb;
     p.ntiles = panels;

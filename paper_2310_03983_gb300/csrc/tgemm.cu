@@ -32,7 +32,10 @@ struct TileCoords {
   int a_row, a_col, b_row, b_col, c_row, c_col;
   int m_valid, n_valid, k_len;
   bool skip;  // grouped FW: this graph does not take part in the launch
-  int pk, pk_row;  // grouped FW panels: 1 column-panel tile, 2 row-panel tile; packed row base
+  // Grouped 16-bit launches: packed copies of the result -- column pairs into set pa_set of
+  // the packed column panels (at the tile's rows), row pairs into set pb_set of the packed row
+  // panels (rows pb_row.., the tile's columns); -1: none.
+  int pa_set, pb_set, pb_row;
 };
 
 // Tile t of a grouped FW launch: find its group and graph (all tiles of one graph are
@@ -73,25 +76,25 @@ __device__ __forceinline__ TileCoords grouped_tile_coords(const TileProblem &p, 
     // (B16, 64 rows per graph); both hold the diagonal tile as well.
     const int a_col = p.arith16 ? 0 : kb0;
     const int b_row = p.arith16 ? q * (kBM / 2) : base + kb0;
-    if (lt < nb1) {
+    const int cur = (int)(kb & 1), nxt = cur ^ 1;
+    tc.pb_row = q * (kBM / 2);
+    if (lt < nb1) {  // row panel (kb, j): phase 3's row operand; column kb + 1: the next column panel
       j = (int)(lt + (lt >= kb));
       tc.a_row = base + kb0; tc.a_col = a_col;
       tc.b_row = b_row;      tc.b_col = j * kBN;
       tc.c_row = base + kb0; tc.c_col = j * kBN;
-      tc.pk = 2;
-      tc.pk_row = q * (kBM / 2);
-    } else {
+      tc.pb_set = cur;
+      tc.pa_set = j == (int)kb + 1 ? nxt : -1;
+    } else {         // column panel (i, kb): phase 3's column operand; row kb + 1: the next row panel
       i = (int)(lt - nb1);
       i += (i >= (int)kb);
       tc.a_row = base + i * kBM; tc.a_col = a_col;
       tc.b_row = b_row;          tc.b_col = kb0;
       tc.c_row = base + i * kBM; tc.c_col = kb0;
-      tc.pk = 1;
-      tc.pk_row = tc.c_row;
+      tc.pa_set = cur;
+      tc.pb_set = i == (int)kb + 1 ? nxt : -1;
     }
   } else {
-    tc.pk = 0;
-    tc.pk_row = 0;
     const unsigned iu = lt / nb1;
     i = (int)iu;
     j = (int)(lt - iu * nb1);
@@ -100,9 +103,15 @@ __device__ __forceinline__ TileCoords grouped_tile_coords(const TileProblem &p, 
     tc.a_row = base + i * kBM;
     tc.c_row = base + i * kBM; tc.c_col = j * kBN;
     tc.b_col = j * kBN;
+    tc.pa_set = tc.pb_set = -1;
+    tc.pb_row = q * (kBM / 2);
     if (MODE == kModeFwRest16) {
       tc.a_col = 0;
       tc.b_row = q * (kBM / 2);
+      // tiles of block row / column kb + 1 (not its diagonal tile) are the next step's panels
+      const int nxt = (int)((kb + 1) & 1);
+      if (i == (int)kb + 1 && j != (int)kb + 1) tc.pb_set = nxt;
+      if (j == (int)kb + 1 && i != (int)kb + 1) tc.pa_set = nxt;
     } else {
       tc.a_col = kb0;
       tc.b_row = base + kb0;
@@ -125,8 +134,8 @@ __device__ __forceinline__ TileCoords tile_coords(const TileProblem &p, int64_t 
   if (MODE != kModeGemm && p.ngroups > 0) return grouped_tile_coords<MODE>(p, t);
   TileCoords tc;
   tc.skip = false;
-  tc.pk = 0;
-  tc.pk_row = 0;
+  tc.pa_set = tc.pb_set = -1;
+  tc.pb_row = 0;
   if (MODE == kModeGemm) {
     // Grouped rasterisation: 8 tile-rows advance together so A slabs are reused from L2.
     const int64_t G = 8;
@@ -274,32 +283,16 @@ __device__ __forceinline__ void consume(const TileProblem &p, const Smem &sm, in
         }
       }
     }
-    if (MODE == kModeFwPanels && !AR::kFloat && p.arith16 && p.pack_a16 && tc.pk) {
-      // Truncated results are at most kCap16: the packed word is hi << 16 | lo.
-      if (tc.pk == 1) {  // column panel: columns 4 tn + 64 h + {0,1} and {2,3} form two words
+    if (MODE != kModeGemm && !AR::kFloat && p.arith16 && p.pk_a[0] && (tc.pa_set >= 0 || tc.pb_set >= 0)) {
+      int v[8][8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
+      for (int i = 0; i < 8; ++i)
 #pragma unroll
-          for (int h = 0; h < 2; ++h)
-            *reinterpret_cast<int2 *>(p.pack_a16 + (int64_t)(tc.pk_row + tm + 16 * i) * (kBM / 2) + 2 * tn + 32 * h) =
-                make_int2((AR::to(acc[i][4 * h + 1]) << 16) | AR::to(acc[i][4 * h]),
-                          (AR::to(acc[i][4 * h + 3]) << 16) | AR::to(acc[i][4 * h + 2]));
-      } else {  // row panel: rows tm and tm ^ 1 sit in lanes lane and lane ^ 8 of this warp
-        const bool even = ((lane >> 3) & 1) == 0;
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            int o[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) o[q] = __shfl_xor_sync(0xffffffffu, AR::to(acc[i][4 * h + q]), 8);
-            if (even)
-              *reinterpret_cast<int4 *>(p.pack_b16 + (int64_t)(tc.pk_row + (tm + 16 * i) / 2) * p.ldc + tc.c_col +
-                                        4 * tn + 64 * h) =
-                  make_int4((o[0] << 16) | AR::to(acc[i][4 * h]), (o[1] << 16) | AR::to(acc[i][4 * h + 1]),
-                            (o[2] << 16) | AR::to(acc[i][4 * h + 2]), (o[3] << 16) | AR::to(acc[i][4 * h + 3]));
-          }
-      }
+        for (int j = 0; j < 8; ++j) v[i][j] = AR::to(acc[i][j]);
+      if (tc.pa_set >= 0) store_col_pairs16(v, tm, tn, (tc.pa_set ? p.pk_a[1] : p.pk_a[0]) + (int64_t)tc.c_row * 64);
+      if (tc.pb_set >= 0)
+        store_row_pairs16(v, tm, tn, lane, (tc.pb_set ? p.pk_b[1] : p.pk_b[0]) + (int64_t)tc.pb_row * p.ldc + tc.c_col,
+                          p.ldc);
     }
   }
 }

@@ -82,12 +82,13 @@ struct TileProblem {
   GraphGroup groups[kMaxGroups];
   const int *gflags;
   int gmask, gwant;
-  // Grouped mode 1 with arith16 (may be null): each panel tile also writes its result packed,
-  // as the next phase's operand -- a column-panel tile into pack_a16 (64 words per staged
-  // row, pairs of consecutive columns), a row-panel tile into pack_b16 (leading dimension
-  // ldc, 64 rows per staged graph, pairs of consecutive rows).  Each tile overwrites only the
-  // packed operand it has itself finished reading; the diagonal tile's words are not written.
-  int *pack_a16, *pack_b16;
+  // Grouped 16-bit launches (may be null): packed outputs.  Set s of the packed operands is
+  // pk_a[s] (64 words per staged row, pairs of consecutive columns, capped at kCap16) and
+  // pk_b[s] (leading dimension ldc, 64 rows per staged graph, pairs of consecutive rows); block
+  // step kb reads set kb & 1.  A panel tile (mode 1) writes its result into set kb & 1 as phase
+  // 3's operand (over the packed words it has itself finished reading); a tile in block row or
+  // column kb + 1 (modes 1 and 3) writes it into set (kb + 1) & 1 as the next step's operand.
+  int *pk_a[2], *pk_b[2];
   // Grouped FW (may be null): vertices of each staged graph; the k range of a graph's last
   // block stops there (the padding vertices are isolated and add nothing).
   const int *gsize;
@@ -95,6 +96,39 @@ struct TileProblem {
   // work the host sums over the graphs of the launch).
   double trace_pairs;
 };
+
+// Packed 16-bit copies of a 128 x 128 tile held in the engine's register layout (thread (tm, tn)
+// holds rows tm + 16 i and columns 4 tn + 64 h + q), values capped at kCap16.  Column pairs:
+// word {v[r][2w], v[r][2w + 1]} at a + r * 64 + w.  Row pairs: word {v[2r][c], v[2r + 1][c]} at
+// b + r * ldb + c; rows tm and tm ^ 1 sit in lanes lane and lane ^ 8, so every lane of the warp
+// must call it.
+__device__ __forceinline__ int pack_pair16(int lo, int hi) { return (min(hi, kCap16) << 16) | min(lo, kCap16); }
+
+__device__ __forceinline__ void store_col_pairs16(const int (&v)[8][8], int tm, int tn, int *a) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      *reinterpret_cast<int2 *>(a + (int64_t)(tm + 16 * i) * 64 + 2 * tn + 32 * h) =
+          make_int2(pack_pair16(v[i][4 * h], v[i][4 * h + 1]), pack_pair16(v[i][4 * h + 2], v[i][4 * h + 3]));
+}
+
+__device__ __forceinline__ void store_row_pairs16(const int (&v)[8][8], int tm, int tn, int lane, int *b,
+                                                  int64_t ldb) {
+  const bool even = ((lane >> 3) & 1) == 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      int o[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) o[q] = __shfl_xor_sync(0xffffffffu, v[i][4 * h + q], 8);
+      if (even)
+        *reinterpret_cast<int4 *>(b + (int64_t)((tm + 16 * i) >> 1) * ldb + 4 * tn + 64 * h) =
+            make_int4(pack_pair16(v[i][4 * h], o[0]), pack_pair16(v[i][4 * h + 1], o[1]),
+                      pack_pair16(v[i][4 * h + 2], o[2]), pack_pair16(v[i][4 * h + 3], o[3]));
+    }
+}
 
 // 16-bit packing of int32 operands for ArithI16x2 (tgemm.cu).  Entries >= inf (and the padding
 // past K) become kCap16.  They run only when words[0] + words[1] < kCap16 (the largest finite

@@ -69,8 +69,8 @@ def _staged_model(ns, count):
     """The staging plan of apsp_batched, restated: int32 graphs of 3..16 blocks of 128 vertices
     (the 14 largest block counts present), grouped by block count; workspace = 256 bytes of
     words, four per-graph int arrays, the index lists of the whole batch, the staging matrix
-    (staged rows x the largest padded size), the packed column panels (staged rows x 64) and
-    the packed row panels (64 rows per staged graph x the largest padded size)."""
+    (staged rows x the largest padded size), and two sets of the packed column panels (staged
+    rows x 64) and packed row panels (64 rows per staged graph x the largest padded size)."""
     r256 = lambda b: -(-b // 256) * 256
     nbs = [-(-n // 128) if n > 0 else 0 for n in ns]
     present = sorted({nb for nb in nbs if 3 <= nb <= 16}, reverse=True)[:14]
@@ -78,8 +78,8 @@ def _staged_model(ns, count):
         return 256
     staged = [nb for nb in nbs if nb in present]
     G, R, NP = len(staged), sum(nb * 128 for nb in staged), present[0] * 128
-    return (256 + 4 * r256(4 * G) + r256(4 * count) + r256(4 * R * NP) + r256(4 * R * 64)
-            + r256(4 * G * 64 * NP))
+    return (256 + 4 * r256(4 * G) + r256(4 * count) + r256(4 * R * NP)
+            + 2 * (r256(4 * R * 64) + r256(4 * G * 64 * NP)))
 
 
 def test_staged_plan_and_chunking_on_the_host():
