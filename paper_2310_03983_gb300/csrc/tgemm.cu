@@ -21,6 +21,7 @@
 // No tensor cores: (min,+) is not a multiply-accumulate.  int32 results are exact; fp32
 // results are bitwise deterministic (min is exact, each candidate sum is one rounding).
 #include <math.h>
+#include <type_traits>
 #include <utility>
 
 #include "slab.cuh"
@@ -129,9 +130,11 @@ __device__ __forceinline__ TileCoords grouped_tile_coords(const TileProblem &p, 
   return tc;
 }
 
-template <int MODE>
+// G: a grouped launch (its own instantiation, so a single-matrix kernel carries none of the
+// grouped decode or packed-output epilogue).
+template <int MODE, bool G>
 __device__ __forceinline__ TileCoords tile_coords(const TileProblem &p, int64_t t) {
-  if (MODE != kModeGemm && p.ngroups > 0) return grouped_tile_coords<MODE>(p, t);
+  if (G) return grouped_tile_coords<MODE>(p, t);
   TileCoords tc;
   tc.skip = false;
   tc.pa_set = tc.pb_set = -1;
@@ -209,7 +212,7 @@ struct Smem {
 
 // Consumer warps: walk the same tile sequence as the producer, fold every k-slab into the
 // 8 x 8 register tile, then (optionally) min with the prefetched C tile and store.
-template <typename AR, int MODE, bool ACC>
+template <typename AR, int MODE, bool ACC, bool G>
 __device__ __forceinline__ void consume(const TileProblem &p, const Smem &sm, int warp, int lane, int init_bits) {
   typedef typename AR::T T;
   const int tm = (warp & 3) * 4 + (lane >> 3);
@@ -219,7 +222,7 @@ __device__ __forceinline__ void consume(const TileProblem &p, const Smem &sm, in
   uint32_t phase = 0, cphase = 0;
   const T init = AR::from(init_bits);
   for (int64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
-    const TileCoords tc = tile_coords<MODE>(p, t);
+    const TileCoords tc = tile_coords<MODE, G>(p, t);
     if (tc.skip) continue;  // the producer skips the same tiles
     const int nk = (tc.k_len + kBK - 1) / kBK;
     T acc[8][8];
@@ -283,7 +286,7 @@ __device__ __forceinline__ void consume(const TileProblem &p, const Smem &sm, in
         }
       }
     }
-    if (MODE != kModeGemm && !AR::kFloat && p.arith16 && p.pk_a[0] && (tc.pa_set >= 0 || tc.pb_set >= 0)) {
+    if (G && MODE != kModeGemm && !AR::kFloat && p.arith16 && p.pk_a[0] && (tc.pa_set >= 0 || tc.pb_set >= 0)) {
       int v[8][8];
 #pragma unroll
       for (int i = 0; i < 8; ++i)
@@ -299,7 +302,7 @@ __device__ __forceinline__ void consume(const TileProblem &p, const Smem &sm, in
 
 // S: storage type (int or float).  Float matrices always take ArithF32; int matrices take
 // ArithF32 when small_int_bound holds for this launch, else ArithI32 (uniform per launch).
-template <typename S, int MODE, bool ACC>
+template <typename S, int MODE, bool ACC, bool G>
 __global__ void __launch_bounds__(kThreads, 1)
     tgemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
                  const __grid_constant__ CUtensorMap mC, const __grid_constant__ TileProblem p) {
@@ -336,7 +339,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool c_issued = false, ok = true;
       uint32_t c_par = 0;
       for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
-        const TileCoords tc = tile_coords<MODE>(p, t);
+        const TileCoords tc = tile_coords<MODE, G>(p, t);
         if (tc.skip) continue;  // the consumers skip the same tiles
         const int nk = (tc.k_len + kBK - 1) / kBK;
         for (int kt = 0; kt < nk; ++kt) {
@@ -368,13 +371,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kConsumerRegs));
   const Smem sm = {sA, sB, sC, full, empty, cfull, cempty};
   if (sizeof(S) == 4 && S(0.5) != S(0)) {  // float storage
-    consume<ArithF32, MODE, ACC>(p, sm, warp, lane, 0x7f800000);
+    consume<ArithF32, MODE, ACC, G>(p, sm, warp, lane, 0x7f800000);
   } else if (p.arith16) {
-    consume<ArithI16x2, MODE, ACC>(p, sm, warp, lane, (kCap16 << 16) | kCap16);
+    consume<ArithI16x2, MODE, ACC, G>(p, sm, warp, lane, (kCap16 << 16) | kCap16);
   } else if (p.wmax && small_int_bound(p.wmax[0], p.wmult, p.wmax[1])) {
-    consume<ArithF32, MODE, ACC>(p, sm, warp, lane, p.inf_i);
+    consume<ArithF32, MODE, ACC, G>(p, sm, warp, lane, p.inf_i);
   } else {
-    consume<ArithI32, MODE, ACC>(p, sm, warp, lane, p.inf_i);
+    consume<ArithI32, MODE, ACC, G>(p, sm, warp, lane, p.inf_i);
   }
 }
 
@@ -388,10 +391,10 @@ template <int MODE> static double algorithmic_pairs(const TileProblem &p) {
   return MODE == kModeFwPanels ? 2.0 * bk * bk * rest : rest * rest * bk;
 }
 
-template <typename T, int MODE, bool ACC>
+template <typename T, int MODE, bool ACC, bool G = false>
 static int launch_one(const CUtensorMap &mA, const CUtensorMap &mB, const CUtensorMap &mC, const TileProblem &p,
                       cudaStream_t s) {
-  auto k = tgemm_kernel<T, MODE, ACC>;
+  auto k = tgemm_kernel<T, MODE, ACC, G>;
   static int checked = 0;  // 1: register split verified for this instantiation
   if (!checked) {
     cudaFuncAttributes fa;
@@ -415,6 +418,17 @@ static int launch_one(const CUtensorMap &mA, const CUtensorMap &mB, const CUtens
 template <typename T>
 static int launch_t(int mode, bool acc, const CUtensorMap &mA, const CUtensorMap &mB, const CUtensorMap &mC,
                     const TileProblem &p, cudaStream_t s) {
+  if (p.ngroups > 0) {  // grouped launches: int32 storage, FW modes only
+    if constexpr (std::is_same<T, int>::value) {
+      switch (mode * 2 + (acc ? 1 : 0)) {
+        case 2: return launch_one<T, kModeFwPanels, false, true>(mA, mB, mC, p, s);
+        case 5: return launch_one<T, kModeFwRest, true, true>(mA, mB, mC, p, s);
+        case 7: return launch_one<T, kModeFwRest16, true, true>(mA, mB, mC, p, s);
+        default: return APSP_ERR_ARG;
+      }
+    }
+    return APSP_ERR_ARG;
+  }
   switch (mode * 2 + (acc ? 1 : 0)) {
     case 0: return launch_one<T, kModeGemm, false>(mA, mB, mC, p, s);
     case 1: return launch_one<T, kModeGemm, true>(mA, mB, mC, p, s);
