@@ -13,9 +13,14 @@
 //     phase 3  every other tile D[i][j] = min(D[i][j], D[i][kb] (x) D[kb][j]).
 // Phases 2-3 run the register-tiled slab arithmetic of the GEMM engine (slab.cuh), fed by a
 // four-stage cp.async pipeline that streams across tile boundaries (each graph has its own
-// shape, so no per-graph TMA descriptors are needed).  int32 graphs whose (n - 1) * largest finite weight < 2^24 use
-// the exact fp32 instruction sequence; others the int32 one.  One CTA per graph needs no
-// inter-CTA synchronisation: there is no spin-wait anywhere in this kernel.
+// shape, so no per-graph TMA descriptors are needed).  int32 graphs whose (n - 1) * largest
+// finite weight < 2^24 use the exact fp32 instruction sequence; others the int32 one.  One CTA
+// per graph needs no inter-CTA synchronisation: there is no spin-wait anywhere in this kernel.
+//
+// apsp_batched (below) gives this kernel the whole batch, or -- for an int32 batch with the
+// host sizes and the staging room in the workspace -- only the graphs of at most 256 vertices
+// (and any above 2048), while the others are closed in lockstep on the GEMM engine
+// (grouped.cu), where a graph's work is spread over every SM instead of one CTA.
 #include <cooperative_groups.h>
 
 #include <vector>
