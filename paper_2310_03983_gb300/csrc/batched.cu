@@ -23,6 +23,7 @@
 // (grouped.cu), where a graph's work is spread over every SM instead of one CTA.
 #include <cooperative_groups.h>
 
+#include <mutex>
 #include <vector>
 
 #include "diag.cuh"
@@ -430,9 +431,13 @@ template <typename S>
 static BatchShape batch_shape() {
   static BatchShape cache[64];
   static bool have[64] = {false};
+  static std::mutex mu;
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && have[dev]) return cache[dev];
+  if (dev >= 0 && dev < 64) {
+    std::lock_guard<std::mutex> lk(mu);
+    if (have[dev]) return cache[dev];
+  }
   BatchShape best;
   best.clusters = sm_count();
   for (int c : {8, 4, 2}) {
@@ -459,6 +464,7 @@ static BatchShape batch_shape() {
     }
   }
   if (dev >= 0 && dev < 64) {
+    std::lock_guard<std::mutex> lk(mu);
     cache[dev] = best;
     have[dev] = true;
   }

@@ -12,28 +12,30 @@ namespace apsp {
 
 __device__ unsigned int g_status = 0;
 
+// Per-device caches below are atomics: calls may come from several host threads, and every
+// thread that fills an entry stores the same value.
 unsigned int *status_word() {
-  static unsigned int *cached[64] = {nullptr};
+  static std::atomic<unsigned int *> cached[64];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-  if (!cached[dev]) {
+  if (!cached[dev].load(std::memory_order_acquire)) {
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return nullptr;
-    cached[dev] = reinterpret_cast<unsigned int *>(p);
+    cached[dev].store(reinterpret_cast<unsigned int *>(p), std::memory_order_release);
   }
-  return cached[dev];
+  return cached[dev].load(std::memory_order_acquire);
 }
 
 int sm_count() {
-  static int cached[64] = {0};
+  static std::atomic<int> cached[64];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
-  if (cached[dev] == 0) {
-    int v = 0;
+  int v = cached[dev].load(std::memory_order_relaxed);
+  if (v == 0) {
     if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
-    cached[dev] = v;
+    cached[dev].store(v, std::memory_order_relaxed);
   }
-  return cached[dev];
+  return v;
 }
 
 // Library workspace pool: a stream-ordered memory pool per device that keeps freed blocks
@@ -144,9 +146,9 @@ struct TraceRec {
 };
 static std::mutex g_trace_mu;
 static std::vector<TraceRec> g_trace;
-static bool g_trace_on = false;
+static std::atomic<bool> g_trace_on{false};
 
-bool trace_on() { return g_trace_on; }
+bool trace_on() { return g_trace_on.load(std::memory_order_relaxed); }
 
 void trace_begin(cudaStream_t s, void **ev0) {
   cudaEvent_t e = nullptr;

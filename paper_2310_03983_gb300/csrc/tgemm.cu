@@ -20,6 +20,7 @@
 //
 // No tensor cores: (min,+) is not a multiply-accumulate.  int32 results are exact; fp32
 // results are bitwise deterministic (min is exact, each candidate sum is one rounding).
+#include <atomic>
 #include <math.h>
 #include <type_traits>
 #include <utility>
@@ -395,13 +396,13 @@ template <typename T, int MODE, bool ACC, bool G = false>
 static int launch_one(const CUtensorMap &mA, const CUtensorMap &mB, const CUtensorMap &mC, const TileProblem &p,
                       cudaStream_t s) {
   auto k = tgemm_kernel<T, MODE, ACC, G>;
-  static int checked = 0;  // 1: register split verified for this instantiation
-  if (!checked) {
+  static std::atomic<int> checked{0};  // 1: register split verified for this instantiation
+  if (!checked.load(std::memory_order_relaxed)) {
     cudaFuncAttributes fa;
     APSP_CUDA_TRY(cudaFuncGetAttributes(&fa, k));
     // setmaxnreg.inc would wait forever if the split asked for more than the launch holds.
     if (fa.numRegs < kLaunchRegs || fa.maxThreadsPerBlock < kThreads) return APSP_ERR_UNSUPPORTED;
-    checked = 1;
+    checked.store(1, std::memory_order_relaxed);
   }
   APSP_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes + 1024));
   const int64_t sms = sm_count();
