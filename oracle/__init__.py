@@ -10,6 +10,8 @@ What is here, each citing the passage it follows:
                          int64 for int32 inputs and fp64 for float32 inputs; ``fw_steps`` runs
                          the same loop over a range of intermediate vertices.
   * ``minplus``       -- Eq. 2 (Sec. 3), the (min,+) product, as a triple loop in C.
+  * ``minplus_rows``  -- selected rows of the same product, on int32 / float32 operands widened
+                         value by value (checks rows of products too large for ``minplus``).
   * ``squaring``      -- the paper's "Floyd-Warshall on GPU" (Sec. 3.2): H <- H (x) H with
                          ``minplus`` until nothing changes (or a given number of products).
   * ``dijkstra_rows`` -- single-source distances from chosen sources by array Dijkstra: an
@@ -93,6 +95,10 @@ def _bind(lib):
     lib.oracle_last_hop_f32.argtypes = [f32p, f32p, i64p, I64, i64p, I64, INT]
     for f in ("oracle_fw_pred_i64", "oracle_fw_pred_f64", "oracle_last_hop_i64", "oracle_last_hop_f32"):
         getattr(lib, f).restype = None
+    lib.oracle_minplus_rows_i32.argtypes = [i64p, i32p, i32p, I64, I64, i64p, I64, I64, INT, INT]
+    lib.oracle_minplus_rows_f32.argtypes = [f64p, f32p, f32p, I64, I64, i64p, I64, INT, INT]
+    lib.oracle_minplus_rows_i32.restype = None
+    lib.oracle_minplus_rows_f32.restype = None
     lib.oracle_openmp_enabled.restype = INT
     for f in ("oracle_fw_i64", "oracle_fw_f64", "oracle_fw_i64_steps", "oracle_fw_f64_steps", "oracle_minplus_i64", "oracle_minplus_f64",
               "oracle_dijkstra_rows_i64", "oracle_dijkstra_rows_f64"):
@@ -170,6 +176,30 @@ def minplus(x: np.ndarray, y: np.ndarray, z: np.ndarray | None = None, inf: int 
     Y = np.ascontiguousarray(y, dtype=np.float64)
     Z = np.full((M, N), np.inf) if z is None else np.ascontiguousarray(z, dtype=np.float64).copy()
     lib.oracle_minplus_f64(Z, X, Y, M, N, K, int(z is not None))
+    return Z
+
+
+def minplus_rows(x: np.ndarray, y: np.ndarray, rows, z: np.ndarray | None = None, inf: int = INF_I32,
+                 threads: int | None = None, lib=None) -> np.ndarray:
+    """Rows ``rows`` of the (min,+) product of Eq. 2, x (M x K) (x) y (K x N), folded into z
+    (len(rows) x N) when given.  int32 operands -> int32 result (int64 sums, >= inf reported as
+    inf); float32 operands -> float64 result (fp64 sums)."""
+    lib = lib or load()
+    M, K = x.shape
+    K2, N = y.shape
+    assert K == K2
+    src = np.ascontiguousarray(rows, dtype=np.int64)
+    assert src.size == 0 or (src.min() >= 0 and src.max() < M)
+    if x.dtype.kind in "iu":
+        X = np.ascontiguousarray(x, dtype=np.int32)
+        Y = np.ascontiguousarray(y, dtype=np.int32)
+        Z = np.empty((len(src), N), np.int64) if z is None else np.ascontiguousarray(z, dtype=np.int64).copy()
+        lib.oracle_minplus_rows_i32(Z, X, Y, N, K, src, len(src), int(inf), int(z is not None), _threads(threads))
+        return Z.astype(np.int32)
+    X = np.ascontiguousarray(x, dtype=np.float32)
+    Y = np.ascontiguousarray(y, dtype=np.float32)
+    Z = np.empty((len(src), N), np.float64) if z is None else np.ascontiguousarray(z, dtype=np.float64).copy()
+    lib.oracle_minplus_rows_f32(Z, X, Y, N, K, src, len(src), int(z is not None), _threads(threads))
     return Z
 
 

@@ -16,6 +16,9 @@
  *   - oracle_minplus_i64 / oracle_minplus_f64: the (min,+) product of Eq. 2,
  *       Z[i,j] = min_k ( X[i,k] + Y[k,j] ),
  *     as a triple loop, optionally folded into an existing Z (Z = min(Z, X (x) Y)).
+ *   - oracle_minplus_rows_i32 / _f32: selected rows of the same product, reading operands in
+ *     their 32-bit storage types and widening each value to int64 / fp64 as it is read (used to
+ *     check rows of a product too large for the full triple loop).
  *   - oracle_fw_pred_i64 / _f64: Eq. 1 with the predecessor indices of Sec. 2: pred[i][j]
  *     starts as i where the edge i -> j exists and, whenever the path through k shortens
  *     d[i][j], becomes pred[k][j], the vertex before j on the path from k.
@@ -179,6 +182,64 @@ void oracle_minplus_f64(double *Z, const double *X, const double *Y, int64_t M, 
       }
       Z[i * N + j] = best;
     }
+}
+
+/* Selected rows of Eq. 2 on operands in their storage types: for r < nrows,
+ *   Z[r][j] = min_k ( X[rows[r]][k] + Y[k][j] )      (folded into Z when accumulate != 0),
+ * X is M x K and Y is K x N (int32, leading dimensions K and N), Z is nrows x N int64.  Each value
+ * is widened to int64 as it is read, so no sum overflows.  The candidate sums are those of
+ * oracle_minplus_i64; they are visited k-outer (a row of Y at a time) because the minimum of a
+ * set does not depend on the order it is taken in, and a column walk of a large Y would take
+ * hours.  Entries >= inf are missing; a result >= inf is written as inf. */
+void oracle_minplus_rows_i32(int64_t *Z, const int32_t *X, const int32_t *Y, int64_t N, int64_t K,
+                             const int64_t *rows, int64_t nrows, int64_t inf, int accumulate, int threads) {
+  set_threads(threads);
+#pragma omp parallel for schedule(dynamic, 1) if (threads > 1)
+  for (int64_t r = 0; r < nrows; ++r) {
+#if ORACLE_PLANT == 8 /* plant 8: the r-th row of X instead of row rows[r] */
+    const int32_t *x = X + r * K;
+#else
+    const int32_t *x = X + rows[r] * K;
+#endif
+    int64_t *z = Z + r * N;
+    for (int64_t j = 0; j < N; ++j) {
+      int64_t v = accumulate ? z[j] : inf;
+      z[j] = v > inf ? inf : v;
+    }
+    for (int64_t k = 0; k < K; ++k) {
+      const int64_t xk = x[k];
+      if (xk >= inf) continue;
+      const int32_t *y = Y + k * N;
+      for (int64_t j = 0; j < N; ++j) {
+        const int64_t ykj = y[j];
+        if (ykj >= inf) continue;
+        if (xk + ykj < z[j]) z[j] = xk + ykj;
+      }
+    }
+  }
+}
+
+/* The same over float32 operands, each widened to fp64 as it is read (the sum of two fp32
+ * values is exact in fp64); +infinity = missing. */
+void oracle_minplus_rows_f32(double *Z, const float *X, const float *Y, int64_t N, int64_t K,
+                             const int64_t *rows, int64_t nrows, int accumulate, int threads) {
+  set_threads(threads);
+#pragma omp parallel for schedule(dynamic, 1) if (threads > 1)
+  for (int64_t r = 0; r < nrows; ++r) {
+    const float *x = X + rows[r] * K;
+    double *z = Z + r * N;
+    if (!accumulate)
+      for (int64_t j = 0; j < N; ++j) z[j] = INFINITY;
+    for (int64_t k = 0; k < K; ++k) {
+      const double xk = x[k];
+      if (isinf(xk)) continue;
+      const float *y = Y + k * N;
+      for (int64_t j = 0; j < N; ++j) {
+        const double s = xk + (double)y[j];
+        if (s < z[j]) z[j] = s;
+      }
+    }
+  }
 }
 
 /* Array Dijkstra from each source in src[0..nsrc): out is nsrc x n.

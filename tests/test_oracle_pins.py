@@ -203,6 +203,45 @@ def test_minplus_matches_broadcast_tensor(M, N, K):
     assert np.array_equal(oracle.minplus(xf, yf), _broadcast_minplus(xf, yf))
 
 
+def _rows_pin_passes(lib):
+    """Selected rows of the product (unsorted, repeated, with a fold into z) against the paper's
+    3-D broadcast formulation of the same rows; True if every case agrees."""
+    rng = np.random.default_rng(77)
+    for M, N, K in [(9, 7, 5), (31, 40, 17), (16, 3, 64), (5, 5, 1)]:
+        rows = rng.integers(0, M, size=6)
+        x = np.where(rng.random((M, K)) < 0.6, rng.integers(0, 1000, (M, K)), INF).astype(np.int32)
+        y = np.where(rng.random((K, N)) < 0.6, rng.integers(0, 1000, (K, N)), INF).astype(np.int32)
+        want = _broadcast_minplus(x[rows], y, INF)
+        if not np.array_equal(oracle.minplus_rows(x, y, rows, lib=lib).astype(np.int64), want):
+            return False
+        z = rng.integers(0, 1500, (len(rows), N)).astype(np.int32)
+        if not np.array_equal(oracle.minplus_rows(x, y, rows, z=z, lib=lib).astype(np.int64),
+                              np.minimum(z.astype(np.int64), want)):
+            return False
+        xf = np.where(rng.random((M, K)) < 0.6, rng.lognormal(size=(M, K)), np.inf).astype(np.float32)
+        yf = np.where(rng.random((K, N)) < 0.6, rng.lognormal(size=(K, N)), np.inf).astype(np.float32)
+        if not np.array_equal(oracle.minplus_rows(xf, yf, rows, threads=3, lib=lib), _broadcast_minplus(xf[rows], yf)):
+            return False
+    return True
+
+
+def test_minplus_rows_match_broadcast_tensor():
+    assert _rows_pin_passes(oracle.load())
+
+
+def test_minplus_rows_pin_catches_a_wrong_row():
+    """Plant 8 reads the r-th row of X instead of row rows[r]: the pin must fail."""
+    assert not _rows_pin_passes(oracle.load(plant=8))
+
+
+def test_minplus_rows_equal_full_product():
+    h = workloads.er_graph(300, 0.05, "int32", lo=1, hi=100, seed=4)
+    rows = np.array([0, 299, 17, 150])
+    assert np.array_equal(oracle.minplus_rows(h, h, rows, threads=4), oracle.minplus(h, h)[rows])
+    hf = workloads.er_graph(200, 0.1, "float32", dist="uniform01", seed=4)
+    assert np.array_equal(oracle.minplus_rows(hf, hf, rows[rows < 200]), oracle.minplus(hf, hf)[rows[rows < 200]])
+
+
 def test_minplus_identity_and_outer_sum():
     rng = np.random.default_rng(5)
     n = 23
