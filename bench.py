@@ -14,8 +14,10 @@ torchrun every rank closes its own replica (no data-path collective: "scaling": 
 the time is the max over ranks and the value sums all ranks' work.
 
 --impl reference times the CPU oracle (the plain k-i-j triple loop of oracle/) on the host
-cores, on a bounded sample of the same workload: the loop over a prefix of the intermediate
-vertices k of the same n x n matrix, converted to the same unit.
+cores, on a bounded sample of the same workload: one full closure of the workload's matrix when
+n <= 4096, else of a 4096-vertex graph from the same generator, in the same 2 n^3 / s unit.  The
+timed steps split that one closure by ranges of intermediate vertices, so their sum is the
+closure's steady rate (an early prefix alone would skip most rows and read high).
 """
 from __future__ import annotations
 
@@ -42,7 +44,23 @@ WORKLOADS = {
     "tgemm_n32768": dict(n=32768, p=0.05, dtype="int32", dist="uniform", lo=1, hi=100, algo="gemm"),
     "tgemm_n8192": dict(n=8192, p=0.05, dtype="int32", dist="uniform", lo=1, hi=100, algo="gemm"),
     "apsp_fw_n32768_f32": dict(n=32768, p=0.05, dtype="float32", dist="uniform01", lo=0, hi=1, algo="fw"),
+    "apsp_fw_n32768_heavy": dict(n=32768, p=0.05, dtype="int32", dist="uniform", lo=1, hi=10**6, algo="fw"),
+    "apsp_rkleene_n32768_f32": dict(n=32768, p=0.05, dtype="float32", dist="uniform01", lo=0, hi=1,
+                                    algo="rkleene", param=1024),
+    "tgemm_n32768_f32": dict(n=32768, p=0.05, dtype="float32", dist="uniform01", lo=0, hi=1, algo="gemm"),
+    # n = 512, p = 0.1, int32 weights in [1, 100]: plain blocked FW
+    "apsp_fw_n512": dict(n=512, p=0.1, dtype="int32", dist="uniform", lo=1, hi=100, algo="fw"),
+    # n = 4096 at p = 0.01 and 0.5 with int32 weights in [1, 1000], and fp32 lognormal(0, 1) at
+    # p = 0.5: blocked FW against R-Kleene with cutoff 256
     "apsp_fw_n4096": dict(n=4096, p=0.5, dtype="int32", dist="uniform", lo=1, hi=1000, algo="fw"),
+    "apsp_fw_n4096_p01": dict(n=4096, p=0.01, dtype="int32", dist="uniform", lo=1, hi=1000, algo="fw"),
+    "apsp_fw_n4096_f32": dict(n=4096, p=0.5, dtype="float32", dist="lognormal", lo=0.0, hi=1.0, algo="fw"),
+    "apsp_rkleene_n4096": dict(n=4096, p=0.5, dtype="int32", dist="uniform", lo=1, hi=1000, algo="rkleene",
+                               param=256),
+    "apsp_rkleene_n4096_p01": dict(n=4096, p=0.01, dtype="int32", dist="uniform", lo=1, hi=1000, algo="rkleene",
+                                   param=256),
+    "apsp_rkleene_n4096_f32": dict(n=4096, p=0.5, dtype="float32", dist="lognormal", lo=0.0, hi=1.0,
+                                   algo="rkleene", param=256),
     "apsp_fw_n8192": dict(n=8192, p=0.05, dtype="int32", dist="uniform", lo=1, hi=100, algo="fw"),
     "apsp_fw_n16384": dict(n=16384, p=0.05, dtype="int32", dist="uniform", lo=1, hi=100, algo="fw"),
     "batched_2048": dict(n=None, count=2048, dtype="int32", dist="uniform", lo=1, hi=100, algo="batched"),
@@ -84,7 +102,8 @@ def parse():
     ap.add_argument("--workload", default="apsp_fw_n32768", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU sample")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target length of the CPU sample (batched and serving workloads)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="length of the Poisson request stream")
     return ap.parse_args()
@@ -178,32 +197,50 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- CPU leg
-def cpu_sample(h, seconds: float, cores: int):
-    """Time the oracle's Eq. 1 loop over a prefix of the intermediate vertices of the same
-    matrix; return (Gop/s, cores, description)."""
-    import oracle
-    n = h.shape[0]
+CPU_SAMPLE_N = 4096
+
+
+def cpu_sample_matrix(w, h=None):
+    """The matrix the CPU leg closes: the workload's own matrix when n <= 4096, else a 4096-vertex
+    graph from the same generator (same edge probability, weight distribution and seed)."""
+    n = w["n"]
+    if h is not None and n <= CPU_SAMPLE_N:
+        return h
+    return gen_input(dict(w, n=min(n, CPU_SAMPLE_N)))
+
+
+def oracle_prepared(h):
+    import oracle  # noqa: F401
     if h.dtype == np.int32:
         d = np.minimum(h.astype(np.int64), workloads.INF_I32)
     else:
         d = h.astype(np.float64)
     np.fill_diagonal(d, 0)
-    k, done, t_total = 0, 0, 0.0
-    step = 1
-    while t_total < seconds and k < n:
-        k1 = min(n, k + step)
+    return d
+
+
+def cpu_closure(h, cores: int, parts: int = 1):
+    """Time one full closure of h by the oracle's Eq. 1 loop (every intermediate vertex k, int64
+    or fp64), split into `parts` consecutive ranges of k.  Returns the seconds of each part; their
+    sum is the whole closure, so 2 n^3 / sum is its steady rate whatever the split."""
+    import oracle
+    n = h.shape[0]
+    d = oracle_prepared(h)
+    out = []
+    bounds = [round(n * i / parts) for i in range(parts + 1)]
+    for k0, k1 in zip(bounds[:-1], bounds[1:]):
         t0 = time.perf_counter()
-        oracle.fw_steps(d, k, k1, threads=cores)
-        dt = time.perf_counter() - t0
-        t_total += dt
-        done += k1 - k
-        k = k1
-        if dt < seconds / 8:
-            step *= 2
-    ops = 2.0 * n * n * done
-    desc = (f"oracle k-i-j loop (Eq. 1, int64/fp64) over intermediate vertices 0..{done - 1} of the same "
-            f"n={n} matrix ({done}/{n} of the full closure), {t_total:.1f} s")
-    return ops / t_total / 1e9, desc
+        oracle.fw_steps(d, k0, k1, threads=cores)
+        out.append(time.perf_counter() - t0)
+    return out
+
+
+def cpu_sample_desc(w, hs, seconds, cores):
+    n = hs.shape[0]
+    what = "the workload's own matrix" if n == w["n"] else (
+        f"a {n}-vertex graph from the same generator (p={w['p']}, weights {w['dtype']} {w['dist']}, seed 0)")
+    return (f"one full closure by the oracle's k-i-j loop (Eq. 1, int64/fp64) of {what}, {seconds:.1f} s on "
+            f"{cores} threads; rate = 2 n^3 / time with n = {n}, the same (min,+) Gop/s unit as the GPU line")
 
 
 def cores_available():
@@ -214,32 +251,40 @@ def cores_available():
 
 
 def run_reference(args, w, rank, world):
+    """The oracle on the host cores.  The timed steps together make ONE full closure of the CPU
+    sample matrix (step s runs its s-th range of intermediate vertices), so the reported rate is
+    that closure's steady rate and the run stays bounded; each warm-up step closes a 512-vertex
+    graph of the same generator."""
     if rank != 0:
         return 0
     import oracle
     oracle.build()
     cores = cores_available() if oracle.openmp_enabled() else 1
-    h = gen_input(w)
-    per_step = max(1.0, args.cpu_seconds / max(1, args.steps))
+    hs = cpu_sample_matrix(w)
+    warm = gen_input(dict(w, n=min(512, hs.shape[0])))
     for _ in range(args.warmup):
-        cpu_sample(h, 0.2, cores)
-    vals, descs = [], []
+        cpu_closure(warm, cores)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        v, desc = cpu_sample(h, per_step, cores)
-        vals.append(v)
-        descs.append(desc)
+    parts = cpu_closure(hs, cores, parts=max(1, args.steps))
     wall = time.perf_counter() - t0
-    value = statistics.median(vals)
+    total = sum(parts)
+    ns = hs.shape[0]
+    value = 2.0 * ns ** 3 / total / 1e9
     n = w["n"]
+    desc = cpu_sample_desc(w, hs, total, cores)
     line = {
         "impl": "reference", "metric": "(min,+) Gop/s (2n^3/s)", "value": round(value, 3), "unit": "Gop/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(2.0 * n ** 3 / (value * 1e9) * 1e3, 1), "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": round(total / len(parts) * 1e3, 1), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "i64" if w["dtype"] == "int32" else "f64", "data": "synthetic",
         "config": config_of(args, w, world),
+        "step": f"1/{len(parts)} of the intermediate vertices of one {ns}-vertex closure (the steps together "
+                f"close it once)",
+        **({"ms_per_closure_extrapolated": round(2.0 * n ** 3 / (value * 1e9) * 1e3, 1),
+            "ms_per_closure_extrapolated_basis": f"2 n^3 at n = {n} divided by the measured rate (not run)"}
+           if n > ns else {}),
         "cpu_baseline": {"value": round(value, 3), "unit": "Gop/s", "cores": cores, "kind": "oracle",
-                         "sample": descs[-1]},
+                         "sample": desc},
         "e2e": {"value": round(value, 3), "unit": "Gop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": round(wall, 1),
     }
@@ -296,6 +341,11 @@ def aggregate(ms_local: float, work_local: float, device=None):
     return float(t.item()), float(w.item())
 
 
+BATCH_LAUNCH = ("one apsp_batched call per step, replayed from a captured CUDA graph: graphs of 257-2048 "
+                "vertices closed in lockstep on the tropical-GEMM engine (a few launches per 128-vertex block "
+                "for all of them), the smaller ones by one persistent launch")
+
+
 def config_of(args, w, world):
     if w["algo"] == "serve":
         return {"workload": args.workload, "arrivals": f"Poisson {w['rate']:.0f}/s for {args.serve_seconds:.0f} s",
@@ -309,18 +359,19 @@ def config_of(args, w, world):
         return {"workload": args.workload, "graphs": w["count"],
                 "generator": "f(V, rho, alpha) of Sec. 3.4: V uniform {4..1000}, rho uniform [0, 100] (rho P clipped "
                              "to 1), alpha = 100, costs uniform {0..100}; sorted by edge count (Sec. 4)",
-                "algo": "batched persistent FW", "launch": "one persistent launch replayed from a captured CUDA graph",
+                "algo": "batched FW", "launch": BATCH_LAUNCH,
                 "parallelism": f"replicas{world}", "l2": "pool 1.4 GB per step, larger than L2; no flush"}
     if w["algo"] == "batched":
         return {"workload": args.workload, "graphs": w["count"], "n": "log-uniform [32, 1024]",
-                "edge_p": "uniform [0.02, 0.8]", "weights": "int32 uniform[1,100]", "algo": "batched persistent FW",
-                "launch": "one persistent launch replayed from a captured CUDA graph", "parallelism": f"replicas{world}",
+                "edge_p": "uniform [0.02, 0.8]", "weights": f"{w['dtype']} " + (
+                    "uniform[1,100]" if w["dtype"] == "int32" else "lognormal(0,1)"), "algo": "batched FW",
+                "launch": BATCH_LAUNCH, "parallelism": f"replicas{world}",
                 "l2": "pool 1.2 GB per step, larger than L2; no flush"}
     c = {"workload": args.workload, "n": w["n"], "edge_p": w["p"], "weights": f"{w['dtype']} {w['dist']}"
          f"[{w['lo']},{w['hi']}]", "algo": w["algo"], "graphs_per_step_per_gpu": 1,
          "parallelism": f"replicas{world}", "l2": "inputs 4 GiB per step, larger than L2; no flush"}
     if w["n"] < 32768:
-        c["l2"] = "inputs smaller than L2: L2 flushed between steps by a 256 MiB write"
+        c["l2"] = "inputs smaller than L2: L2 flushed between steps by a 256 MiB write (outside the timed steps)"
     if "param" in w:
         c["param"] = w["param"]
     return c
@@ -396,20 +447,28 @@ def run_ours(args, w, rank, world, local_rank):
         dist.barrier()
     torch.cuda.synchronize()
     sampler.begin()
+    # Each step is bracketed by its own events; the L2 flush and any restore copy between steps
+    # fall outside them.
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     apsp.apsp_launch_count(reset=True)
+    launches = 0
     e0.record(stream)
     for i in range(args.steps):
         if flush is not None:
             flush.zero_()
-        step_fn(prepare(args.warmup + i), gemm_out)
+        buf = prepare(args.warmup + i)
+        ev[i][0].record(stream)
+        c0 = apsp.apsp_launch_count()
+        step_fn(buf, gemm_out)
+        launches += apsp.apsp_launch_count() - c0
+        ev[i][1].record(stream)
     e1.record(stream)
-    launches = apsp.apsp_launch_count()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     apsp.apsp_trace_enable(False)
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
+    ms = sum(a.elapsed_time(b) for a, b in ev)
     dom_mode = 0 if w["algo"] in ("gemm", "rkleene") else 2
     k_ms, k_launches, k_pairs = apsp.apsp_trace_read(dom_mode)
 
@@ -457,7 +516,7 @@ def run_ours(args, w, rank, world, local_rank):
     traffic, traffic_note = None, None
     bt = 2 if n >= 16384 else 1
     per_elem = PHASE3_DRAM_BYTES_PER_C_ELEM.get(bt)
-    if dom_mode == 2 and w["dtype"] == "int32" and n >= 4096:
+    if dom_mode == 2 and w["dtype"] == "int32" and n >= 4096 and w["hi"] <= 0x3FFF // 4:
         if per_elem is None or tgemm_src_hash() != PHASE3_TRAFFIC_SRC_HASH:
             traffic_note = "no ncu capture of this phase-3 kernel build: traffic not known"
         else:
@@ -466,8 +525,12 @@ def run_ours(args, w, rank, world, local_rank):
             traffic_note = (f"dram bytes per launch from one ncu capture of the 16-bit phase-3 kernel at "
                             f"n={8192 * bt} ({128 * bt}-vertex blocks), scaled by (n-{128 * bt})^2; "
                             f"algorithmic {8 * c_elems} B (each C tile read and written once)")
-    fw16 = w["algo"] == "fw" and w["dtype"] == "int32" and n >= 4096
-    if w["dtype"] != "int32":
+    fw16 = w["algo"] == "fw" and w["dtype"] == "int32" and n >= 4096 and w["hi"] <= 0x3FFF // 4
+    heavy = w["dtype"] == "int32" and (n - 1) * w["hi"] >= (1 << 24) and not fw16
+    if heavy:
+        arith = ("int32 DPX add-min (__viaddmin_s32): weights too large for the 16-bit pass and for the "
+                 "a-priori exact fp32 bound")
+    elif w["dtype"] != "int32":
         arith = "fp32 packed add + 3-input min"
     elif w["algo"] == "gemm":
         arith = "packed 16-bit pairs, one DPX add-min per two pairs (exact: max A + max B < 0x3FFF)"
@@ -481,7 +544,8 @@ def run_ours(args, w, rank, world, local_rank):
                  "< cap; else an int32 pass); phases 1-2 exact in fp32 on int32 bit patterns")
     else:
         arith = "fp32 packed add + 3-input min on int32 bit patterns (exact: every distance < 2^24)"
-    dtype_tag = "f32" if w["dtype"] != "int32" else ("i16x2" if (fw16 or w["algo"] in ("gemm", "rkleene")) else "i32")
+    dtype_tag = "f32" if w["dtype"] != "int32" else (
+        "i16x2" if (fw16 or (w["algo"] in ("gemm", "rkleene") and w["hi"] <= 100)) else "i32")
     line = {
         "metric": "(min,+) Gop/s (2n^3/s)", "value": round(value, 2), "unit": "Gop/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 2),
@@ -509,9 +573,10 @@ def run_ours(args, w, rank, world, local_rank):
         import oracle
         oracle.build()
         cores = cores_available() if oracle.openmp_enabled() else 1
-        v, desc = cpu_sample(h, args.cpu_seconds, cores)
-        line["cpu_baseline"] = {"value": round(v, 3), "unit": "Gop/s", "cores": cores, "kind": "oracle",
-                                "sample": desc}
+        hs = cpu_sample_matrix(w, h)
+        t = sum(cpu_closure(hs, cores))
+        line["cpu_baseline"] = {"value": round(2.0 * hs.shape[0] ** 3 / t / 1e9, 3), "unit": "Gop/s", "cores": cores,
+                                "kind": "oracle", "sample": cpu_sample_desc(w, hs, t, cores)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -550,8 +615,8 @@ def run_reference_batched(args, w, rank, world):
 
 
 def run_batched(args, w, rank, world, local_rank):
-    """2048 graphs of uneven size closed in one persistent launch replayed from a CUDA graph;
-    compared with one apsp_fw call per graph on the same GPU."""
+    """2048 graphs of uneven size closed by one apsp_batched call per step, replayed from a
+    captured CUDA graph; compared with one apsp_fw call per graph on the same GPU."""
     import torch
     import torch.distributed as dist
     import paper_2310_03983_gb300 as apsp

@@ -202,7 +202,10 @@ int apsp_squaring(void *d, int64_t n, int64_t ld, int dtype, const void *inf, in
  *   - the first call on a device looks up the array's device address (cudaGetSymbolAddress);
  *     make that first call before any stream capture;
  *   - every call shares the array: calls that overlap on the GPU race and must be serialised
- *     by the caller.
+ *     by the caller;
+ *   - for n up to about 2816 the array also has room for the packed 16-bit operands of the
+ *     largest int32 products, which then run on 16-bit pairs as in apsp_rkleene with a full
+ *     workspace; larger n take the 32-bit products.
  * Results are identical to apsp_rkleene's. */
 #define APSP_NOALLOC_MAX_N 4096
 int apsp_rkleene_noalloc(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int cutoff,

@@ -8,8 +8,9 @@
 // from the caller or allocates.  This variant takes it from a fixed array compiled into the
 // library instead, so the caller passes only the matrix.
 //
-// The array holds 256 bytes of bound words plus one 2048 x 2048 int32 block: enough for any
-// n <= APSP_NOALLOC_MAX_N (4096).  Every GPU that loads libapsp.so keeps these ~16 MiB until
+// The array holds 256 bytes of bound words plus one 2048 x 2048 int32 block: enough for the
+// required scratch of any n <= APSP_NOALLOC_MAX_N (4096), and for smaller n (up to about 2816)
+// also the packed 16-bit operands of the largest products.  Every GPU that loads libapsp.so keeps these ~16 MiB until
 // the process exits.  All calls share the one array per device, so calls that overlap on the
 // GPU (different streams, or different host threads) race on it and must be serialised by
 // the caller.  The array keeps whatever the previous call left in it; the closure zeroes the
@@ -56,8 +57,10 @@ extern "C" int apsp_rkleene_noalloc(void *d, int64_t n, int64_t ld, int dtype, c
   using namespace apsp;
   if (n < 0 || n > kNoAllocMaxN) return APSP_ERR_ARG;   // larger graphs need apsp_rkleene
   if (n > 0 && ld % 4 != 0) return APSP_ERR_ARG;        // would need an aligned copy of the whole matrix
-  // The array holds the required scratch; the optional 16-bit room does not fit, so int32
-  // products run on the plain 32-bit path here.
+  // The array always holds the required scratch.  When the optional room for packed 16-bit
+  // operands also fits beside it (top-level split h <= 1408, i.e. n up to about 2816), int32
+  // products of at least 1e9 pairs run on 16-bit pairs inside the array, as apsp_rkleene does
+  // with a full workspace; otherwise they take the 32-bit path.  Results are the same either way.
   if (closure_required_bytes(1, n, ld, cutoff) > kNoAllocBytes) return APSP_ERR_ARG;
   int err = APSP_OK;
   void *ws = noalloc_scratch(&err);

@@ -59,6 +59,44 @@ def test_staged_equals_persistent_kernel(apsp):
         assert_dist_equal(staged.graph(g, out_s).numpy(), oracle.fw(mats[g], threads=THREADS), f"graph {g}")
 
 
+def _check_batch_against_oracle(b, mats, out, full_max=512, rows_per_large=16):
+    """Every graph of at most full_max vertices in full against the oracle's Eq. 1 closure;
+    rows_per_large seeded Dijkstra rows of every larger graph."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    def check(g):
+        m = mats[g]
+        n = m.shape[0]
+        got = b.graph(g, out).numpy()
+        if n <= full_max:
+            assert_dist_equal(got, oracle.fw(m), f"graph {g} n={n}")
+        else:
+            src = np.sort(np.random.default_rng(g).choice(n, rows_per_large, replace=False))
+            assert_dist_equal(got[src], oracle.dijkstra_rows(m, src), f"graph {g} n={n} rows")
+        return n <= full_max
+
+    with ThreadPoolExecutor(THREADS) as ex:
+        full = list(ex.map(check, range(len(mats))))
+    return sum(full)
+
+
+def test_config4_batch_against_oracle(apsp):
+    """The benchmark's 2048-graph batch itself (n log-uniform in [32, 1024], p uniform in
+    [0.02, 0.8], int32 weights in [1, 100], graph g seeded 1000 + g), closed by one apsp_batched
+    call on the staged path, as the benchmark closes it."""
+    from concurrent.futures import ThreadPoolExecutor
+    ns, ps = workloads.batch_specs(2048, seed=0)
+    with ThreadPoolExecutor(THREADS) as ex:
+        mats = list(ex.map(lambda g: workloads.er_graph(int(ns[g]), float(ps[g]), "int32", lo=1, hi=100,
+                                                        seed=1000 + g, threads=1), range(len(ns))))
+    b = apsp.Batch(mats)
+    out, launches = _run(apsp, b)
+    assert launches > 10  # the staged sequence ran
+    assert apsp.apsp_device_status() == 0
+    full = _check_batch_against_oracle(b, mats, out)
+    assert full > 1500 and len(mats) - full > 300
+
+
 def test_certificate_both_sides_of_the_cap(apsp):
     """Paths whose longest distance plus the largest weight lands just below CAP (certified)
     and just above it (the int32 pass finishes them), next to ordinary graphs."""

@@ -57,7 +57,8 @@ def test_noalloc_matches_rkleene_twice(apsp):
     f = _noalloc(apsp)
     # first call: the largest size the array holds, weights large enough for the int32 path
     h1 = workloads.er_graph(4096, 0.01, "int32", lo=1, hi=10**5, seed=21)
-    # second call: a different size and the exact fp32 path, over the first call's leftovers
+    # second call: a different size, int32 weights small enough for the exact fp32 instruction
+    # sequence on int32 bit patterns, over the first call's leftovers
     h2 = workloads.er_graph(1500, 0.05, "int32", lo=1, hi=100, seed=22)
     for h, cutoff in ((h1, 256), (h2, 128)):
         d = torch.from_numpy(h).cuda()
@@ -78,4 +79,45 @@ def test_noalloc_float_and_limits(apsp):
     assert _call(f, big, 256) == APSP_ERR_ARG
     odd = torch.zeros((300, 303), dtype=torch.int32, device="cuda")[:, :300]
     assert _call(f, odd, 128) == APSP_ERR_ARG
+    assert apsp.apsp_device_status() == 0
+
+
+def test_noalloc_packed_products_in_the_array(apsp):
+    """n = 2560, int32 weights in [1, 100], cutoff 256: the top-level products (1280^3 pairs) run
+    on packed 16-bit pairs whose operands sit in the shared array beside the required scratch.
+    The launch count shows that path ran (it matches apsp_rkleene with a full workspace and
+    exceeds apsp_rkleene with the required workspace only).  Two calls in a row, the second over
+    the first's leftovers, each checked against apsp_rkleene and the second against the oracle's
+    Eq. 1 closure directly."""
+    import oracle
+    f = _noalloc(apsp)
+    n, cutoff = 2560, 256
+    hs = [workloads.er_graph(n, 0.05, "int32", lo=1, hi=100, seed=s) for s in (41, 42)]
+
+    def launches(fn):
+        torch.cuda.synchronize()
+        apsp.apsp_launch_count(reset=True)
+        fn()
+        c = apsp.apsp_launch_count()
+        torch.cuda.synchronize()
+        return c
+
+    dfull = torch.from_numpy(hs[0]).cuda()
+    full_ws = torch.empty(apsp.apsp_rkleene_workspace_bytes(n, n, torch.int32, cutoff), dtype=torch.uint8,
+                          device="cuda")
+    c_full = launches(lambda: apsp.apsp_rkleene(dfull, cutoff=cutoff, ws=full_ws))
+    dbase = torch.from_numpy(hs[0]).cuda()
+    h = (n // 2 + 127) // 128 * 128  # top-level split; the required scratch is one h x h block
+    base_ws = torch.empty(256 + h * h * 4, dtype=torch.uint8, device="cuda")
+    c_base = launches(lambda: apsp.apsp_rkleene(dbase, cutoff=cutoff, ws=base_ws))
+    assert c_full > c_base
+    assert torch.equal(dfull, dbase)
+    for t, h in enumerate(hs):
+        d = torch.from_numpy(h).cuda()
+        c = launches(lambda: _call(f, d, cutoff) == 0 or pytest.fail("noalloc call refused"))
+        assert c == c_full, f"call {t}: {c} launches, {c_full} with the packed path, {c_base} without"
+        got = d.cpu().numpy()
+        assert_dist_equal(got, _reference(apsp, h, cutoff), f"noalloc n={n} call {t}")
+        if t == 1:
+            assert_dist_equal(got, oracle.fw(h, threads=16), f"noalloc n={n} against the oracle")
     assert apsp.apsp_device_status() == 0
