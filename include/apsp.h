@@ -131,8 +131,11 @@ int tropical_gemm(void *C, const void *A, const void *B, int64_t M, int64_t N, i
  * packed pairs (two (min,+) pairs per DPX operation) in the (min,+) semiring truncated at
  * 0x3FFF; a device-side certificate (largest stored value below 0x3FFF plus the largest weight
  * stays below 0x3FFF) proves the result exact, and otherwise the int32 Floyd-Warshall runs
- * again over it.  Results are bit-exact either way.  A workspace without that room is accepted
- * and closes with the plain phase 3. */
+ * again over it.  With the same room, an int32 matrix whose largest weight is above 0x0FFF and
+ * at most 2^22, and too large for the exact fp32 bound, runs phase 3 in fp32 on its bit patterns
+ * truncated at 2^24, certified the same way (largest stored value below 2^24 plus the largest
+ * weight stays below 2^24), else followed by the exact int32 loop.  Results are bit-exact either
+ * way.  A workspace without that room is accepted and closes with the plain phase 3. */
 size_t apsp_fw_workspace_bytes(int64_t n, int64_t ld, int dtype, int tile);
 int apsp_fw(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int tile, void *ws,
             size_t ws_bytes, void *stream);
@@ -150,7 +153,10 @@ int apsp_fw(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int tile
  * largest product packed into 16-bit pairs (h x round_up(ceil(h/2), 4) + ceil(h/2) x
  * round_up(h, 4) words).  With that room, a product of at least 10^9 pairs whose operands'
  * largest finite entries sum below 0x3FFF (a device-side scan) runs on the packed pairs; the
- * result is identical.  A workspace without the packed room is accepted. */
+ * result is identical.  Leaves close as apsp_fw closes a matrix (those of at least 4096
+ * vertices reuse that room for the 16-bit pass); their certificates step by the leaf block's own
+ * largest finite entry (a device-side scan), since a leaf holds path lengths through the
+ * vertices closed before it.  A workspace without the packed room is accepted. */
 size_t apsp_rkleene_workspace_bytes(int64_t n, int64_t ld, int dtype, int cutoff);
 int apsp_rkleene(void *d, int64_t n, int64_t ld, int dtype, const void *inf, int cutoff,
                  void *ws, size_t ws_bytes, void *stream);
@@ -297,6 +303,21 @@ int apsp_mlp_backward(const float *params, int in_dim, const float *x, const flo
 int apsp_mlp_adam(float *params, const float *grads, float *m, float *v, int64_t count, float lr,
                   float beta1, float beta2, float eps, int step, void *stream);
 
+/* ---- host memory for fast transfers ----------------------------------------------------
+ * apsp_host_alloc returns `bytes` of page-locked host memory, registered with CUDA (usable by
+ * cudaMemcpyAsync and the *_host calls below, and readable by kernels), or NULL on failure.
+ * Large buffers (at least a quarter of the system's transparent huge page, 512 MiB on a
+ * 64 KiB-page Grace host, 2 MiB with 4 KiB pages) are mapped on huge-page boundaries and
+ * advised for huge pages before they are pinned.  The GPU reaches host memory through its own
+ * page tables: a 4 GiB buffer of small pages needs tens of thousands of translations, and after
+ * a large closure has pushed them out of the GPU's caches a copy of it ran at about a tenth of
+ * the link's rate (measured on GB300: 200 ms against 20 ms for 4 GiB); the same buffer in huge
+ * pages copies at full rate every time.  Smaller buffers come from cudaHostAlloc.  Free with
+ * apsp_host_free (exactly the pointer returned; NULL is a no-op).  Returns APSP_OK or
+ * APSP_ERR_ARG (a pointer this library did not allocate) / APSP_ERR_CUDA. */
+void *apsp_host_alloc(size_t bytes);
+int apsp_host_free(void *p);
+
 /* ---- host buffers: copy in, close, copy back ------------------------------------------
  * These calls take HOST memory (pinned for full copy speed; pageable works), run the device
  * entry points above on `stream`, and return once the results are in the host buffer (they
@@ -331,8 +352,11 @@ int apsp_batched_host(const void *h_in, void *h_out, void *pool, const int64_t *
  * product and blocked-FW phases 2 and 3) record a CUDA event before and after itself on its
  * stream.  apsp_trace_read(mode, ...) waits for those events, returns the summed elapsed
  * time (ms), the number of launches and their algorithmic (min,+) pairs for engine mode
- * `mode` (0 = product, 1 = FW panels, 2 = FW remaining tiles; -1 = all), then discards
- * every record.  Host-global; not for use inside CUDA-graph capture. */
+ * `mode` (0 = product, 1 = FW panels, 2 = FW remaining tiles; 16 + those: the 32-bit pass
+ * of an int32 FW, which runs unless a 16-bit pass did the work; 32 + those: passes that
+ * normally return at once, such as the exact int32 pass after a certified truncated one;
+ * -1 = all), then discards the records it returned.  Host-global; not for use inside
+ * CUDA-graph capture. */
 int apsp_trace_enable(int on);
 int apsp_trace_read(int mode, double *total_ms, int64_t *launches, double *pairs);
 

@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 
 import numpy as np
 import torch
@@ -71,6 +72,8 @@ def _load():
         "apsp_mlp_backward": ([vp, i32, vp, vp, vp, i32, vp, vp, sz, vp], i32),
         "apsp_mlp_adam": ([vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, i32,
                            vp], i32),
+        "apsp_host_alloc": ([sz], vp),
+        "apsp_host_free": ([vp], i32),
         "apsp_trace_enable": ([i32], i32),
         "apsp_launch_count": ([i32], i64),
         "apsp_trace_read": ([i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
@@ -89,7 +92,7 @@ EXPORTS = ("apsp_version", "apsp_workspace_pool_trim", "apsp_status_str", "apsp_
            "apsp_fw_signed_workspace_bytes", "apsp_fw_signed", "apsp_squaring_workspace_bytes", "apsp_squaring", "apsp_predecessors_workspace_bytes", "apsp_predecessors",
            "apsp_probe_minplus", "apsp_trace_enable", "apsp_trace_read", "apsp_launch_count",
            "apsp_batched_workspace_bytes", "apsp_batched_staged_workspace_bytes", "apsp_solve_host",
-           "apsp_batched_host_workspace_bytes", "apsp_batched_host",
+           "apsp_batched_host_workspace_bytes", "apsp_batched_host", "apsp_host_alloc", "apsp_host_free",
            "apsp_batched", "apsp_mlp_param_count", "apsp_mlp_backward_workspace_bytes", "apsp_mlp_forward",
            "apsp_mlp_loss", "apsp_mlp_backward", "apsp_mlp_adam")
 
@@ -326,9 +329,11 @@ class Batch:
         host = np.zeros(max(total, 4), dtype=dt)
         for m, o, n, ld in zip(mats, self.offsets, self.ns, self.lds):
             host[o:o + n * ld].reshape(n, ld)[:, :n] = m
-        self.host = torch.from_numpy(host)
-        if pin:
-            self.host = self.host.pin_memory()
+        if pin:  # page-locked (huge pages when large) for full-rate copies
+            self.host = host_empty(host.shape, torch.int32 if dt == np.int32 else torch.float32)
+            self.host.numpy()[:] = host
+        else:
+            self.host = torch.from_numpy(host)
         self.dtype = self.host.dtype
         self.pool = self.host.to(dev, non_blocking=True)
         self.d_offsets = torch.from_numpy(self.offsets).to(dev)
@@ -425,7 +430,7 @@ def apsp_batched_host(batch: Batch, host_in=None, host_out=None, chunks: int = 4
     src = batch.host if host_in is None else host_in
     if src.is_cuda or src.numel() < batch.pool.numel() or not src.is_contiguous():
         raise ValueError("host_in must be a contiguous CPU tensor laid out like batch.host")
-    out = torch.empty_like(src).pin_memory() if host_out is None else host_out
+    out = host_empty(tuple(src.shape), src.dtype) if host_out is None else host_out
     if out.is_cuda or out.numel() < batch.pool.numel() or not out.is_contiguous():
         raise ValueError("host_out must be a contiguous CPU tensor laid out like batch.host")
     code = _dtype_code(batch.pool)
@@ -482,6 +487,25 @@ def apsp_mlp_adam(params, grads, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-
 ALGOS = {"fw": apsp_fw, "rkleene": apsp_rkleene, "squaring": apsp_squaring}
 
 
+_NP_OF = {torch.int32: np.int32, torch.float32: np.float32, torch.int64: np.int64, torch.uint8: np.uint8}
+
+
+def host_empty(shape, dtype=torch.int32) -> torch.Tensor:
+    """A page-locked host tensor from apsp_host_alloc (huge pages for large buffers, which keep
+    host-device copies at full rate after large closures); freed when the last tensor or array
+    viewing it is garbage-collected."""
+    npdt = np.dtype(_NP_OF[dtype])
+    shape = tuple(int(x) for x in (shape if isinstance(shape, (tuple, list)) else (shape,)))
+    count = int(np.prod(shape)) if shape else 1
+    nbytes = max(1, count * npdt.itemsize)
+    p = _lib.apsp_host_alloc(nbytes)
+    if not p:
+        raise MemoryError(f"apsp_host_alloc({nbytes}) failed")
+    arr = np.frombuffer((ctypes.c_byte * nbytes).from_address(p), dtype=npdt, count=count).reshape(shape)
+    weakref.finalize(arr, _lib.apsp_host_free, p)
+    return torch.from_numpy(arr)
+
+
 def solve(h, algo: str = "fw", inf=None, param: int = 0, device=None, out=None, predecessors: bool = False):
     """End-to-end solve of a HOST cost matrix (numpy array or CPU tensor): copy it to the
     device, close it there, copy the distances back.  Returns a CPU tensor (``out`` if given,
@@ -506,7 +530,7 @@ def solve(h, algo: str = "fw", inf=None, param: int = 0, device=None, out=None, 
     n = t.shape[0]
     code = _dtype_code(t)
     if out is None:
-        out = torch.empty_like(t)
+        out = host_empty(tuple(t.shape), t.dtype)
     elif out.is_cuda or out.dtype != t.dtype or tuple(out.shape) != (n, n) or not out.is_contiguous():
         raise ValueError("out must be a contiguous host tensor of h's shape and dtype")
     ip, _keep = _inf_arg(inf, code)

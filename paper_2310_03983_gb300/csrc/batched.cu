@@ -520,6 +520,7 @@ struct RestCtx {
   apsp::BatchArgs a;
   bool clusters;
   cudaStream_t s;
+  bool is_float;
 };
 
 // The persistent kernel over a sub-list of the batch (the graphs the staged path leaves out).
@@ -528,7 +529,7 @@ int launch_rest_graphs(void *ctx, const int *order, int64_t nq) {
   apsp::BatchArgs a = c->a;
   a.order = order;
   a.nq = nq;
-  return apsp::launch_batched<int>(a, c->clusters, c->s);
+  return c->is_float ? apsp::launch_batched<float>(a, c->clusters, c->s) : apsp::launch_batched<int>(a, c->clusters, c->s);
 }
 
 }  // namespace
@@ -540,8 +541,8 @@ extern "C" size_t apsp_batched_workspace_bytes(int64_t count) {
 
 extern "C" size_t apsp_batched_staged_workspace_bytes(const int32_t *ns_host, int64_t count, int dtype) {
   apsp::StagePlan pl;
-  if (dtype != APSP_I32 || !apsp::make_stage_plan(ns_host, count, pl)) return 256;
-  return apsp::staged_workspace_bytes(pl, count);
+  if (!apsp::dtype_ok(dtype) || !apsp::make_stage_plan(ns_host, count, pl)) return 256;
+  return apsp::staged_workspace_bytes(pl, count, dtype);
 }
 
 extern "C" int apsp_batched(void *pool, const int64_t *offsets, const int32_t *ns, const int32_t *lds,
@@ -574,15 +575,15 @@ extern "C" int apsp_batched(void *pool, const int64_t *offsets, const int32_t *n
   int r = APSP_OK;
   if (cudaMemsetAsync(a.queue, 0, 2 * sizeof(int), s) != cudaSuccess) r = APSP_ERR_CUDA;
   // Graphs of 257..2048 vertices go through the engine in lockstep when the workspace has room
-  // for the staging (int32, a sentinel above the 16-bit cap).
+  // for the staging (int32 with a sentinel above the 16-bit cap, or float32).
   StagePlan pl;
-  if (!r && !own && dtype == APSP_I32 && a.inf_i > kCap16 && make_stage_plan(ns_host, count, pl) &&
-      ws_bytes >= staged_workspace_bytes(pl, count)) {
+  if (!r && !own && (dtype == APSP_F32 || a.inf_i > kCap16) && make_stage_plan(ns_host, count, pl) &&
+      ws_bytes >= staged_workspace_bytes(pl, count, dtype)) {
     std::vector<int32_t> rest_ns;
     rest_ns.reserve(pl.rest.size());
     for (int g : pl.rest) rest_ns.push_back(ns_host[g]);
-    RestCtx ctx = {a, needs_clusters(rest_ns.data(), (int64_t)rest_ns.size()), s};
-    r = batched_staged(pl, a.pool, offsets, ns, lds, count, a.inf_i, ws, launch_rest_graphs, &ctx, s);
+    RestCtx ctx = {a, needs_clusters(rest_ns.data(), (int64_t)rest_ns.size()), s, dtype == APSP_F32};
+    r = batched_staged(pl, a.pool, offsets, ns, lds, count, dtype, a.inf_i, a.inf_f, ws, launch_rest_graphs, &ctx, s);
     return r;
   }
   const bool clusters = needs_clusters(ns_host, count);

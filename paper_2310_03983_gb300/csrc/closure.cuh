@@ -6,10 +6,17 @@
 namespace apsp {
 
 // Device bound words of a closure (see TileProblem::wmax): w[0] = largest finite weight,
-// mult = n - 1 of the whole graph.  w == nullptr for float32.
+// mult = n - 1 of the whole graph.  w == nullptr for float32.  cert (may be null: then w[0])
+// is the largest finite entry of the block this closure starts from, the step bound of the
+// truncated passes' certificates: an R-Kleene leaf starts from path lengths, not from edge
+// weights, so its own scan gives it.
 struct Bound {
   const int *w;
   int64_t mult;
+  const int *cert = nullptr;
+  // Two device words, zero at the start: the tile counters of phase 3's dynamic scheduling
+  // (TileProblem::tile_counter; null: static order, and phase 1 in its own launch).
+  int *counters = nullptr;
 };
 
 // Blocked Floyd-Warshall on an aligned, normalised block (fw.cu).  panels16: scratch of

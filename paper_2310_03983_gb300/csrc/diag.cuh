@@ -48,10 +48,21 @@ __device__ __forceinline__ int canon(int v, const SignedCtl *sc) {
   return v >= sc->thr ? sc->inf : v;
 }
 
+// The barrier among the 256 threads that hold a tile: the whole CTA (BAR = 0), or named barrier
+// BAR over 256 threads, when the tile's threads are part of a larger CTA (the GEMM engine's
+// consumer warps).
+template <int BAR>
+__device__ __forceinline__ void tile_barrier() {
+  if (BAR == 0)
+    __syncthreads();
+  else
+    asm volatile("bar.sync %0, 256;" ::"n"(BAR) : "memory");
+}
+
 // Closes the bk x bk leading part of the register tile d in place.  buf: 512 ints of shared
 // memory.  Entries outside bk x bk are scratch (never read back by callers).  With sc (signed
 // closures) returns true when a negative cycle was found (the tile is then left partly closed).
-template <bool FLOAT>
+template <bool FLOAT, int BAR = 0>
 __device__ bool close_tile_regs(int (&d)[8][8], int bk, int tm, int tn, int *buf, const SignedCtl *sc = nullptr) {
   bool negative = false;
 #pragma unroll
@@ -87,7 +98,7 @@ __device__ bool close_tile_regs(int (&d)[8][8], int bk, int tm, int tn, int *buf
           default: put_col<7>(d, cb, tm); break;
         }
       }
-      __syncthreads();
+      tile_barrier<BAR>();
       if (sc) {  // d[k][k] sits in the published row at column k
         const int dkk = rb[k];
         if (FLOAT ? __int_as_float(dkk) < 0.0f : dkk < 0) {
@@ -110,7 +121,7 @@ __device__ bool close_tile_regs(int (&d)[8][8], int bk, int tm, int tn, int *buf
         for (int j = 0; j < 8; ++j) d[i][j] = relax<FLOAT>(d[i][j], c[i], r[j]);
     }
   }
-  __syncthreads();  // buf is reused by the caller
+  tile_barrier<BAR>();  // buf is reused by the caller
   return negative;
 }
 

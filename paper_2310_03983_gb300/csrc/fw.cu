@@ -59,10 +59,28 @@ int launch_fw_diag(void *d, int64_t ld, int64_t n, int64_t kb, int dtype, cudaSt
 // is unreachable and becomes the sentinel, which gives the exact closure.  Otherwise (checked
 // on the device) the same mapping leaves a matrix whose entries lie between the distances and
 // the weights (every edge is below CAP), and the int32 Floyd-Warshall runs again over it.
+//
+// The same argument holds for a second cap, 2^24, with the fp32 instruction sequence on int32 bit
+// patterns (ArithF32).  A pattern v < 2^24 read as fp32 is v * 2^-149; two such values add
+// exactly while their sum stays below 2^24, and otherwise round to a value whose pattern is at
+// least 2^24 (rounding is monotone, and every larger pattern is a larger float), so
+// t(computed sum) = t(exact sum) with t(v) = min(v, 2^24), and min is exact.  An int32 closure
+// whose weights are too large for the 16-bit pass and for the exact bound ((n - 1) w_max < 2^24)
+// but at most 2^24 / 4 therefore runs phase 3 with that sequence (phases 1 and 2 stay exact), is
+// certified in the same way, and only when the certificate fails runs the exact int32 pass.
+//
+// One pass does the work in every case: per block, phases 1 and 2 (exact), then one phase-3
+// launch that runs on the packed 16-bit panels, or -- decided on the device -- its 32-bit
+// alternative over the matrix's own panels (fp32 sequence when exact or truncated at 2^24,
+// else int32).  Then one certificate for the cap in use, and the exact int32 pass, whose
+// launches return at once unless that certificate failed.
 // Words of the bound block used here:
-//   [0] largest finite weight (a1), [4] 16-bit phase 3 in use, [5] largest stored value < CAP,
-//   [6] the int32 pass must run again.
+//   [0] largest finite weight (a1), [4] 16-bit phase 3 in use, [5] largest stored value below
+//   the cap in use, [6] the exact int32 pass must run, [7] phase 3 runs its 32-bit alternative,
+//   [16] that alternative is truncated at 2^24.
 constexpr int kUse16MaxWeight = kCap16 / 4;
+constexpr int kCap24 = 1 << 24;
+constexpr int kUse24MaxWeight = kCap24 / 4;
 // From kFw16WideN vertices the 16-bit pass works on diagonal blocks of two tiles (256 vertices):
 // phase 3 then has K = 256 (128 packed words) per launch, which halves the per-tile epilogue and
 // C traffic per pair, at the price of a heavier phase 1 and 2 per block (a 2 x 2-tile closure,
@@ -72,10 +90,16 @@ constexpr int64_t kFw16Block = kFw16Tiles * kBM;
 constexpr int kFw16Words = (int)(kFw16Block / 2);
 constexpr int64_t kFw16WideN = 16384;
 
-__global__ void fw16_decide_kernel(int *words) {
-  words[4] = words[0] <= kUse16MaxWeight;
+// w = words[0]: the largest weight of the whole graph (the exact bound); c = *cert: the largest
+// finite entry of the block being closed (the certificates' step bound).
+__global__ void fw_decide_kernel(int *words, const int *cert, int may24, int64_t mult) {
+  const int w = words[0], c = *cert;
+  const int use16 = c <= kUse16MaxWeight;
+  words[4] = use16;
   words[5] = 0;
-  words[6] = !words[4];  // without the 16-bit pass the int32 pass does all the work
+  words[6] = 0;
+  words[7] = !use16;
+  words[16] = !use16 && may24 && (int64_t)w * mult >= kCap24 && c <= kUse24MaxWeight;
 }
 
 // Packs the column panel D[:, kb0 .. kb0+bw) into A16 (n rows x kFw16Words words) and the row
@@ -105,25 +129,42 @@ __global__ void __launch_bounds__(256) fw_pack16_kernel(const int *d, int64_t ld
   }
 }
 
-// words[5] = largest stored value below CAP, and every entry at or above CAP becomes the
-// sentinel; then words[6] = 1 when words[5] plus the largest weight reaches CAP (the truncated
-// result cannot be certified).
-__global__ void __launch_bounds__(256) fw16_certify_kernel(int *d, int64_t ld, int64_t n, int inf, int *words) {
-  if (!words[4]) return;
+// The cap of the truncated computation in use (0: none, the closure is exact).
+__device__ __forceinline__ int cap_in_use(const int *words) {
+  return words[4] ? kCap16 : (words[16] ? kCap24 : 0);
+}
+
+// words[5] = largest stored value below the cap in use, and every entry at or above it becomes
+// the sentinel (nothing when the closure ran exact).
+__global__ void __launch_bounds__(256) trunc_certify_kernel(int *d, int64_t ld, int64_t n, int inf, int *words) {
+  const int cap = cap_in_use(words);
+  if (!cap) return;
   int m = 0;
   for (int64_t i = blockIdx.x; i < n; i += gridDim.x)
     for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
       int *e = d + i * ld + j;
       const int v = *e;
-      if (v < kCap16) m = max(m, v);
+      if (v < cap) m = max(m, v);
       else if (v != inf) *e = inf;
     }
   m = __reduce_max_sync(0xffffffffu, m);
   if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(words + 5, m);
 }
 
-__global__ void fw16_verdict_kernel(int *words) {
-  if (words[4]) words[6] = (int64_t)words[5] + (int64_t)words[0] >= kCap16;
+// words[6] = 1 when the largest stored value below the cap plus the step bound *cert reaches the
+// cap (the truncated result cannot be certified).
+__global__ void trunc_verdict_kernel(int *words, const int *cert) {
+  const int cap = cap_in_use(words);
+  words[6] = cap && (int64_t)words[5] + (int64_t)*cert >= cap;
+}
+
+static int certify(void *d, int64_t ld, int64_t n, int inf, int *words, const int *cert, cudaStream_t s) {
+  const int64_t grid = std::min<int64_t>(n, (int64_t)sm_count() * 8);
+  trunc_certify_kernel<<<(int)grid, 256, 0, s>>>(reinterpret_cast<int *>(d), ld, n, inf, words);
+  APSP_LAUNCH_CHECK();
+  trunc_verdict_kernel<<<1, 1, 0, s>>>(words, cert);
+  APSP_LAUNCH_CHECK();
+  return APSP_OK;
 }
 
 // Scratch of the 16-bit pass: the packed column and row panels, and copies of the int32 row and
@@ -135,27 +176,42 @@ size_t fw16_panel_bytes(int64_t n) {
 }
 
 // The plain three-phase loop; every launch returns at once unless *run_if (when given) is set.
+// trace_class: added to the engine mode in trace records (kTraceFallback for passes that
+// normally return at once, and for the small sub-closures of the wide pass).
+// counters (may be null): phase 3 hands out its tiles dynamically and closes the next diagonal
+// tile itself (TileProblem::close_next), so phase 1 has a launch of its own only for block 0.
 static int fw_loop(void *d, int64_t n, int64_t ld, int dtype, const CUtensorMap &mA, const CUtensorMap &mB,
-                   const CUtensorMap &mC, TileProblem p, const int *run_if, cudaStream_t s) {
+                   const CUtensorMap &mC, TileProblem p, const int *run_if, cudaStream_t s, int trace_class = 0,
+                   int *counters = nullptr) {
   int r;
   const int64_t nb = p.nb;
   p.run_if = run_if;
-  p.no_trace = run_if != nullptr;
+  p.trace_class = trace_class;
   for (int64_t kb = 0; kb < nb; ++kb) {
-    if ((r = launch_fw_diag(d, ld, n, kb, dtype, s, run_if))) return r;
+    if ((kb == 0 || !counters) && (r = launch_fw_diag(d, ld, n, kb, dtype, s, run_if))) return r;
     if (nb == 1) break;
     p.kb = kb;
     p.ntiles = 2 * (nb - 1);
+    p.tile_counter = nullptr;
+    p.close_next = 0;
     if ((r = launch_tgemm(kModeFwPanels, false, dtype, mA, mB, mC, p, s))) return r;
     p.ntiles = (nb - 1) * (nb - 1);
+    p.tile_counter = counters;
+    p.close_next = counters && kb + 1 < nb;
     if ((r = launch_tgemm(kModeFwRest, true, dtype, mA, mB, mC, p, s))) return r;
   }
   return APSP_OK;
 }
 
+static int fw_wide_pass(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bound b, cudaStream_t s,
+                        void *panels16, const TileProblem &p, const CUtensorMap &mA, const CUtensorMap &mB,
+                        const CUtensorMap &mC);
+
 // Closes the n x n block at d (16-byte aligned, ld % 4 == 0, already normalised) in place.
-// panels16 (may be null): fw16_panel_bytes(n) of device scratch; with it, an int32 closure
-// whose largest weight is at most CAP / 4 runs phase 3 on packed 16-bit pairs (above).
+// panels16 (may be null): fw16_panel_bytes(n) of device scratch; with it an int32 closure runs
+// the pass above: phase 3 on packed 16-bit pairs when its largest weight (step) is at most
+// CAP / 4, else its 32-bit alternative (truncated at 2^24 when allowed), then the certificate
+// and the exact pass if needed.
 int fw_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bound b, cudaStream_t s, void *panels16) {
   if (n == 0) return APSP_OK;
   CUtensorMap mA, mB, mC;
@@ -172,12 +228,23 @@ int fw_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bound b, cu
   p.wmax = b.w;
   p.wmult = b.mult;
   if (!(panels16 && dtype == APSP_I32 && b.w && nb > 1 && inf_i > kCap16))
-    return fw_loop(d, n, ld, dtype, mA, mB, mC, p, nullptr, s);
-
-  // The 16-bit pass, over diagonal blocks of kFw16Block vertices; every launch returns at once
-  // unless words[4] (decided on the device from the largest weight) is set.
+    return fw_loop(d, n, ld, dtype, mA, mB, mC, p, nullptr, s, 0, b.counters);
   int *words = const_cast<int *>(b.w);
-  const int *use16 = words + 4;
+  const int *cert = b.cert ? b.cert : b.w;
+  fw_decide_kernel<<<1, 1, 0, s>>>(words, cert, inf_i > kCap24, b.mult);
+  APSP_LAUNCH_CHECK();
+  if ((r = fw_wide_pass(d, n, ld, dtype, inf_i, b, s, panels16, p, mA, mB, mC))) return r;
+  if ((r = certify(d, ld, n, inf_i, words, cert, s))) return r;
+  return fw_loop(d, n, ld, dtype, mA, mB, mC, p, words + 6, s, kTraceFallback, b.counters);
+}
+
+// The pass over diagonal blocks of bt = 1 or 2 tiles: phases 1 and 2 exact, the block's panels
+// packed (when words[4]), phase 3 on them or on the 32-bit alternative (words[7]).
+static int fw_wide_pass(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bound b, cudaStream_t s,
+                        void *panels16, const TileProblem &p, const CUtensorMap &mA, const CUtensorMap &mB,
+                        const CUtensorMap &mC) {
+  int r;
+  int *words = const_cast<int *>(b.w);
   const int64_t ldp = round_up(n, 4);
   uint8_t *sp = reinterpret_cast<uint8_t *>(panels16);
   int *A16 = reinterpret_cast<int *>(sp);
@@ -190,8 +257,6 @@ int fw_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bound b, cu
   CUtensorMap pA, pB;
   if ((r = make_operand_maps(A16, n, kFw16Words, kFw16Words, APSP_I32, &pA, nullptr, nullptr))) return r;
   if ((r = make_operand_maps(B16, kFw16Words, n, ldp, APSP_I32, nullptr, &pB, nullptr))) return r;
-  fw16_decide_kernel<<<1, 1, 0, s>>>(words);
-  APSP_LAUNCH_CHECK();
   const int64_t cap = (int64_t)sm_count() * 8;
   const int64_t bt = n >= kFw16WideN ? kFw16Tiles : 1, blk = bt * kBM;
   const int64_t nbb = cdiv(n, blk), nt = cdiv(n, kBM);
@@ -199,13 +264,13 @@ int fw_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bound b, cu
   for (int64_t kbb = 0; kbb < nbb; ++kbb) {
     const int64_t kb0 = kbb * blk, bw = std::min<int64_t>(blk, n - kb0);
     int *sub = D + kb0 * ld + kb0, *rowp = D + kb0 * ld, *colp = D + kb0;
-    if (bt == 1) {  // phases 1 and 2 of a single-tile block, in place (as in the plain loop)
-      if ((r = launch_fw_diag(d, ld, n, kbb, dtype, s, use16))) return r;
+    if (bt == 1) {  // phases 1 and 2 of a single-tile block, in place (as in the plain loop); with
+                    // counters, phase 1 of every block after the first ran in the previous phase 3
+      if ((kbb == 0 || !b.counters) && (r = launch_fw_diag(d, ld, n, kbb, dtype, s, nullptr))) return r;
       TileProblem pp = p;
       pp.kb = kbb;
       pp.ntiles = 2 * (nt - 1);
-      pp.run_if = use16;
-      pp.no_trace = 1;
+      pp.trace_class = kTraceFallback;
       if ((r = launch_tgemm(kModeFwPanels, false, dtype, mA, mB, mC, pp, s))) return r;
     } else {
       // Phase 1: close the diagonal block (itself a small blocked Floyd-Warshall, exact).
@@ -215,20 +280,16 @@ int fw_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bound b, cu
       ps.n = bw;
       ps.nb = cdiv(bw, kBM);
       ps.C = sub;
-      if ((r = fw_loop(sub, bw, ld, dtype, dA, dB, dC, ps, use16, s))) return r;
+      if ((r = fw_loop(sub, bw, ld, dtype, dA, dB, dC, ps, nullptr, s, kTraceFallback))) return r;
       // Phase 2: the row panel becomes D* (x) (row panel) and the column panel (column panel) (x)
       // D*, each one exact product (D* is closed, so its zero diagonal keeps the old entry) read
       // from a copy of the panel; the block's own entries are reproduced (D* (x) D* = D*).
-      if ((r = launch_copy2d(Rc, ldp, rowp, ld, bw, n, s, use16))) return r;
-      if ((r = gemm_aligned(rowp, ld, sub, ld, Rc, ldp, bw, n, bw, dtype, false, inf_i, b, s,
-                            {nullptr, nullptr, 0}, use16)))
-        return r;
-      if ((r = launch_copy2d(Cc, kFw16Block, colp, ld, n, bw, s, use16))) return r;
-      if ((r = gemm_aligned(colp, ld, Cc, kFw16Block, sub, ld, n, bw, bw, dtype, false, inf_i, b, s,
-                            {nullptr, nullptr, 0}, use16)))
-        return r;
+      if ((r = launch_copy2d(Rc, ldp, rowp, ld, bw, n, s))) return r;
+      if ((r = gemm_aligned(rowp, ld, sub, ld, Rc, ldp, bw, n, bw, dtype, false, inf_i, b, s))) return r;
+      if ((r = launch_copy2d(Cc, kFw16Block, colp, ld, n, bw, s))) return r;
+      if ((r = gemm_aligned(colp, ld, Cc, kFw16Block, sub, ld, n, bw, bw, dtype, false, inf_i, b, s))) return r;
     }
-    // Phase 3 on the packed panels, K = bw.
+    // Phase 3, K = bw: on the packed panels, or the 32-bit alternative.
     const int64_t work = 2 * n * ((bw + 1) >> 1);
     fw_pack16_kernel<<<(int)std::min<int64_t>(cap, cdiv(work, 256)), 256, 0, s>>>(D, ld, n, kb0, (int)bw, A16, B16,
                                                                                   ldp, words);
@@ -240,18 +301,19 @@ int fw_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bound b, cu
     q.bt = (int)bt;
     q.ntiles = rest * rest;
     q.arith16 = 1;
-    q.run_if = use16;
+    q.alt_if = words + 7;
+    q.f32_if = words + 16;
     q.no_trace = 1;
+    if (bt == 1) {
+      q.tile_counter = b.counters;
+      q.close_next = b.counters && kbb + 1 < nbb;
+    }
     void *tev = nullptr;
     if (trace_on()) trace_begin(s, &tev);
-    if ((r = launch_tgemm(kModeFwRest16, true, dtype, pA, pB, mC, q, s))) return r;
+    if ((r = launch_tgemm(kModeFwRest16, true, dtype, pA, pB, mC, q, s, &mA, &mB))) return r;
     if (tev) trace_end(s, tev, kModeFwRest, (double)(n - bw) * (double)(n - bw) * (double)bw);
   }
-  fw16_certify_kernel<<<(int)std::min<int64_t>(n, cap), 256, 0, s>>>(reinterpret_cast<int *>(d), ld, n, inf_i, words);
-  APSP_LAUNCH_CHECK();
-  fw16_verdict_kernel<<<1, 1, 0, s>>>(words);
-  APSP_LAUNCH_CHECK();
-  return fw_loop(d, n, ld, dtype, mA, mB, mC, p, words + 6, s);
+  return APSP_OK;
 }
 
 // Shared entry logic of apsp_fw and apsp_rkleene: validation, the workspace (caller's or
@@ -288,7 +350,8 @@ int closure_entry(int algo, void *d, int64_t n, int64_t ld, int dtype, const voi
   int *words = reinterpret_cast<int *>(wsp);  // [0]: largest finite weight, [1]: 0
   wsp += kFlagBytes;
   if (cudaMemsetAsync(words, 0, 16, s) != cudaSuccess) r = APSP_ERR_CUDA;
-  const Bound bound = {dtype == APSP_I32 ? words : nullptr, n - 1};
+  Bound bound = {dtype == APSP_I32 ? words : nullptr, n - 1};
+  bound.counters = words + 2;  // zeroed with the bound words above
   void *work = d;
   int64_t ldw = ld;
   if (ld % 4 != 0) {  // repack into an aligned copy at the front of the workspace

@@ -27,6 +27,9 @@
 // weights; that pass's launches return at once when no graph needs it.  Results are identical
 // to closing each graph alone.
 //
+// Float32 batches stage the same way (the sentinel and the padding are +infinity) and run only
+// the second pass, in fp32 (the engine's packed pair add and 3-input min), with no certificate.
+//
 // The plan (which graphs, their order and rows) is made on the host from the host copy of the
 // sizes and reaches the device as kernel arguments, so the whole sequence can be captured in a
 // CUDA graph.  Graphs whose device size, leading dimension or offset disagree with the plan are
@@ -70,7 +73,9 @@ struct StageArgs {
   const int32_t *ns, *lds;
   const int *sidx;
   int *gflags, *maxb, *wmaxg, *gsize, *words;
-  int inf;
+  int inf;       // int32: the sentinel; float32: the bits of +infinity (what staging writes)
+  float inf_f;   // float32: the caller's sentinel (entries at or above it are missing edges)
+  int is_float;
   unsigned int *status;
 };
 
@@ -119,9 +124,26 @@ __device__ __forceinline__ bool graph_ok(const StageArgs &a, int g, int nb, int 
   return n > 0 && ld >= n && !(ld & 3) && !(off & 3) && off >= 0 && (n + kBM - 1) / kBM == nb;
 }
 
+// One entry of a1 (column c of row i): the diagonal becomes 0, an entry at or above the
+// sentinel becomes a.inf (int32: the sentinel; float32: +infinity), a negative entry (float32:
+// or NaN) is flagged.  m keeps the largest finite int32 weight.
+__device__ __forceinline__ int stage_entry(const StageArgs &a, int x, int c, int i, bool &bad, int &m) {
+  if (c == i) return 0;
+  if (a.is_float) {
+    const float f = __int_as_float(x);
+    bad |= !(f >= 0.f);
+    if (f == 0.f) return 0;  // -0 stored as +0
+    return f >= a.inf_f ? a.inf : x;
+  }
+  bad |= x < 0;
+  x = x >= a.inf ? a.inf : x;
+  if (x < a.inf) m = max(m, x);
+  return x;
+}
+
 // a1 into the staging matrix, one warp per staged row: zero diagonal, entries >= inf become
 // inf, negative entries flag APSP_ERR_DOMAIN; padding rows and columns are isolated vertices.
-// The largest finite weight of each graph is maxed into wmaxg[q].
+// The largest finite weight of each int32 graph is maxed into wmaxg[q].
 __global__ void __launch_bounds__(256) stage_in_kernel(const StageArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -162,17 +184,7 @@ __global__ void __launch_bounds__(256) stage_in_kernel(const StageArgs a) {
         }
       }
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        int x = (&v.x)[e];
-        if (c + e == i) {
-          x = 0;
-        } else {
-          bad |= x < 0;
-          x = x >= a.inf ? a.inf : x;
-          if (x < a.inf) m = max(m, x);
-        }
-        (&v.x)[e] = x;
-      }
+      for (int e = 0; e < 4; ++e) (&v.x)[e] = stage_entry(a, (&v.x)[e], c + e, i, bad, m);
       *reinterpret_cast<int4 *>(dst + c) = v;
     }
     m = __reduce_max_sync(0xffffffffu, m);
@@ -182,12 +194,18 @@ __global__ void __launch_bounds__(256) stage_in_kernel(const StageArgs a) {
 }
 
 // Per graph: the 16-bit pass is used when the largest weight is at most CAP / 4 (else the
-// int32 pass does all the work), and the bound word for exact fp32 arithmetic.
+// int32 pass does all the work), and the bound word for exact fp32 arithmetic.  Float32
+// graphs all take the second pass.
 __global__ void stage_decide_kernel(const StageArgs a, int64_t G) {
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < G; q += (int64_t)gridDim.x * blockDim.x) {
     if (a.gflags[q] & kGfBad) continue;
     const int w = a.wmaxg[q], n = a.ns[a.sidx[q]];
     a.gsize[q] = n;
+    if (a.is_float) {
+      a.gflags[q] |= kGfRerun;
+      a.words[kWRerun] = 1;
+      continue;
+    }
     const int64_t prod = (int64_t)(n - 1) * (int64_t)w;
     atomicMax(a.words + kWBound, (int)(prod < INT_MAX ? prod : INT_MAX));
     if (w <= kCap16 / 4) {
@@ -275,7 +293,7 @@ __device__ void close_tile_regs16(int (&w)[8][4], int bk, int tm, int tn, int *b
 // step's packed column and row panels is written to pa / pb.
 __global__ void __launch_bounds__(256, 2) group_diag_kernel(int *S, int64_t ldS, GroupSet gs, int kb, const int *gflags,
                                                          const int *gsize, int mask, int want, const int *run_if,
-                                                         bool truncated, int *pa, int *pb) {
+                                                         bool truncated, int *pa, int *pb, bool is_float) {
   if (run_if && !*run_if) return;
   const int q = blockIdx.x;
   if ((gflags[q] & mask) != want) return;
@@ -305,6 +323,8 @@ __global__ void __launch_bounds__(256, 2) group_diag_kernel(int *S, int64_t ldS,
         r[i][2 * j] = w[i][j] & 0xFFFF;
         r[i][2 * j + 1] = (int)((unsigned)w[i][j] >> 16);
       }
+  } else if (is_float) {
+    close_tile_regs<true>(r, bk, tm, tn, buf);
   } else {
     close_tile_regs<false>(r, bk, tm, tn, buf);
   }
@@ -439,7 +459,7 @@ struct Layout {
   size_t gflags, maxb, wmaxg, gsize, lists, S, A16[2], B16[2], total;
 };
 
-Layout layout_of(const StagePlan &pl, int64_t count) {
+Layout layout_of(const StagePlan &pl, int64_t count, int dtype) {
   Layout L;
   size_t o = kFlagBytes;
   auto take = [&](size_t bytes) {
@@ -454,8 +474,8 @@ Layout layout_of(const StagePlan &pl, int64_t count) {
   L.lists = take((size_t)count * 4);
   L.S = take((size_t)pl.R * pl.NP * 4);
   for (int k = 0; k < 2; ++k) {  // two sets: block step kb reads set kb & 1, writes the other
-    L.A16[k] = take((size_t)pl.R * 64 * 4);
-    L.B16[k] = take((size_t)pl.G * 64 * pl.NP * 4);
+    L.A16[k] = dtype == APSP_I32 ? take((size_t)pl.R * 64 * 4) : 0;
+    L.B16[k] = dtype == APSP_I32 ? take((size_t)pl.G * 64 * pl.NP * 4) : 0;
   }
   L.total = o;
   return L;
@@ -522,12 +542,15 @@ bool make_stage_plan(const int32_t *ns_host, int64_t count, StagePlan &pl) {
   return true;
 }
 
-size_t staged_workspace_bytes(const StagePlan &pl, int64_t count) { return layout_of(pl, count).total; }
+size_t staged_workspace_bytes(const StagePlan &pl, int64_t count, int dtype) {
+  return layout_of(pl, count, dtype).total;
+}
 
 int batched_staged(const StagePlan &pl, int *pool, const int64_t *offsets, const int32_t *ns, const int32_t *lds,
-                   int64_t count, int inf_i, void *ws, int (*launch_rest)(void *ctx, const int *order, int64_t nq),
-                   void *ctx, cudaStream_t s) {
-  const Layout L = layout_of(pl, count);
+                   int64_t count, int dtype, int inf_i, float inf_f, void *ws,
+                   int (*launch_rest)(void *ctx, const int *order, int64_t nq), void *ctx, cudaStream_t s) {
+  const bool isf = dtype == APSP_F32;
+  const Layout L = layout_of(pl, count, dtype);
   uint8_t *w = reinterpret_cast<uint8_t *>(ws);
   int *words = reinterpret_cast<int *>(w);
   StageArgs a = {};
@@ -547,7 +570,9 @@ int batched_staged(const StagePlan &pl, int *pool, const int64_t *offsets, const
   a.wmaxg = reinterpret_cast<int *>(w + L.wmaxg);
   a.gsize = reinterpret_cast<int *>(w + L.gsize);
   a.words = words;
-  a.inf = inf_i;
+  a.inf = isf ? 0x7f800000 : inf_i;
+  a.inf_f = inf_f;
+  a.is_float = isf;
   a.status = status_word();
   int *A16[2] = {reinterpret_cast<int *>(w + L.A16[0]), reinterpret_cast<int *>(w + L.A16[1])};
   int *B16[2] = {reinterpret_cast<int *>(w + L.B16[0]), reinterpret_cast<int *>(w + L.B16[1])};
@@ -571,8 +596,8 @@ int batched_staged(const StagePlan &pl, int *pool, const int64_t *offsets, const
   APSP_LAUNCH_CHECK();
 
   CUtensorMap mA, mB, mC, pA[2], pB[2];
-  if ((r = make_operand_maps(a.S, pl.R, pl.NP, pl.NP, APSP_I32, &mA, &mB, &mC))) return r;
-  for (int k = 0; k < 2; ++k) {
+  if ((r = make_operand_maps(a.S, pl.R, pl.NP, pl.NP, dtype, &mA, &mB, &mC))) return r;
+  for (int k = 0; k < 2 && !isf; ++k) {
     if ((r = make_operand_maps(A16[k], pl.R, 64, 64, APSP_I32, &pA[k], nullptr, nullptr))) return r;
     if ((r = make_operand_maps(B16[k], pl.G * 64, pl.NP, pl.NP, APSP_I32, nullptr, &pB[k], nullptr))) return r;
   }
@@ -581,8 +606,9 @@ int batched_staged(const StagePlan &pl, int *pool, const int64_t *offsets, const
   p.C = a.S;
   p.ldc = pl.NP;
   p.inf_i = inf_i;
+  p.inf_f = inf_f;
   p.status = status_word();
-  p.wmax = words + kWBound;  // (n - 1) * largest weight over every staged graph, then 0
+  p.wmax = isf ? nullptr : words + kWBound;  // (n - 1) * largest weight over every staged graph, then 0
   p.wmult = 1;
   p.bt = 1;
   p.ngroups = pl.ngroups;
@@ -593,7 +619,7 @@ int batched_staged(const StagePlan &pl, int *pool, const int64_t *offsets, const
 
   // Pass 1: graphs of the 16-bit pass.  Per block: the diagonal tile (exact), the packed
   // panels, phase 2 on them (truncated), the panels packed again, phase 3 (truncated).
-  for (int kb = 0; kb < max_nb; ++kb) {
+  for (int kb = 0; kb < max_nb && !isf; ++kb) {
     int64_t open = 0, panels = 0, rest = 0;
     double panel_pairs = 0.0, rest_pairs = 0.0;  // (min,+) pairs by definition, k to each graph's size
     for (int k = 0; k < pl.ngroups; ++k) {
@@ -613,7 +639,7 @@ int batched_staged(const StagePlan &pl, int *pool, const int64_t *offsets, const
     // except at kb = 0, where one packing pass writes them.
     const int cur = kb & 1;
     group_diag_kernel<<<(int)open, 256, 0, s>>>(a.S, pl.NP, a.gs, kb, a.gflags, a.gsize, kGfBad | kGfUse16, kGfUse16,
-                                                nullptr, true, A16[cur], B16[cur]);
+                                                nullptr, true, A16[cur], B16[cur], false);
     APSP_LAUNCH_CHECK();
     if (kb == 0) {
       group_pack16_kernel<<<dim3((unsigned)open, 4), 256, 0, s>>>(a.S, pl.NP, a.gs, kb, a.gflags, A16[0], B16[0]);
@@ -635,34 +661,43 @@ int batched_staged(const StagePlan &pl, int *pool, const int64_t *offsets, const
     q16.trace_pairs = rest_pairs;
     if ((r = launch_tgemm(kModeFwRest16, true, APSP_I32, pA[cur], pB[cur], mC, q16, s))) return r;
   }
-  certify_out_kernel<<<row_grid, 256, 0, s>>>(a);
-  APSP_LAUNCH_CHECK();
-  group_verdict_kernel<<<g_grid, 256, 0, s>>>(a, pl.G);
-  APSP_LAUNCH_CHECK();
+  if (!isf) {
+    certify_out_kernel<<<row_grid, 256, 0, s>>>(a);
+    APSP_LAUNCH_CHECK();
+    group_verdict_kernel<<<g_grid, 256, 0, s>>>(a, pl.G);
+    APSP_LAUNCH_CHECK();
+  }
 
-  // Pass 2: the int32 closure of the graphs that need it (none: every launch returns at once).
-  p.no_trace = 1;
+  // Pass 2: the 32-bit closure of the graphs that need it (int32: none, usually, and then
+  // every launch returns at once; float32: every staged graph).
+  p.no_trace = !isf;
   p.run_if = words + kWRerun;
   p.gmask = kGfBad | kGfRerun;
   p.gwant = kGfRerun;
   p.arith16 = 0;
   for (int kb = 0; kb < max_nb; ++kb) {
     int64_t open = 0, panels = 0, rest = 0;
+    double rest_pairs = 0.0;
     for (int k = 0; k < pl.ngroups; ++k) {
       const int64_t nb = pl.groups[k].nb, c = pl.groups[k].count;
       if (nb <= kb) continue;
       open += c;
       panels += c * 2 * (nb - 1);
       rest += c * (nb - 1) * (nb - 1);
+      for (int64_t g = pl.groups[k].first; g < pl.groups[k].first + c; ++g)
+        rest_pairs += (double)(nb - 1) * (nb - 1) * kBM * kBM *
+                      (double)std::min<int64_t>(kBM, pl.sizes[g] - (int64_t)kb * kBM);
     }
     group_diag_kernel<<<(int)open, 256, 0, s>>>(a.S, pl.NP, a.gs, kb, a.gflags, a.gsize, kGfBad | kGfRerun,
-                                                kGfRerun, words + kWRerun, false, nullptr, nullptr);
+                                                kGfRerun, words + kWRerun, false, nullptr, nullptr, isf);
     APSP_LAUNCH_CHECK();
     p.kb = kb;
     p.ntiles = panels;
-    if ((r = launch_tgemm(kModeFwPanels, false, APSP_I32, mA, mB, mC, p, s))) return r;
+    p.trace_pairs = 0.0;
+    if ((r = launch_tgemm(kModeFwPanels, false, dtype, mA, mB, mC, p, s))) return r;
     p.ntiles = rest;
-    if ((r = launch_tgemm(kModeFwRest, true, APSP_I32, mA, mB, mC, p, s))) return r;
+    p.trace_pairs = rest_pairs;
+    if ((r = launch_tgemm(kModeFwRest, true, dtype, mA, mB, mC, p, s))) return r;
   }
   stage_out_kernel<<<row_grid, 256, 0, s>>>(a);
   APSP_LAUNCH_CHECK();

@@ -26,14 +26,15 @@ struct StagePlan {
 bool make_stage_plan(const int32_t *ns_host, int64_t count, StagePlan &pl);
 
 // Workspace bytes of apsp_batched with the staged path (the 256-byte word block included).
-size_t staged_workspace_bytes(const StagePlan &pl, int64_t count);
+size_t staged_workspace_bytes(const StagePlan &pl, int64_t count, int dtype);
 
 // Enqueues the whole batched closure: the graphs of pl.rest through launch_rest (the
 // persistent kernel, given a device order list of nq entries), the staged graphs in lockstep.
-// ws: staged_workspace_bytes(pl, count) bytes, 256-byte aligned; its first two words (the
-// persistent kernel's queue counters) are zeroed by the caller.  int32 only; inf_i > kCap16.
+// ws: staged_workspace_bytes(pl, count, dtype) bytes, 256-byte aligned; its first two words
+// (the persistent kernel's queue counters) are zeroed by the caller.  int32: inf_i > kCap16;
+// float32: inf_f is the caller's sentinel.
 int batched_staged(const StagePlan &pl, int *pool, const int64_t *offsets, const int32_t *ns, const int32_t *lds,
-                   int64_t count, int inf_i, void *ws, int (*launch_rest)(void *ctx, const int *order, int64_t nq),
-                   void *ctx, cudaStream_t s);
+                   int64_t count, int dtype, int inf_i, float inf_f, void *ws,
+                   int (*launch_rest)(void *ctx, const int *order, int64_t nq), void *ctx, cudaStream_t s);
 
 }  // namespace apsp

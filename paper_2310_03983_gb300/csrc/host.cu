@@ -7,8 +7,13 @@
 // the copy of chunk c - 1 back to the host run while chunk c is closed on the caller's stream.
 // Host-device copies use their own copy engines, so on pinned host memory the step costs about
 // the closure plus one chunk's copies instead of the sum of the three.
+#include <sys/mman.h>
+#include <unistd.h>
+
 #include <algorithm>
 #include <climits>
+#include <cstdio>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -41,6 +46,28 @@ int copy_streams(CopyStreams *cs) {
   *cs = c;
   return APSP_OK;
 }
+
+// --------------------------------------------------------------- huge-page host memory
+// The transparent-huge-page size of this host (the kernel's PMD size), 0 when unknown.
+size_t thp_bytes() {
+  static size_t cached = [] {
+    size_t v = 0;
+    if (FILE *f = std::fopen("/sys/kernel/mm/transparent_hugepage/hpage_pmd_size", "r")) {
+      unsigned long long x = 0;
+      if (std::fscanf(f, "%llu", &x) == 1) v = (size_t)x;
+      std::fclose(f);
+    }
+    return v;
+  }();
+  return cached;
+}
+
+struct HostMapping {
+  void *raw;       // the mmap'ed range (with room to align), or null for cudaHostAlloc memory
+  size_t raw_len;
+};
+std::mutex g_host_mu;
+std::map<void *, HostMapping> g_host_allocs;
 
 struct Chunk {
   int64_t g0, g1;  // graphs [g0, g1)
@@ -81,6 +108,56 @@ std::vector<Chunk> make_chunks(const int64_t *off, const int32_t *ns, const int3
 }  // namespace
 
 }  // namespace apsp
+
+extern "C" void *apsp_host_alloc(size_t bytes) {
+  using namespace apsp;
+  if (bytes == 0) return nullptr;
+  const size_t hp = thp_bytes();
+  void *p = nullptr;
+  HostMapping m = {nullptr, 0};
+  if (hp && bytes >= hp / 4) {
+    const size_t len = (bytes + hp - 1) / hp * hp;
+    void *raw = mmap(nullptr, len + hp, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
+    if (raw != MAP_FAILED) {
+      const uintptr_t base = (reinterpret_cast<uintptr_t>(raw) + hp - 1) / hp * hp;
+      p = reinterpret_cast<void *>(base);
+      madvise(p, len, MADV_HUGEPAGE);  // advice only: small pages still work
+      if (cudaHostRegister(p, len, cudaHostRegisterDefault) != cudaSuccess) {
+        cudaGetLastError();
+        munmap(raw, len + hp);
+        p = nullptr;
+      } else {
+        m = {raw, len + hp};
+      }
+    }
+  }
+  if (!p) {
+    if (cudaHostAlloc(&p, bytes, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+  }
+  std::lock_guard<std::mutex> lk(g_host_mu);
+  g_host_allocs[p] = m;
+  return p;
+}
+
+extern "C" int apsp_host_free(void *p) {
+  using namespace apsp;
+  if (!p) return APSP_OK;
+  HostMapping m;
+  {
+    std::lock_guard<std::mutex> lk(g_host_mu);
+    auto it = g_host_allocs.find(p);
+    if (it == g_host_allocs.end()) return APSP_ERR_ARG;
+    m = it->second;
+    g_host_allocs.erase(it);
+  }
+  if (!m.raw) return cudaFreeHost(p) == cudaSuccess ? APSP_OK : APSP_ERR_CUDA;
+  const int r = cudaHostUnregister(p) == cudaSuccess ? APSP_OK : APSP_ERR_CUDA;
+  munmap(m.raw, m.raw_len);
+  return r;
+}
 
 extern "C" size_t apsp_batched_host_workspace_bytes(const int32_t *ns_host, const int64_t *offsets_host,
                                                     const int32_t *lds_host, int64_t count, int dtype, int chunks) {

@@ -87,12 +87,24 @@ int gemm_aligned(void *C, int64_t ldc, const void *A, int64_t lda, const void *B
 
 static int rk(uint8_t *d, int64_t m, int64_t ld, int dtype, int inf_i, int cutoff, Bound bd, uint8_t *W,
               cudaStream_t s, Packed16 pk) {
-  // Leaves of at least kFw16MinN vertices close with the packed 16-bit phase 3 (certified per
-  // leaf: a leaf's closure is the closure of its induced subgraph); they reuse the product
-  // scratch, which is idle while a leaf runs.
-  if (m <= cutoff)
-    return fw_closure(d, m, ld, dtype, inf_i, bd, s,
-                      (m >= kFw16MinN && pk.scratch && pk.bytes >= fw16_panel_bytes(m)) ? pk.scratch : nullptr);
+  // Leaves of at least kFw16MinN vertices close with the packed 16-bit phase 3, or, when too
+  // heavy for it and for the exact fp32 bound, with phase 3 truncated at 2^24 (each certified per
+  // leaf: a leaf's closure is the closure of the graph its block describes).  A leaf's block holds
+  // path lengths through the vertices closed before it, so the certificates' step bound is the
+  // block's own largest finite entry, scanned into words[32], not the largest edge weight.  The
+  // leaves reuse the product scratch, which is idle while a leaf runs.
+  if (m <= cutoff) {
+    void *p16 = (m >= kFw16MinN && pk.scratch && pk.bytes >= fw16_panel_bytes(m)) ? pk.scratch : nullptr;
+    Bound lb = bd;
+    if (dtype == APSP_I32 && bd.w && p16) {
+      int *lw = const_cast<int *>(bd.w) + 32;
+      if (cudaMemsetAsync(lw, 0, sizeof(int), s) != cudaSuccess) return APSP_ERR_CUDA;
+      int r;
+      if ((r = launch_scan_max(d, m, m, ld, inf_i, lw, s))) return r;
+      lb.cert = lw;
+    }
+    return fw_closure(d, m, ld, dtype, inf_i, lb, s, p16);
+  }
   const int64_t h = split_of(m), r2 = m - h;
   const int64_t es = 4;
   uint8_t *A = d, *B = d + h * es, *C = d + h * ld * es, *D = d + (h * ld + h) * es;

@@ -178,19 +178,22 @@ extern "C" int apsp_trace_read(int mode, double *total_ms, int64_t *launches, do
   double ms = 0, pr = 0;
   int64_t cnt = 0;
   int rc = APSP_OK;
+  std::vector<TraceRec> keep;
   for (auto &t : g_trace) {
+    if (t.mode != mode && mode >= 0) {
+      keep.push_back(t);
+      continue;
+    }
     if (cudaEventSynchronize(t.e1) != cudaSuccess) rc = APSP_ERR_CUDA;
     float e = 0.f;
-    if (t.mode == mode || mode < 0) {
-      if (cudaEventElapsedTime(&e, t.e0, t.e1) != cudaSuccess) rc = APSP_ERR_CUDA;
-      ms += e;
-      pr += t.pairs;
-      ++cnt;
-    }
+    if (cudaEventElapsedTime(&e, t.e0, t.e1) != cudaSuccess) rc = APSP_ERR_CUDA;
+    ms += e;
+    pr += t.pairs;
+    ++cnt;
     cudaEventDestroy(t.e0);
     cudaEventDestroy(t.e1);
   }
-  g_trace.clear();
+  g_trace.swap(keep);
   *total_ms = ms;
   *launches = cnt;
   *pairs = pr;

@@ -25,6 +25,7 @@
 #include <type_traits>
 #include <utility>
 
+#include "diag.cuh"
 #include "slab.cuh"
 #include "tgemm.cuh"
 
@@ -131,10 +132,20 @@ __device__ __forceinline__ TileCoords grouped_tile_coords(const TileProblem &p, 
   return tc;
 }
 
+// Phase 3 with close_next hands out the next diagonal tile (kb + 1, kb + 1) first: it moves to
+// index 0 and the tiles before it shift up by one.  In the skip-kb numbering of the remaining
+// tiles (row-major, per row) that tile is (kb, kb).
+__device__ __forceinline__ int64_t next_diag_first(const TileProblem &p, int64_t t, int64_t per_row) {
+  if (!p.close_next) return t;
+  const int64_t dg = p.kb * per_row + p.kb;
+  return t == 0 ? dg : (t <= dg ? t - 1 : t);
+}
+
 // G: a grouped launch (its own instantiation, so a single-matrix kernel carries none of the
-// grouped decode or packed-output epilogue).
+// grouped decode or packed-output epilogue).  alt: kModeFwRest16's 32-bit alternative (the
+// block's columns and rows of the matrix, K = the block width).
 template <int MODE, bool G>
-__device__ __forceinline__ TileCoords tile_coords(const TileProblem &p, int64_t t) {
+__device__ __forceinline__ TileCoords tile_coords(const TileProblem &p, int64_t t, bool alt = false) {
   if (G) return grouped_tile_coords<MODE>(p, t);
   TileCoords tc;
   tc.skip = false;
@@ -178,14 +189,17 @@ __device__ __forceinline__ TileCoords tile_coords(const TileProblem &p, int64_t 
       const int64_t bt = p.bt > 1 ? p.bt : 1;
       const int64_t nt = (p.n + kBM - 1) / kBM, e0 = p.kb * bt;
       const int64_t ec = nt - e0 < bt ? nt - e0 : bt, rest = nt - ec;
+      t = next_diag_first(p, t, rest);
       i = (int)(t / rest);
       j = (int)(t - (int64_t)i * rest);
       i += (i >= e0) ? (int)ec : 0;
       j += (j >= e0) ? (int)ec : 0;
-      tc.a_row = i * kBM; tc.a_col = 0;
-      tc.b_row = 0;       tc.b_col = j * kBN;
+      const int k0 = alt ? (int)(e0 * kBM) : 0;
+      tc.a_row = i * kBM; tc.a_col = k0;
+      tc.b_row = k0;      tc.b_col = j * kBN;
       tc.c_row = i * kBM; tc.c_col = j * kBN;
     } else {          // D[i][j] = min(D[i][j], D[i][kb] (x) D[kb][j]), i, j != kb
+      t = next_diag_first(p, t, nb1);
       i = (int)(t / nb1);
       j = (int)(t - (int64_t)i * nb1);
       i += (i >= p.kb);
@@ -197,8 +211,8 @@ __device__ __forceinline__ TileCoords tile_coords(const TileProblem &p, int64_t 
     tc.m_valid = (int)(p.n - tc.c_row < kBM ? p.n - tc.c_row : kBM);
     tc.n_valid = (int)(p.n - tc.c_col < kBN ? p.n - tc.c_col : kBN);
     if (MODE == kModeFwRest16) {
-      const int64_t w = (p.bt > 1 ? p.bt : 1) * kBM, b0 = p.kb * w;
-      tc.k_len = (int)(((p.n - b0 < w ? p.n - b0 : w) + 1) >> 1);
+      const int64_t w = (p.bt > 1 ? p.bt : 1) * kBM, b0 = p.kb * w, len = p.n - b0 < w ? p.n - b0 : w;
+      tc.k_len = alt ? (int)len : (int)((len + 1) >> 1);
     } else {
       tc.k_len = bk;
     }
@@ -206,15 +220,25 @@ __device__ __forceinline__ TileCoords tile_coords(const TileProblem &p, int64_t 
   return tc;
 }
 
+// Tile-index ring of dynamic scheduling (TileProblem::tile_counter): the producer fetches each
+// tile index from the counter and passes it to the consumer warps through kTileRing slots.
+constexpr int kTileRing = 2;
+
 struct Smem {
   const int *sA, *sB, *sC;
-  uint64_t *full, *empty, *cfull, *cempty;
+  uint64_t *full, *empty, *cfull, *cempty, *tq_full, *tq_empty;
+  volatile int *tq;
+  int *dbuf;  // row / column buffers of the in-kernel diagonal closure
 };
 
 // Consumer warps: walk the same tile sequence as the producer, fold every k-slab into the
 // 8 x 8 register tile, then (optionally) min with the prefetched C tile and store.
-template <typename AR, int MODE, bool ACC, bool G>
-__device__ __forceinline__ void consume(const TileProblem &p, const Smem &sm, int warp, int lane, int init_bits) {
+// fstore: float storage (the in-kernel diagonal closure then relaxes in fp32, else in int32).
+// CN: the phase-3 instantiation with dynamic tile scheduling and the in-kernel closure of the
+// next diagonal tile (TileProblem::tile_counter, close_next).
+template <typename AR, int MODE, bool ACC, bool G, bool CN>
+__device__ __forceinline__ void consume(const TileProblem &p, const Smem &sm, int warp, int lane, int init_bits,
+                                        bool fstore, bool alt = false) {
   typedef typename AR::T T;
   const int tm = (warp & 3) * 4 + (lane >> 3);
   const int tn = (warp >> 2) * 8 + (lane & 7);
@@ -222,8 +246,22 @@ __device__ __forceinline__ void consume(const TileProblem &p, const Smem &sm, in
   int stage = 0;
   uint32_t phase = 0, cphase = 0;
   const T init = AR::from(init_bits);
-  for (int64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
-    const TileCoords tc = tile_coords<MODE, G>(p, t);
+  const bool dyn = CN && p.tile_counter;  // uniform
+  int tqs = 0;
+  uint32_t tqp = 0;
+  for (int64_t it = blockIdx.x;; it += gridDim.x) {
+    int64_t t = it;
+    if (dyn) {  // the next index from the producer (-1: no tiles left)
+      if (!mbar_wait(&sm.tq_full[tqs], tqp, p.status)) return;
+      t = sm.tq[tqs];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&sm.tq_empty[tqs]);
+      if (++tqs == kTileRing) { tqs = 0; tqp ^= 1; }
+      if (t < 0) break;
+    } else if (t >= p.ntiles) {
+      break;
+    }
+    const TileCoords tc = tile_coords<MODE, G>(p, t, alt);
     if (tc.skip) continue;  // the producer skips the same tiles
     const int nk = (tc.k_len + kBK - 1) / kBK;
     T acc[8][8];
@@ -269,6 +307,23 @@ __device__ __forceinline__ void consume(const TileProblem &p, const Smem &sm, in
       if (lane == 0) mbar_arrive(sm.cempty);
       cphase ^= 1;
     }
+    if (CN && p.close_next && t == 0) {
+      // Phase 1 of block kb + 1 on its freshly updated diagonal tile (Eq. 1 in registers, the
+      // 256 consumer threads synchronised by named barrier 1).
+      int d[8][8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) d[i][j] = AR::to(acc[i][j]);
+      if (fstore)
+        close_tile_regs<true, 1>(d, tc.m_valid, tm, tn, sm.dbuf);
+      else
+        close_tile_regs<false, 1>(d, tc.m_valid, tm, tn, sm.dbuf);
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = AR::from(d[i][j]);
+    }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int rl = tm + 16 * i;
@@ -302,12 +357,15 @@ __device__ __forceinline__ void consume(const TileProblem &p, const Smem &sm, in
 }
 
 // S: storage type (int or float).  Float matrices always take ArithF32; int matrices take
-// ArithF32 when small_int_bound holds for this launch, else ArithI32 (uniform per launch).
-template <typename S, int MODE, bool ACC, bool G>
+// ArithF32 when small_int_bound holds for this launch (or *p.f32_if), else ArithI32 (uniform
+// per launch).
+template <typename S, int MODE, bool ACC, bool G, bool CN>
 __global__ void __launch_bounds__(kThreads, 1)
     tgemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
-                 const __grid_constant__ CUtensorMap mC, const __grid_constant__ TileProblem p) {
+                 const __grid_constant__ CUtensorMap mC, const __grid_constant__ TileProblem p,
+                 const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mB2) {
   if ((p.skip && *p.skip) || (p.run_if && !*p.run_if)) return;  // uniform, before any barrier exists
+  const bool alt = MODE == kModeFwRest16 && !G && p.alt_if && *p.alt_if;  // uniform
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   int *sA = reinterpret_cast<int *>(smem);
@@ -315,6 +373,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   int *sC = reinterpret_cast<int *>(smem + kStages * (kAStageBytes + kBStageBytes));
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * (kAStageBytes + kBStageBytes) + kCBytes);
   uint64_t *full = bars, *empty = bars + kStages, *cfull = bars + 2 * kStages, *cempty = cfull + 1;
+  uint64_t *tq_full = cempty + 1, *tq_empty = tq_full + kTileRing;
+  volatile int *tq = reinterpret_cast<volatile int *>(tq_empty + kTileRing);
+  int *dbuf = reinterpret_cast<int *>(smem + kStages * (kAStageBytes + kBStageBytes) + kCBytes + 256);
+  static_assert((2 * kStages + 2 + 2 * kTileRing) * 8 + kTileRing * 4 <= 256, "barrier block");
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -324,30 +386,50 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     mbar_init(cfull, 1);
     mbar_init(cempty, kConsumerWarps);
+    for (int s = 0; s < kTileRing; ++s) {
+      mbar_init(&tq_full[s], 1);
+      mbar_init(&tq_empty[s], kConsumerWarps);
+    }
     fence_barrier_init();
   }
   __syncthreads();
+  const bool dyn = CN && p.tile_counter;  // uniform
 
   if (warp >= kConsumerWarps) {
     // ------------------------------- producer --------------------------------------
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kProducerRegs));
     if (warp == kConsumerWarps && lane == 0) {
-      tma_prefetch_desc(&mA);
-      tma_prefetch_desc(&mB);
+      const CUtensorMap *ma = alt ? &mA2 : &mA, *mb = alt ? &mB2 : &mB;
+      tma_prefetch_desc(ma);
+      tma_prefetch_desc(mb);
       if (ACC) tma_prefetch_desc(&mC);
-      int stage = 0;
-      uint32_t phase = 0, cphase = 0, issued = 0, issued_par = 0;
+      int stage = 0, tqs = 0;
+      uint32_t phase = 0, cphase = 0, issued = 0, issued_par = 0, tqp = 0;
       bool c_issued = false, ok = true;
       uint32_t c_par = 0;
-      for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
-        const TileCoords tc = tile_coords<MODE, G>(p, t);
-        if (tc.skip) continue;  // the consumers skip the same tiles
+      // Dynamic order: the index of the next tile is fetched while the current one is issued,
+      // so the atomic's round trip overlaps the stage waits.
+      int64_t t = dyn ? (int64_t)atomicAdd(p.tile_counter, 1) : (int64_t)blockIdx.x;
+      while (ok) {
+        if (dyn) {  // hand the index to the consumers
+          if (!mbar_wait(&tq_empty[tqs], tqp ^ 1, p.status)) { ok = false; break; }
+          tq[tqs] = t < p.ntiles ? (int)t : -1;
+          mbar_arrive(&tq_full[tqs]);
+          if (++tqs == kTileRing) { tqs = 0; tqp ^= 1; }
+        }
+        if (t >= p.ntiles) break;
+        const int64_t t_next = dyn ? (int64_t)atomicAdd(p.tile_counter, 1) : t + gridDim.x;
+        const TileCoords tc = tile_coords<MODE, G>(p, t, alt);
+        if (tc.skip) {  // the consumers skip the same tiles
+          t = t_next;
+          continue;
+        }
         const int nk = (tc.k_len + kBK - 1) / kBK;
         for (int kt = 0; kt < nk; ++kt) {
           if (!mbar_wait(&empty[stage], phase ^ 1, p.status)) { ok = false; break; }
           mbar_arrive_expect_tx(&full[stage], kAStageBytes + kBStageBytes);
-          tma_load_2d(sA + stage * (kBM * kBK), &mA, tc.a_col + kt * kBK, tc.a_row, &full[stage]);
-          tma_load_2d(sB + stage * (kBK * kBN), &mB, tc.b_col, tc.b_row + kt * kBK, &full[stage]);
+          tma_load_2d(sA + stage * (kBM * kBK), ma, tc.a_col + kt * kBK, tc.a_row, &full[stage]);
+          tma_load_2d(sB + stage * (kBK * kBN), mb, tc.b_col, tc.b_row + kt * kBK, &full[stage]);
           issued |= 1u << stage;
           issued_par = (issued_par & ~(1u << stage)) | (phase << stage);
           if (++stage == kStages) { stage = 0; phase ^= 1; }
@@ -360,25 +442,37 @@ __global__ void __launch_bounds__(kThreads, 1)
           c_par = cphase;
           cphase ^= 1;
         }
+        t = t_next;
       }
       // Never leave a bulk copy writing into shared memory of an exiting CTA.
       for (int s = 0; s < kStages; ++s)
         if (issued & (1u << s)) mbar_wait(&full[s], (issued_par >> s) & 1, p.status);
       if (c_issued) mbar_wait(cfull, c_par, p.status);
+      // The last producer to finish has seen every other producer's final fetch: it resets the
+      // counter pair for the next launch on the stream.
+      if (dyn && atomicAdd(p.tile_counter + 1, 1) == (int)gridDim.x - 1) {
+        p.tile_counter[0] = 0;
+        p.tile_counter[1] = 0;
+      }
     }
     return;
   }
 
   asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kConsumerRegs));
-  const Smem sm = {sA, sB, sC, full, empty, cfull, cempty};
+  const Smem sm = {sA, sB, sC, full, empty, cfull, cempty, tq_full, tq_empty, tq, dbuf};
   if (sizeof(S) == 4 && S(0.5) != S(0)) {  // float storage
-    consume<ArithF32, MODE, ACC, G>(p, sm, warp, lane, 0x7f800000);
+    consume<ArithF32, MODE, ACC, G, CN>(p, sm, warp, lane, 0x7f800000, true, alt);
+  } else if (alt) {  // the 32-bit alternative of a packed launch (int32 storage)
+    if ((p.f32_if && *p.f32_if) || (p.wmax && small_int_bound(p.wmax[0], p.wmult, p.wmax[1])))
+      consume<ArithF32, MODE, ACC, G, CN>(p, sm, warp, lane, p.inf_i, false, true);
+    else
+      consume<ArithI32, MODE, ACC, G, CN>(p, sm, warp, lane, p.inf_i, false, true);
   } else if (p.arith16) {
-    consume<ArithI16x2, MODE, ACC, G>(p, sm, warp, lane, (kCap16 << 16) | kCap16);
-  } else if (p.wmax && small_int_bound(p.wmax[0], p.wmult, p.wmax[1])) {
-    consume<ArithF32, MODE, ACC, G>(p, sm, warp, lane, p.inf_i);
+    consume<ArithI16x2, MODE, ACC, G, CN>(p, sm, warp, lane, (kCap16 << 16) | kCap16, false);
+  } else if ((p.f32_if && *p.f32_if) || (p.wmax && small_int_bound(p.wmax[0], p.wmult, p.wmax[1]))) {
+    consume<ArithF32, MODE, ACC, G, CN>(p, sm, warp, lane, p.inf_i, false);
   } else {
-    consume<ArithI32, MODE, ACC, G>(p, sm, warp, lane, p.inf_i);
+    consume<ArithI32, MODE, ACC, G, CN>(p, sm, warp, lane, p.inf_i, false);
   }
 }
 
@@ -392,10 +486,10 @@ template <int MODE> static double algorithmic_pairs(const TileProblem &p) {
   return MODE == kModeFwPanels ? 2.0 * bk * bk * rest : rest * rest * bk;
 }
 
-template <typename T, int MODE, bool ACC, bool G = false>
+template <typename T, int MODE, bool ACC, bool G = false, bool CN = false>
 static int launch_one(const CUtensorMap &mA, const CUtensorMap &mB, const CUtensorMap &mC, const TileProblem &p,
-                      cudaStream_t s) {
-  auto k = tgemm_kernel<T, MODE, ACC, G>;
+                      cudaStream_t s, const CUtensorMap &mA2, const CUtensorMap &mB2) {
+  auto k = tgemm_kernel<T, MODE, ACC, G, CN>;
   static std::atomic<int> checked{0};  // 1: register split verified for this instantiation
   if (!checked.load(std::memory_order_relaxed)) {
     cudaFuncAttributes fa;
@@ -410,40 +504,49 @@ static int launch_one(const CUtensorMap &mA, const CUtensorMap &mB, const CUtens
   void *ev = nullptr;
   const bool tr = trace_on() && !p.no_trace;
   if (tr) trace_begin(s, &ev);
-  k<<<grid, kThreads, kSmemBytes + 1024, s>>>(mA, mB, mC, p);
+  k<<<grid, kThreads, kSmemBytes + 1024, s>>>(mA, mB, mC, p, mA2, mB2);
   APSP_LAUNCH_CHECK();
-  if (tr) trace_end(s, ev, MODE, algorithmic_pairs<MODE>(p));
+  if (tr) trace_end(s, ev, MODE + p.trace_class, algorithmic_pairs<MODE>(p));
   return APSP_OK;
 }
 
 template <typename T>
 static int launch_t(int mode, bool acc, const CUtensorMap &mA, const CUtensorMap &mB, const CUtensorMap &mC,
-                    const TileProblem &p, cudaStream_t s) {
-  if (p.ngroups > 0) {  // grouped launches: int32 storage, FW modes only
-    if constexpr (std::is_same<T, int>::value) {
-      switch (mode * 2 + (acc ? 1 : 0)) {
-        case 2: return launch_one<T, kModeFwPanels, false, true>(mA, mB, mC, p, s);
-        case 5: return launch_one<T, kModeFwRest, true, true>(mA, mB, mC, p, s);
-        case 7: return launch_one<T, kModeFwRest16, true, true>(mA, mB, mC, p, s);
-        default: return APSP_ERR_ARG;
-      }
+                    const TileProblem &p, cudaStream_t s, const CUtensorMap &mA2, const CUtensorMap &mB2) {
+  if (p.ngroups > 0) {  // grouped launches: FW modes only; packed 16-bit pairs for int32 only
+    switch (mode * 2 + (acc ? 1 : 0)) {
+      case 2: return launch_one<T, kModeFwPanels, false, true>(mA, mB, mC, p, s, mA2, mB2);
+      case 5: return launch_one<T, kModeFwRest, true, true>(mA, mB, mC, p, s, mA2, mB2);
+      case 7:
+        if constexpr (std::is_same<T, int>::value) return launch_one<T, kModeFwRest16, true, true>(mA, mB, mC, p, s, mA2, mB2);
+        return APSP_ERR_ARG;
+      default: return APSP_ERR_ARG;
     }
-    return APSP_ERR_ARG;
   }
   switch (mode * 2 + (acc ? 1 : 0)) {
-    case 0: return launch_one<T, kModeGemm, false>(mA, mB, mC, p, s);
-    case 1: return launch_one<T, kModeGemm, true>(mA, mB, mC, p, s);
-    case 2: return launch_one<T, kModeFwPanels, false>(mA, mB, mC, p, s);
-    case 5: return launch_one<T, kModeFwRest, true>(mA, mB, mC, p, s);
-    case 7: return launch_one<T, kModeFwRest16, true>(mA, mB, mC, p, s);
+    case 0: return launch_one<T, kModeGemm, false>(mA, mB, mC, p, s, mA2, mB2);
+    case 1: return launch_one<T, kModeGemm, true>(mA, mB, mC, p, s, mA2, mB2);
+    case 2: return launch_one<T, kModeFwPanels, false>(mA, mB, mC, p, s, mA2, mB2);
+    case 5:
+      if (p.tile_counter) return launch_one<T, kModeFwRest, true, false, true>(mA, mB, mC, p, s, mA2, mB2);
+      return launch_one<T, kModeFwRest, true>(mA, mB, mC, p, s, mA2, mB2);
+    case 7:
+      if constexpr (std::is_same<T, int>::value) {
+        if (p.tile_counter) return launch_one<T, kModeFwRest16, true, false, true>(mA, mB, mC, p, s, mA2, mB2);
+        return launch_one<T, kModeFwRest16, true>(mA, mB, mC, p, s, mA2, mB2);
+      }
+      return APSP_ERR_ARG;
     default: return APSP_ERR_ARG;
   }
 }
 
 int launch_tgemm(int mode, bool acc, int dtype, const CUtensorMap &mA, const CUtensorMap &mB, const CUtensorMap &mC,
-                 const TileProblem &p, cudaStream_t s) {
+                 const TileProblem &p, cudaStream_t s, const CUtensorMap *mA2, const CUtensorMap *mB2) {
   if (p.ntiles <= 0) return APSP_OK;
-  return dtype == APSP_I32 ? launch_t<int>(mode, acc, mA, mB, mC, p, s) : launch_t<float>(mode, acc, mA, mB, mC, p, s);
+  if (p.alt_if && (!mA2 || !mB2)) return APSP_ERR_ARG;
+  const CUtensorMap &a2 = mA2 ? *mA2 : mA, &b2 = mB2 ? *mB2 : mB;
+  return dtype == APSP_I32 ? launch_t<int>(mode, acc, mA, mB, mC, p, s, a2, b2)
+                           : launch_t<float>(mode, acc, mA, mB, mC, p, s, a2, b2);
 }
 
 int make_operand_maps(const void *base, int64_t rows, int64_t cols, int64_t ld, int dtype, CUtensorMap *mA,
@@ -655,6 +758,7 @@ extern "C" int tropical_gemm(void *C, const void *A, const void *B, int64_t M, i
   if ((r = make_operand_maps(C, M, N, ldc, dtype, nullptr, nullptr, &mC))) return r;
   void *own = nullptr;
   int *words = nullptr;
+  const size_t p16 = dtype == APSP_I32 ? packed16_bytes(M, N, K) : 0;
   if (dtype == APSP_I32) {  // largest finite entries of A and B decide the exact fp32 path
     if (!ws) {
       ws_bytes = tropical_gemm_workspace_bytes(M, N, K, dtype);
@@ -684,7 +788,7 @@ extern "C" int tropical_gemm(void *C, const void *A, const void *B, int64_t M, i
   // below 0x3FFF (checked by the pack kernels on the device), the product runs on 16-bit pairs,
   // two (min,+) pairs per DPX operation; the plain launch then returns at once.
   void *tev = nullptr;
-  const bool group = !r && dtype == APSP_I32 && K > 0 && ws_bytes >= kFlagBytes + packed16_bytes(M, N, K);
+  const bool group = !r && dtype == APSP_I32 && K > 0 && ws_bytes >= kFlagBytes + p16;
   if (group && trace_on()) trace_begin(s, &tev);
   if (group) {
     const int64_t kw = (K + 1) >> 1, lda16 = round_up(kw, 4), ldb16 = round_up(N, 4);

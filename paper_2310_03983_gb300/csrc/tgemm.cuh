@@ -18,7 +18,10 @@ static_assert(128 * kProducerRegs + 256 * kConsumerRegs <= kThreads * kLaunchReg
 constexpr int kAStageBytes = kBM * kBK * 4;         // A tile [128 m][32 k]
 constexpr int kBStageBytes = kBK * kBN * 4;         // B tile [32 k][128 n]
 constexpr int kCBytes = kBM * kBN * 4;              // C tile [128 m][128 n]
-constexpr int kSmemBytes = kStages * (kAStageBytes + kBStageBytes) + kCBytes + 256;
+// Shared memory: the stage ring, the C tile, 256 bytes of mbarriers and the tile-index ring, and
+// 2 KB of row / column buffers for the in-kernel diagonal closure (close_next).
+constexpr int kDiagBufBytes = 512 * 4;
+constexpr int kSmemBytes = kStages * (kAStageBytes + kBStageBytes) + kCBytes + 256 + kDiagBufBytes;
 
 // Which tiles a launch visits and where their operands live.
 enum TileMode : int {
@@ -95,6 +98,28 @@ struct TileProblem {
   // Host only, for tracing: when > 0, the launch's algorithmic pairs (grouped launches, whose
   // work the host sums over the graphs of the launch).
   double trace_pairs;
+  // Added to the mode in trace records: 0, or kTracePass32 for the launches of an int32 FW's
+  // conditional 32-bit pass, or kTraceFallback for passes that normally return at once.
+  int trace_class;
+  // int32 storage (may be null): when *f32_if is non-zero the fp32 sequence runs even though
+  // the exact bound does not hold -- a pass truncated at 2^24 that is certified afterwards
+  // (fw.cu).
+  const int *f32_if;
+  // FW phase-3 launches (kModeFwRest, and kModeFwRest16 with bt <= 1; single matrix; may be
+  // null): two device words, zero before the first such launch.  Tiles are then handed out by
+  // an atomic counter, in the order the CTAs ask for them, and the last CTA to finish resets
+  // both words for the next launch on the stream.
+  int *tile_counter;
+  // With tile_counter, and kb + 1 < nb: the launch also performs phase 1 of the next block.
+  // The diagonal tile (kb + 1, kb + 1) is handed out first, and after its phase-3 update the
+  // CTA's consumer warps close it by Eq. 1 in registers (diag.cuh) before storing it, while the
+  // other CTAs share the rest of the tiles.
+  int close_next;
+  // kModeFwRest16, single matrix (may be null): when *alt_if is non-zero the launch runs its 32-bit
+  // alternative instead of the packed one -- the same tiles over the block's bt * 128 columns
+  // and rows of the matrix itself (maps mA2 / mB2 of launch_tgemm), K = the block width, with
+  // the fp32 sequence (exact bound or *f32_if) or the int32 one.
+  const int *alt_if;
 };
 
 // Packed 16-bit copies of a 128 x 128 tile held in the engine's register layout (thread (tm, tn)
@@ -139,9 +164,11 @@ int launch_pack16_b(const int *B, int64_t ldb, int64_t K, int64_t N, int *B16, i
                     cudaStream_t s);
 
 // Launch one tile pass.  acc: fold into the existing C (min) instead of overwriting it.
-// maps: A box 128 rows x 32 cols, B box 32 rows x 128 cols, C box 128 x 128.
+// maps: A box 128 rows x 32 cols, B box 32 rows x 128 cols, C box 128 x 128.  mA2 / mB2 (may be
+// null): the matrix maps of kModeFwRest16's 32-bit alternative (TileProblem::alt_if).
 int launch_tgemm(int mode, bool acc, int dtype, const CUtensorMap &mA, const CUtensorMap &mB, const CUtensorMap &mC,
-                 const TileProblem &p, cudaStream_t s);
+                 const TileProblem &p, cudaStream_t s, const CUtensorMap *mA2 = nullptr,
+                 const CUtensorMap *mB2 = nullptr);
 
 // Generic (any alignment, any leading dimension) tropical GEMM used when TMA's alignment
 // rules do not hold.  Same semantics as tropical_gemm.
@@ -165,7 +192,9 @@ int launch_normalise(void *d, int64_t n, int64_t ld, int dtype, int inf_i, float
 int launch_scan_max(const void *x, int64_t rows, int64_t cols, int64_t ld, int inf, int *out, cudaStream_t s);
 
 // Launch tracing (runtime.cu): when enabled, every tropical-GEMM-engine launch is bracketed
-// by two CUDA events on its stream and tagged with its mode and algorithmic pair count.
+// by two CUDA events on its stream and tagged with its mode plus TileProblem::trace_class, and
+// its algorithmic pair count.
+constexpr int kTracePass32 = 16, kTraceFallback = 32;
 bool trace_on();
 void trace_begin(cudaStream_t s, void **ev0);
 void trace_end(cudaStream_t s, void *ev0, int mode, double pairs);

@@ -208,14 +208,16 @@ DEFAULT_LOG = os.path.join(os.path.dirname(os.path.abspath(__file__)), "timings_
 
 
 def sweep_graphs(seed: int = 0):
-    """The autotuning sweep: sizes 32..16384 (log-spaced), both dtypes, sparse and dense."""
+    """The autotuning sweep: sizes 32..16384 (log-spaced), both dtypes, sparse and dense, and
+    very dense int32 graphs (p = 0.8, diameter 2) between 362 and 2896 vertices, where a few
+    full-size products of repeated squaring compete with Floyd-Warshall's block steps."""
     import workloads
     sizes = sorted({int(round(2 ** e)) for e in np.arange(5.0, 14.01, 0.5)})
     for i, n in enumerate(sizes):
         for dt in ("int32", "float32"):
-            for p in (0.02, 0.4):
+            for p in ((0.02, 0.4, 0.8) if dt == "int32" and 362 <= n <= 2896 else (0.02, 0.4)):
                 kw = {"lo": 1, "hi": 100} if dt == "int32" else {"dist": "lognormal", "lo": 0.0, "hi": 1.0}
-                yield workloads.er_graph(n, p, dt, seed=seed * 100000 + 10 * n + (p > 0.1), **kw)
+                yield workloads.er_graph(n, p, dt, seed=seed * 100000 + 10 * n + (p > 0.1) + (p > 0.5), **kw)
 
 
 def main(log_path: str = DEFAULT_LOG, model_path: str = DEFAULT_MODEL, reps: int = 5):

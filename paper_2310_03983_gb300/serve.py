@@ -87,6 +87,8 @@ class Request:
     t_admit: float = -1.0
     t_done: float = -1.0
     result: object = None
+    ready: bool = True       # False until a Feeder has made the host matrix
+    host_off: object = None  # the matrix's offset in the Feeder's HostArena
 
     @property
     def footprint(self) -> int:
@@ -160,6 +162,99 @@ class Scheduler:
         r.off = -1
 
 
+class HostArena:
+    """A page-locked host buffer (huge pages when large, so that copies keep their full rate)
+    carved by the first-fit Arena: the host side of requests whose matrices are made while the
+    stream runs.  view(off, n, dtype) is an n x n tensor at element offset off."""
+
+    def __init__(self, nbytes: int):
+        from . import host_empty
+        import torch
+        self.buf = host_empty((nbytes // 4,), torch.int32)
+        self.arena = Arena(nbytes // 4)
+
+    def view(self, off: int, n: int, dtype: str):
+        import torch
+        t = self.buf[off:off + n * n].view(n, n)
+        return t.view(torch.float32) if dtype == "float32" else t
+
+
+class Feeder:
+    """Makes the request matrices of a stream ahead of their arrival, on a pool of host threads,
+    into a HostArena: request i is made once its arrival is within `lead` seconds (all at once
+    with lead = None) and its matrix fits the arena; the server releases its slice when done.
+    ``make(k, n, p, dtype, out)`` writes request k's matrix into the numpy array ``out``.
+    ``stats()`` reports how late, if ever, a matrix became ready after its arrival time."""
+
+    def __init__(self, requests: list, arena: HostArena, make, threads: int = 8, lead: float | None = 1.0,
+                 time_scale: float = 1.0):
+        import threading
+        from concurrent.futures import ThreadPoolExecutor
+        self.reqs = sorted(requests, key=lambda r: r.arrival)
+        self.arena, self.make, self.lead, self.ts = arena, make, lead, time_scale
+        self.cv = threading.Condition()
+        self.pool = ThreadPoolExecutor(threads)
+        self.t0 = None
+        self.late = []
+        self.stop = False
+        self.thread = threading.Thread(target=self._run, daemon=True)
+
+    def start(self, t0: float):
+        self.t0 = t0
+        self.thread.start()
+
+    def _run(self):
+        for r in self.reqs:
+            if self.lead is not None:
+                while not self.stop:
+                    wait = r.arrival * self.ts - self.lead - (time.perf_counter() - self.t0)
+                    if wait <= 0:
+                        break
+                    time.sleep(min(wait, 0.01))
+            with self.cv:
+                while not self.stop:
+                    r.host_off = self.arena.arena.alloc(r.n * r.n)
+                    if r.host_off is not None:
+                        break
+                    self.cv.wait(0.01)
+            if self.stop:
+                return
+            self.pool.submit(self._fill, r)
+
+    def _fill(self, r):
+        v = self.arena.view(r.host_off, r.n, r.dtype)
+        self.make(r.rid, r.n, r.density, r.dtype, v.numpy())
+        r.host = v
+        late = (time.perf_counter() - self.t0) - r.arrival * self.ts
+        with self.cv:
+            self.late.append(late)
+            r.ready = True
+            self.cv.notify_all()
+
+    def release(self, r):
+        with self.cv:
+            self.arena.arena.free(r.host_off)
+            r.host, r.host_off = None, None
+            self.cv.notify_all()
+
+    def close(self):
+        self.stop = True
+        self.thread.join(timeout=5)
+        self.pool.shutdown(wait=True)
+
+    def stats(self) -> dict:
+        late = np.maximum(np.asarray(self.late, np.float64), 0.0) * 1e3
+        return {"matrices": len(late), "ready_after_arrival_ms_p99": float(np.percentile(late, 99)) if len(late) else None,
+                "ready_after_arrival_ms_max": float(late.max()) if len(late) else None}
+
+
+def stream_requests(arrivals, ns, ps, dtypes):
+    """Requests of a stream whose matrices a Feeder makes: request k has n = ns[k], edge
+    probability ps[k] (its density feature) and dtype dtypes[k]; not ready until made."""
+    return [Request(rid=k, n=int(ns[k]), dtype=str(dtypes[k]), arrival=float(t), density=float(ps[k]), ready=False)
+            for k, t in enumerate(arrivals)]
+
+
 def make_requests(arrivals, library, density=None):
     """Requests for arrival times `arrivals` (seconds): request k carries library graph
     k mod len(library) (a list of numpy cost matrices), copied once to pinned host memory."""
@@ -219,6 +314,8 @@ class Server:
         dt = torch.float32 if r.dtype == "float32" else torch.int32
         if self.keep_results:
             return torch.empty((r.n, r.n), dtype=dt).pin_memory()
+        if r.host_off is not None:
+            return r.host  # a Feeder's request: back into its own host slice
         key = (r.n, r.dtype)
         if key not in self._staging:
             self._staging[key] = torch.empty((r.n, r.n), dtype=dt).pin_memory()
@@ -273,8 +370,10 @@ class Server:
         return ev, reqs, keep
 
     # -- the loop ----------------------------------------------------------------------------
-    def serve(self, requests: list, time_scale: float = 1.0) -> dict:
-        """Serve requests at their arrival times (arrival * time_scale seconds after start)."""
+    def serve(self, requests: list, time_scale: float = 1.0, feeder: Feeder | None = None) -> dict:
+        """Serve requests at their arrival times (arrival * time_scale seconds after start).  With
+        a feeder, a request enters once its matrix is made, and its host slice is released (the
+        result then goes back into it unless keep_results) when it is done."""
         torch = self.torch
         reqs = sorted(requests, key=lambda r: r.arrival)
         for r in reqs:
@@ -283,6 +382,8 @@ class Server:
                 raise ValueError(f"request {r.rid} (n={r.n}) can never fit the {self.arena_elems * 4} B arena")
         total = len(reqs)
         t0 = time.perf_counter()
+        if feeder is not None:
+            feeder.start(t0)
         nxt, done = 0, 0
         inflight = []  # (event, reqs, keepalive, slot)
         free_slots = list(range(self.slots))
@@ -290,7 +391,7 @@ class Server:
         launches = {"batch": 0, "solo": 0}
         while done < total:
             now = time.perf_counter() - t0
-            while nxt < total and reqs[nxt].arrival * time_scale <= now:
+            while nxt < total and reqs[nxt].arrival * time_scale <= now and reqs[nxt].ready:
                 self.sched.arrive(reqs[nxt])
                 nxt += 1
             for r in self.sched.admit(now):
@@ -315,6 +416,8 @@ class Server:
                     for r in rs:
                         r.t_done = t
                         self.sched.release(r)
+                        if feeder is not None and not self.keep_results:
+                            feeder.release(r)
                         done += 1
                     free_slots.append(slot)
                     progressed = True
@@ -324,6 +427,8 @@ class Server:
             if not progressed:
                 time.sleep(50e-6)
         wall = time.perf_counter() - t0
+        if feeder is not None:
+            feeder.close()
         lat = [(r.t_done - r.arrival * time_scale) * 1e3 for r in reqs]
         st = percentiles(lat)
         st.update({"requests": total, "wall_s": wall, "graphs_per_s": total / wall, "launches": launches,
@@ -331,27 +436,38 @@ class Server:
         return st
 
 
-def serve_one_at_a_time(requests: list, device=None, time_scale: float = 1.0, planner=None) -> dict:
+def serve_one_at_a_time(requests: list, device=None, time_scale: float = 1.0, planner=None,
+                        feeder: Feeder | None = None) -> dict:
     """Baseline: each request in arrival order is copied in, closed alone (apsp_fw) and copied
-    back before the next one starts."""
+    back before the next one starts (with a feeder: back into its own host slice)."""
     import torch
     from . import apsp_fw
     dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
     reqs = sorted(requests, key=lambda r: r.arrival)
     staging = {}
     t0 = time.perf_counter()
+    if feeder is not None:
+        feeder.start(t0)
     for r in reqs:
-        while time.perf_counter() - t0 < r.arrival * time_scale:
+        while time.perf_counter() - t0 < r.arrival * time_scale or not r.ready:
             time.sleep(50e-6)
         d = r.host.to(dev, non_blocking=True)
         apsp_fw(d)
-        key = (r.n, r.dtype)
-        if key not in staging:
-            staging[key] = torch.empty_like(r.host).pin_memory()
-        staging[key].copy_(d, non_blocking=True)
+        if r.host_off is not None:  # a Feeder's request: back into its own host slice
+            dst = r.host
+        else:
+            key = (r.n, r.dtype)
+            if key not in staging:
+                staging[key] = torch.empty_like(r.host).pin_memory()
+            dst = staging[key]
+        dst.copy_(d, non_blocking=True)
         torch.cuda.current_stream(dev).synchronize()
         r.t_done = time.perf_counter() - t0
+        if feeder is not None:
+            feeder.release(r)
     wall = time.perf_counter() - t0
+    if feeder is not None:
+        feeder.close()
     st = percentiles([(r.t_done - r.arrival * time_scale) * 1e3 for r in reqs])
     st.update({"requests": len(reqs), "wall_s": wall, "graphs_per_s": len(reqs) / wall})
     return st

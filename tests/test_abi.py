@@ -65,12 +65,13 @@ def test_host_side_calls_without_gpu():
     assert h(None, 0, 0, 0, None, 0, None, 0, None) == 0
 
 
-def _staged_model(ns, count):
-    """The staging plan of apsp_batched, restated: int32 graphs of 3..16 blocks of 128 vertices
+def _staged_model(ns, count, packed=True):
+    """The staging plan of apsp_batched, restated: graphs of 3..16 blocks of 128 vertices
     (the 14 largest block counts present), grouped by block count; workspace = 256 bytes of
     words, four per-graph int arrays, the index lists of the whole batch, the staging matrix
-    (staged rows x the largest padded size), and two sets of the packed column panels (staged
-    rows x 64) and packed row panels (64 rows per staged graph x the largest padded size)."""
+    (staged rows x the largest padded size), and (int32 only) two sets of the packed column
+    panels (staged rows x 64) and packed row panels (64 rows per staged graph x the largest
+    padded size)."""
     r256 = lambda b: -(-b // 256) * 256
     nbs = [-(-n // 128) if n > 0 else 0 for n in ns]
     present = sorted({nb for nb in nbs if 3 <= nb <= 16}, reverse=True)[:14]
@@ -79,7 +80,7 @@ def _staged_model(ns, count):
     staged = [nb for nb in nbs if nb in present]
     G, R, NP = len(staged), sum(nb * 128 for nb in staged), present[0] * 128
     return (256 + 4 * r256(4 * G) + r256(4 * count) + r256(4 * R * NP)
-            + 2 * (r256(4 * R * 64) + r256(4 * G * 64 * NP)))
+            + (2 * (r256(4 * R * 64) + r256(4 * G * 64 * NP)) if packed else 0))
 
 
 def test_staged_plan_and_chunking_on_the_host():
@@ -98,7 +99,7 @@ def test_staged_plan_and_chunking_on_the_host():
         arr = np.asarray(ns, np.int32)
         ptr = arr.ctypes.data_as(ctypes.c_void_p)
         assert f(ptr, len(arr), 0) == _staged_model(ns, len(arr)), ns
-        assert f(ptr, len(arr), 1) == 256  # float32 batches are never staged
+        assert f(ptr, len(arr), 1) == _staged_model(ns, len(arr), packed=False)  # float32: no packed panels
         # chunking: consecutive runs of about equal n^3, each run's staged room; the largest
         lds = ((np.maximum(arr, 1) + 3) // 4 * 4).astype(np.int32)
         offs = np.concatenate([[0], np.cumsum(np.maximum(arr, 0).astype(np.int64) * lds)[:-1]]).astype(np.int64)

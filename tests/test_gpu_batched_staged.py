@@ -1,6 +1,6 @@
-"""a7, staged path: the larger graphs of an int32 batch (257..2048 vertices) closed in lockstep
-on the tropical-GEMM engine (16-bit phase 3 certified per graph, int32 pass for the rest),
-against the persistent kernel alone (bit for bit) and the oracle."""
+"""a7, staged path: the larger graphs of a batch (257..2048 vertices) closed in lockstep on the
+tropical-GEMM engine (int32: 16-bit phase 3 certified per graph, an int32 pass for the rest;
+float32: one fp32 pass), against the persistent kernel alone and the oracle."""
 import os
 
 import numpy as np
@@ -95,6 +95,37 @@ def test_config4_batch_against_oracle(apsp):
     assert apsp.apsp_device_status() == 0
     full = _check_batch_against_oracle(b, mats, out)
     assert full > 1500 and len(mats) - full > 300
+
+
+def test_staged_float32_equals_persistent_kernel(apsp):
+    """Float32 batches stage too (one fp32 lockstep pass, no certificate): the same distances
+    as the persistent kernel alone and as the oracle (1e-5 relative of fp64)."""
+    ns, ps = workloads.batch_specs(300, n_lo=32, n_hi=1100, seed=9)
+    mats = workloads.batch_graphs(ns, ps, dtype="float32", dist="lognormal", lo=0.0, hi=1.0)
+    staged = apsp.Batch(mats)
+    plain = apsp.Batch(mats, staged=False)
+    assert staged.ws.numel() > plain.ws.numel()
+    out_s, launches_s = _run(apsp, staged)
+    out_p, launches_p = _run(apsp, plain)
+    assert launches_p == 1 and launches_s > 10
+    assert apsp.apsp_device_status() == 0
+    for g in range(len(mats)):
+        assert_dist_equal(staged.graph(g, out_s).numpy(), staged.graph(g, out_p).numpy().astype(np.float64),
+                          f"graph {g} staged vs persistent")
+    full = _check_batch_against_oracle(staged, mats, out_s)
+    assert full > 100
+
+
+def test_config4_float32_batch_against_oracle(apsp):
+    """The 2048-graph batch shape with float32 lognormal(0, 1) weights, staged."""
+    ns, ps = workloads.batch_specs(2048, seed=0)
+    mats = workloads.batch_graphs(ns, ps, dtype="float32", dist="lognormal", lo=0.0, hi=1.0)
+    b = apsp.Batch(mats)
+    out, launches = _run(apsp, b)
+    assert launches > 10
+    assert apsp.apsp_device_status() == 0
+    full = _check_batch_against_oracle(b, mats, out)
+    assert full > 1500
 
 
 def test_certificate_both_sides_of_the_cap(apsp):

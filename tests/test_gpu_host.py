@@ -104,3 +104,29 @@ def test_batched_host_in_place_and_out_of_order_layout(apsp):
         got = out[o:o + n * ld].view(n, ld)[:, :n].numpy()
         assert np.array_equal(got, b.graph(g, want).numpy()), f"graph {g}"
     assert apsp.apsp_device_status() == 0
+
+
+@pytest.mark.parametrize("shape", [(7, 5), (8192, 8192)])
+def test_host_alloc_buffers(apsp, shape):
+    """apsp_host_alloc / host_empty: page-locked (registered) host memory, small buffers from
+    cudaHostAlloc and large ones on huge pages; exact round trips through the device, solve()
+    on them, and the free of a pointer the library did not allocate refused."""
+    t = apsp.host_empty(shape, torch.int32)
+    assert t.is_pinned() and t.shape == shape
+    rng = np.random.default_rng(shape[0])
+    t.numpy()[:] = rng.integers(0, 1 << 30, shape, dtype=np.int32)
+    d = t.to("cuda", non_blocking=True)
+    back = apsp.host_empty(shape, torch.int32)
+    back.copy_(d, non_blocking=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(back.numpy(), t.numpy())
+    if shape[0] == shape[1] and shape[0] >= 1024:
+        h = workloads.er_graph(shape[0], 0.01, "int32", lo=1, hi=100, seed=3)
+        t.numpy()[:] = h
+        out = apsp.solve(t, out=back)
+        d2 = torch.from_numpy(h).cuda()
+        apsp.apsp_fw(d2)
+        assert np.array_equal(out.numpy(), d2.cpu().numpy())
+    x = np.zeros(16, np.int32)
+    assert apsp.lib().apsp_host_free(x.ctypes.data) == APSP_ERR_ARG
+    assert apsp.lib().apsp_host_free(None) == 0

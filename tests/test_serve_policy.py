@@ -1,4 +1,6 @@
 """a9 host logic without a GPU: the arena allocator and the admission/batching policy."""
+import time
+
 import numpy as np
 
 from paper_2310_03983_gb300.serve import Arena, Request, Scheduler, percentiles
@@ -92,3 +94,69 @@ def test_very_large_requests_do_not_share_the_gpu():
 def test_percentiles():
     p = percentiles(list(range(1, 101)))
     assert abs(p["p50"] - 50.5) < 1e-9 and abs(p["p99"] - 99.01) < 1e-9
+
+
+class _NumpyHostArena:
+    """The HostArena interface over plain numpy memory (no GPU needed)."""
+
+    def __init__(self, elems):
+        import torch
+        self.buf = torch.zeros(elems, dtype=torch.int32)
+        self.arena = Arena(elems)
+
+    def view(self, off, n, dtype):
+        import torch
+        t = self.buf[off:off + n * n].view(n, n)
+        return t.view(torch.float32) if dtype == "float32" else t
+
+
+def test_feeder_makes_every_request_within_the_arena():
+    """The feeder makes each request's matrix (in arrival order, on worker threads) into the
+    host arena, waits for room when the arena is full, and the matrices are the request's own."""
+    import threading
+    import workloads
+    from paper_2310_03983_gb300.serve import Feeder, stream_requests
+    pool = workloads.RequestPool(seed=1, size_u=1 << 20, size_w=1 << 18, threads=2)
+    t = np.linspace(0.0, 0.05, 40)
+    ns = np.array([8 + (7 * k) % 90 for k in range(40)])
+    ps = np.linspace(0.05, 0.5, 40)
+    dts = np.where(np.arange(40) % 2 == 0, "int32", "float32")
+    reqs = stream_requests(t, ns, ps, dts)
+    host = _NumpyHostArena(4 * 96 * 96)  # room for about four matrices at a time
+    make = lambda k, n, p, dt, out: workloads.request_matrix(pool, k, n, p, dt, out=out)  # noqa: E731
+    f = Feeder(reqs, host, make, threads=3, lead=None)
+    f.start(time.perf_counter())
+    seen, peak = 0, 0
+    deadline = time.perf_counter() + 60
+    while seen < len(reqs) and time.perf_counter() < deadline:
+        for r in reqs:
+            if r.ready and r.host is not None:
+                want = workloads.request_matrix(pool, r.rid, r.n, r.density, r.dtype)
+                assert np.array_equal(r.host.numpy(), want), r.rid
+                peak = max(peak, host.arena.used)
+                f.release(r)
+                seen += 1
+        time.sleep(0.001)
+    f.close()
+    assert seen == len(reqs)
+    assert host.arena.used == 0 and peak <= host.arena.capacity
+    assert all(r.ready for r in reqs)
+
+
+def test_request_matrix_is_an_er_graph_of_its_own_parameters():
+    import workloads
+    pool = workloads.RequestPool(seed=2, size_u=1 << 22, size_w=1 << 20, threads=2)
+    m = workloads.request_matrix(pool, 5, 600, 0.2, "int32")
+    off = ~np.eye(600, dtype=bool)
+    e = m[off] < workloads.INF_I32
+    assert abs(e.mean() - 0.2) < 0.01 and np.all(np.diagonal(m) == 0)
+    assert m[off][e].min() == 1 and m[off][e].max() == 100
+    assert np.array_equal(m, workloads.request_matrix(pool, 5, 600, 0.2, "int32"))  # deterministic per k
+    assert not np.array_equal(m, workloads.request_matrix(pool, 6, 600, 0.2, "int32"))
+    f = workloads.request_matrix(pool, 7, 300, 0.4, "float32")
+    ef = np.isfinite(f[~np.eye(300, dtype=bool)])
+    assert abs(ef.mean() - 0.4) < 0.02 and np.all(f[~np.eye(300, dtype=bool)][ef] > 0)
+    big = np.zeros((50, 64), np.int32)  # in place, with a row stride past n
+    workloads.request_matrix(pool, 8, 50, 0.3, "int32", out=big[:, :50])
+    assert np.array_equal(big[:, :50], workloads.request_matrix(pool, 8, 50, 0.3, "int32"))
+    assert np.all(big[:, 50:] == 0)

@@ -144,9 +144,15 @@ def batch_specs(count: int = 2048, n_lo: int = 32, n_hi: int = 1024, p_lo: float
     return ns, ps
 
 
-def batch_graphs(ns, ps, dtype="int32", lo=1, hi=100, inf: int = INF_I32):
-    return [er_graph(int(n), float(p), dtype=dtype, lo=lo, hi=hi, seed=1000 + g, inf=inf, threads=1)
-            for g, (n, p) in enumerate(zip(ns, ps))]
+def batch_graphs(ns, ps, dtype="int32", lo=1, hi=100, inf: int = INF_I32, dist: str = "uniform",
+                 threads: int | None = None):
+    """Graph g = er_graph(ns[g], ps[g], dtype, dist, lo, hi, seed=1000 + g) (float32: dist
+    "lognormal" with lo = mu, hi = sigma, as in er_graph), drawn on a pool of threads."""
+    def one(g):
+        return er_graph(int(ns[g]), float(ps[g]), dtype=dtype, dist=dist, lo=lo, hi=hi, seed=1000 + g, inf=inf,
+                        threads=1)
+    with ThreadPoolExecutor(threads or min(16, os.cpu_count() or 1)) as ex:
+        return list(ex.map(one, range(len(ns))))
 
 
 def request_library(count: int = 128, n_lo: int = 64, n_hi: int = 8192, p_lo: float = 0.01, p_hi: float = 0.5,
@@ -167,6 +173,62 @@ def request_library(count: int = 128, n_lo: int = 64, n_hi: int = 8192, p_lo: fl
     with ThreadPoolExecutor(threads or min(16, os.cpu_count() or 1)) as ex:
         mats = list(ex.map(make, range(count)))
     return ns, ps, mats
+
+
+class RequestPool:
+    """Pre-drawn variates from which request matrices are cut quickly (a serving stream needs
+    several GB/s of fresh cost matrices, more than drawing each one from scratch delivers):
+    ``u`` holds uniform 32-bit integers, ``logn`` float32 lognormal(0, 1) weights.  Request k
+    takes windows of both at offsets drawn from its own seeded stream (see request_matrix)."""
+
+    def __init__(self, seed: int = 0, size_u: int = 1 << 28, size_w: int = 1 << 26, threads: int | None = None):
+        blocks = 64
+        self.u = np.empty(size_u, np.uint32)
+        self.logn = np.empty(size_w, np.float32)
+
+        def fill(b):
+            rng = np.random.Generator(np.random.PCG64([int(seed), 0x504F4F4C, int(b)]))
+            lo, hi = size_u * b // blocks, size_u * (b + 1) // blocks
+            self.u[lo:hi] = rng.integers(0, 1 << 32, size=hi - lo, dtype=np.uint32)
+            lo, hi = size_w * b // blocks, size_w * (b + 1) // blocks
+            self.logn[lo:hi] = rng.lognormal(0.0, 1.0, size=hi - lo).astype(np.float32)
+
+        with ThreadPoolExecutor(threads or min(16, os.cpu_count() or 1)) as ex:
+            list(ex.map(fill, range(blocks)))
+
+
+def request_matrix(pool: RequestPool, k: int, n: int, p: float, dtype: str, out: np.ndarray | None = None,
+                   seed: int = 0, inf: int = INF_I32) -> np.ndarray:
+    """The cost matrix of request k: a directed Erdos-Renyi graph on n vertices with edge
+    probability p.  Entry (i, j), i != j, is an edge when the pool variate u at the request's
+    offset o + i n + j is below p 2^32; an int32 weight is 1 + (u mod 100) (uniform in [1, 100]
+    up to a bias below 100 / (p 2^32)), a float32 weight the lognormal(0, 1) variate at the
+    request's second offset.  Missing edges hold the sentinel (+inf for float32); the diagonal
+    is 0.  ``out`` (n x n, any row stride) receives it in place when given."""
+    nn = n * n
+    rng = np.random.Generator(np.random.PCG64([int(seed), 0x52455155, int(k)]))
+    o = int(rng.integers(0, pool.u.size - nn + 1))
+    ow = int(rng.integers(0, pool.logn.size - min(nn, pool.logn.size) + 1))
+    thr = np.uint32(min(int(p * 4294967296.0), 4294967295))
+    dt = np.dtype(dtype)
+    if out is None:
+        out = np.empty((n, n), dt)
+    rows = max(1, (1 << 22) // max(n, 1))  # about 4M entries per step
+    for r0 in range(0, n, rows):
+        r1 = min(n, r0 + rows)
+        u = pool.u[o + r0 * n: o + r1 * n].reshape(r1 - r0, n)
+        edge = u < thr
+        if dt == np.int32:
+            w = (u % np.uint32(100)).astype(np.int32) + 1
+            out[r0:r1] = np.where(edge, w, np.int32(inf))
+        else:
+            a = (ow + r0 * n) % pool.logn.size
+            b = a + (r1 - r0) * n
+            wv = pool.logn[a:b] if b <= pool.logn.size else np.concatenate([pool.logn[a:], pool.logn[:b - pool.logn.size]])
+            out[r0:r1] = np.where(edge, wv.reshape(r1 - r0, n), np.float32(np.inf))
+        idx = np.arange(r0, r1)
+        out[idx, idx] = 0
+    return out
 
 
 def poisson_requests(rate: float = 200.0, duration: float = 60.0, n_lo: int = 64, n_hi: int = 8192,
