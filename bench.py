@@ -359,6 +359,8 @@ def config_of(args, w, world):
                 "graphs": "each request draws its own n, p and dtype; its ER matrix is cut from a pre-drawn pool of "
                           "uniform and lognormal variates at request-specific offsets, on host threads, during the run",
                 "admission": "HBM arena 16 GiB, first fit", "batching": "n <= 1024 continuously batched",
+                "large": ("up to 2 closures of n >= 2048 share the GPU" if w.get("closed") else
+                          "one closure of n >= 2048 at a time"),
                 "plans": ("n > 1024: the trained cost model (cost_model.json) picks FW, R-Kleene or squaring"
                           if args.serve_policy == "model" else "n > 1024: always FW"),
                 "parallelism": f"replicas{world}"}
@@ -480,13 +482,9 @@ def run_ours(args, w, rank, world, local_rank):
     clocks = sampler.stop()
     ms = sum(a.elapsed_time(b) for a, b in ev)
     dom_mode = 0 if w["algo"] in ("gemm", "rkleene") else 2
-    # The dominant launches: the engine mode's unconditional launches, or its conditional ones
-    # (mode + 16: a pass that runs only when a device word says so, such as the 32-bit pass
-    # of an int32 closure too heavy for the 16-bit pass), whichever took longer.
+    # The dominant launches: the engine mode's records in the closure's main sequence (mode + 16
+    # marks launches outside it, such as passes that return at once).
     k_ms, k_launches, k_pairs = apsp.apsp_trace_read(dom_mode)
-    c_ms, c_launches, c_pairs = apsp.apsp_trace_read(dom_mode + 16)
-    if c_ms > k_ms:
-        k_ms, k_launches, k_pairs = c_ms, c_launches, c_pairs
     apsp.apsp_trace_read(-1)
 
     ops_step = 2.0 * n ** 3
@@ -861,8 +859,9 @@ def run_serve(args, w, rank, world, local_rank):
     host = serve.HostArena(min(need, 48 << 30) if ts == 0.0 else (24 << 30))
     model = apsp_planner.CostModel.load(apsp_planner.DEFAULT_MODEL, device=dev) if args.serve_policy == "model" else None
 
-    def server():
-        return serve.Server(device=dev, arena_bytes=16 << 30, small_max=1024, slots=4, planner=model)
+    def server():  # the closed loop measures throughput: two large closures may share the GPU
+        return serve.Server(device=dev, arena_bytes=16 << 30, small_max=1024, slots=4, planner=model,
+                            big_slots=2 if ts == 0.0 else 1)
 
     # warm-up: a short stream through both paths (first-launch set-up of every kernel)
     wreq = serve.stream_requests(np.linspace(0, 0.2, 64), ns[:64], ps[:64], dts[:64])

@@ -352,11 +352,10 @@ int apsp_batched_host(const void *h_in, void *h_out, void *pool, const int64_t *
  * product and blocked-FW phases 2 and 3) record a CUDA event before and after itself on its
  * stream.  apsp_trace_read(mode, ...) waits for those events, returns the summed elapsed
  * time (ms), the number of launches and their algorithmic (min,+) pairs for engine mode
- * `mode` (0 = product, 1 = FW panels, 2 = FW remaining tiles; 16 + those: the 32-bit pass
- * of an int32 FW, which runs unless a 16-bit pass did the work; 32 + those: passes that
- * normally return at once, such as the exact int32 pass after a certified truncated one;
- * -1 = all), then discards the records it returned.  Host-global; not for use inside
- * CUDA-graph capture. */
+ * `mode` (0 = product, 1 = FW panels, 2 = FW remaining tiles; 16 + those: launches outside
+ * the closure's main sequence, such as the exact int32 pass that returns at once after a
+ * certified truncated one, or the small sub-closures of a 256-vertex block; -1 = all), then
+ * discards the records it returned.  Host-global; not for use inside CUDA-graph capture. */
 int apsp_trace_enable(int on);
 int apsp_trace_read(int mode, double *total_ms, int64_t *launches, double *pairs);
 

@@ -14,8 +14,8 @@ struct Bound {
   const int *w;
   int64_t mult;
   const int *cert = nullptr;
-  // Two device words, zero at the start: the tile counters of phase 3's dynamic scheduling
-  // (TileProblem::tile_counter; null: static order, and phase 1 in its own launch).
+  // Three device words, zero at the start: the counters of phase 3's dynamic scheduling
+  // (TileProblem::tile_counter; null: static order, and phases 1 and 2 in launches of their own).
   int *counters = nullptr;
 };
 

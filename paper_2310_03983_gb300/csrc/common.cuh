@@ -147,6 +147,30 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsign
   return false;
 }
 
+// Bounded wait until the device counter *c reaches `need` (loads with acquire semantics at GPU
+// scope; the writers store, then add with release semantics: counter_add_release).  Returns
+// false (and flags APSP_ERR_TIMEOUT) if the limit is reached.
+__device__ __forceinline__ bool counter_wait(const int *c, int need, unsigned int *st) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
+    if (v >= need) return true;
+    __nanosleep(32);
+  }
+  flag_status(st, APSP_ERR_TIMEOUT);
+  return false;
+}
+
+__device__ __forceinline__ void counter_add_release(int *c, int v) {
+  asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(c), "r"(v) : "memory");
+}
+
+// Orders this thread's earlier generic-proxy accesses (the acquire above) before its later
+// async-proxy ones (TMA loads of the data the counter guards).
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
 __device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap *m) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(m)) : "memory");
 }

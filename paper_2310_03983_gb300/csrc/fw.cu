@@ -102,11 +102,12 @@ __global__ void fw_decide_kernel(int *words, const int *cert, int may24, int64_t
   words[16] = !use16 && may24 && (int64_t)w * mult >= kCap24 && c <= kUse24MaxWeight;
 }
 
-// Packs the column panel D[:, kb0 .. kb0+bw) into A16 (n rows x kFw16Words words) and the row
-// panel D[kb0 .. kb0+bw, :] into B16 (kFw16Words words x ldb16) as 16-bit pairs of consecutive
-// k, every value capped at CAP (the sentinel included).
+// Packs the column panel D[:, kb0 .. kb0+bw) into A16 (n rows x lda16 words) and the row panel
+// D[kb0 .. kb0+bw, :] into B16 (kFw16Words words x ldb16) as 16-bit pairs of consecutive k,
+// every value capped at CAP (the sentinel included).
 __global__ void __launch_bounds__(256) fw_pack16_kernel(const int *d, int64_t ld, int64_t n, int64_t kb0, int bw,
-                                                        int *A16, int *B16, int64_t ldb16, const int *words) {
+                                                        int *A16, int64_t lda16, int *B16, int64_t ldb16,
+                                                        const int *words) {
   if (!words[4]) return;
   const int kw = (bw + 1) >> 1;
   const int64_t na = n * kw, total = na + (int64_t)kw * n;
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(256) fw_pack16_kernel(const int *d, int64_t ld
       const int w = (int)(e - i * kw), k = 2 * w;
       const int *row = d + i * ld + kb0;
       const int lo = min(row[k], kCap16), hi = k + 1 < bw ? min(row[k + 1], kCap16) : kCap16;
-      A16[i * kFw16Words + w] = (hi << 16) | lo;
+      A16[i * lda16 + w] = (hi << 16) | lo;
     } else {
       const int64_t f = e - na;
       const int w = (int)(f / n);
@@ -168,18 +169,23 @@ static int certify(void *d, int64_t ld, int64_t n, int inf, int *words, const in
 }
 
 // Scratch of the 16-bit pass: the packed column and row panels, and copies of the int32 row and
-// column panels (the operands of the in-place panel products).
+// column panels (the operands of the in-place panel products).  Both packed panels are whole
+// tiles long (round_up(n, 128) rows of the column panel, words per row of the row panel): the
+// tiles store all 128 rows and columns of their register tile.
+static int64_t fw16_ldb(int64_t n) { return round_up(n, kBN); }
 size_t fw16_panel_bytes(int64_t n) {
   const int64_t ldp = round_up(n, 4);
-  return (size_t)round_up(n * kFw16Words * 4, 256) + (size_t)round_up(kFw16Words * ldp * 4, 256) +
-         (size_t)round_up(kFw16Block * ldp * 4, 256) + (size_t)round_up(n * kFw16Block * 4, 256);
+  return (size_t)round_up(round_up(n, kBM) * kFw16Words * 4, 256) +
+         (size_t)round_up(kFw16Words * fw16_ldb(n) * 4, 256) + (size_t)round_up(kFw16Block * ldp * 4, 256) +
+         (size_t)round_up(n * kFw16Block * 4, 256);
 }
 
 // The plain three-phase loop; every launch returns at once unless *run_if (when given) is set.
-// trace_class: added to the engine mode in trace records (kTraceFallback for passes that
+// trace_class: added to the engine mode in trace records (kTraceSide for passes that
 // normally return at once, and for the small sub-closures of the wide pass).
-// counters (may be null): phase 3 hands out its tiles dynamically and closes the next diagonal
-// tile itself (TileProblem::close_next), so phase 1 has a launch of its own only for block 0.
+// counters (may be null): phase 3 hands out its tiles dynamically and performs phases 1 and 2
+// of the next block itself (TileProblem::close_next), so the closure is phase 1 and 2 of block
+// 0 and then one launch per block.
 static int fw_loop(void *d, int64_t n, int64_t ld, int dtype, const CUtensorMap &mA, const CUtensorMap &mB,
                    const CUtensorMap &mC, TileProblem p, const int *run_if, cudaStream_t s, int trace_class = 0,
                    int *counters = nullptr) {
@@ -191,13 +197,15 @@ static int fw_loop(void *d, int64_t n, int64_t ld, int dtype, const CUtensorMap 
     if ((kb == 0 || !counters) && (r = launch_fw_diag(d, ld, n, kb, dtype, s, run_if))) return r;
     if (nb == 1) break;
     p.kb = kb;
-    p.ntiles = 2 * (nb - 1);
-    p.tile_counter = nullptr;
-    p.close_next = 0;
-    if ((r = launch_tgemm(kModeFwPanels, false, dtype, mA, mB, mC, p, s))) return r;
-    p.ntiles = (nb - 1) * (nb - 1);
+    if (kb == 0 || !counters) {
+      p.ntiles = 2 * (nb - 1);
+      p.tile_counter = nullptr;
+      p.close_next = 0;
+      if ((r = launch_tgemm(kModeFwPanels, false, dtype, mA, mB, mC, p, s))) return r;
+    }
     p.tile_counter = counters;
     p.close_next = counters && kb + 1 < nb;
+    p.ntiles = (nb - 1) * (nb - 1) + (p.close_next ? 2 * (nb - 1) : 0);
     if ((r = launch_tgemm(kModeFwRest, true, dtype, mA, mB, mC, p, s))) return r;
   }
   return APSP_OK;
@@ -235,7 +243,7 @@ int fw_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bound b, cu
   APSP_LAUNCH_CHECK();
   if ((r = fw_wide_pass(d, n, ld, dtype, inf_i, b, s, panels16, p, mA, mB, mC))) return r;
   if ((r = certify(d, ld, n, inf_i, words, cert, s))) return r;
-  return fw_loop(d, n, ld, dtype, mA, mB, mC, p, words + 6, s, kTraceFallback, b.counters);
+  return fw_loop(d, n, ld, dtype, mA, mB, mC, p, words + 6, s, kTraceSide, b.counters);
 }
 
 // The pass over diagonal blocks of bt = 1 or 2 tiles: phases 1 and 2 exact, the block's panels
@@ -248,30 +256,46 @@ static int fw_wide_pass(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bo
   const int64_t ldp = round_up(n, 4);
   uint8_t *sp = reinterpret_cast<uint8_t *>(panels16);
   int *A16 = reinterpret_cast<int *>(sp);
-  sp += round_up(n * kFw16Words * 4, 256);
+  const int64_t arows = round_up(n, kBM);  // rows of one set of the packed column panel
+  sp += round_up(arows * kFw16Words * 4, 256);
   int *B16 = reinterpret_cast<int *>(sp);
-  sp += round_up(kFw16Words * ldp * 4, 256);
+  const int64_t ldb16 = fw16_ldb(n);
+  sp += round_up(kFw16Words * ldb16 * 4, 256);
   int *Rc = reinterpret_cast<int *>(sp);
   sp += round_up(kFw16Block * ldp * 4, 256);
   int *Cc = reinterpret_cast<int *>(sp);
-  CUtensorMap pA, pB;
-  if ((r = make_operand_maps(A16, n, kFw16Words, kFw16Words, APSP_I32, &pA, nullptr, nullptr))) return r;
-  if ((r = make_operand_maps(B16, kFw16Words, n, ldp, APSP_I32, nullptr, &pB, nullptr))) return r;
   const int64_t cap = (int64_t)sm_count() * 8;
   const int64_t bt = n >= kFw16WideN ? kFw16Tiles : 1, blk = bt * kBM;
+  // A16 rows hold the block's packed words: 64 for 128-vertex blocks (written by the panel tiles
+  // themselves), kFw16Words for 256-vertex blocks (written by fw_pack16_kernel).
+  // 128-vertex blocks: two sets of packed panels one below the other (set s of the column panel
+  // at row s * arows of A16, 64 words per row; set s of the row panel at row 64 s of B16),
+  // written by the panel tiles themselves and by the tiles of the next block row and column (no
+  // packing pass).  256-vertex blocks: one set, 128 words per row, written by fw_pack16_kernel.
+  const int64_t lda16 = bt == 1 ? kBM / 2 : kFw16Words;
+  CUtensorMap pA, pB;
+  if ((r = make_operand_maps(A16, bt == 1 ? 2 * arows : n, lda16, lda16, APSP_I32, &pA, nullptr, nullptr))) return r;
+  if ((r = make_operand_maps(B16, kFw16Words, n, ldb16, APSP_I32, nullptr, &pB, nullptr))) return r;
   const int64_t nbb = cdiv(n, blk), nt = cdiv(n, kBM);
   int *D = reinterpret_cast<int *>(d);
   for (int64_t kbb = 0; kbb < nbb; ++kbb) {
     const int64_t kb0 = kbb * blk, bw = std::min<int64_t>(blk, n - kb0);
     int *sub = D + kb0 * ld + kb0, *rowp = D + kb0 * ld, *colp = D + kb0;
     if (bt == 1) {  // phases 1 and 2 of a single-tile block, in place (as in the plain loop); with
-                    // counters, phase 1 of every block after the first ran in the previous phase 3
+                    // counters, those of every block after the first ran in the previous phase 3
       if ((kbb == 0 || !b.counters) && (r = launch_fw_diag(d, ld, n, kbb, dtype, s, nullptr))) return r;
-      TileProblem pp = p;
-      pp.kb = kbb;
-      pp.ntiles = 2 * (nt - 1);
-      pp.trace_class = kTraceFallback;
-      if ((r = launch_tgemm(kModeFwPanels, false, dtype, mA, mB, mC, pp, s))) return r;
+      if (kbb == 0 || !b.counters) {
+        TileProblem pp = p;
+        pp.kb = kbb;
+        pp.ntiles = 2 * (nt - 1);
+        pp.trace_class = kTraceSide;
+        pp.pk_a[0] = A16;
+        pp.pk_a[1] = A16 + arows * lda16;
+        pp.pk_b[0] = B16;
+        pp.pk_b[1] = B16 + (kBM / 2) * ldb16;
+        pp.pk_ldb = ldb16;
+        if ((r = launch_tgemm(kModeFwPanels, false, dtype, mA, mB, mC, pp, s))) return r;
+      }
     } else {
       // Phase 1: close the diagonal block (itself a small blocked Floyd-Warshall, exact).
       CUtensorMap dA, dB, dC;
@@ -280,7 +304,7 @@ static int fw_wide_pass(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bo
       ps.n = bw;
       ps.nb = cdiv(bw, kBM);
       ps.C = sub;
-      if ((r = fw_loop(sub, bw, ld, dtype, dA, dB, dC, ps, nullptr, s, kTraceFallback))) return r;
+      if ((r = fw_loop(sub, bw, ld, dtype, dA, dB, dC, ps, nullptr, s, kTraceSide))) return r;
       // Phase 2: the row panel becomes D* (x) (row panel) and the column panel (column panel) (x)
       // D*, each one exact product (D* is closed, so its zero diagonal keeps the old entry) read
       // from a copy of the panel; the block's own entries are reproduced (D* (x) D* = D*).
@@ -290,10 +314,12 @@ static int fw_wide_pass(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bo
       if ((r = gemm_aligned(colp, ld, Cc, kFw16Block, sub, ld, n, bw, bw, dtype, false, inf_i, b, s))) return r;
     }
     // Phase 3, K = bw: on the packed panels, or the 32-bit alternative.
-    const int64_t work = 2 * n * ((bw + 1) >> 1);
-    fw_pack16_kernel<<<(int)std::min<int64_t>(cap, cdiv(work, 256)), 256, 0, s>>>(D, ld, n, kb0, (int)bw, A16, B16,
-                                                                                  ldp, words);
-    APSP_LAUNCH_CHECK();
+    if (bt > 1) {
+      const int64_t work = 2 * n * ((bw + 1) >> 1);
+      fw_pack16_kernel<<<(int)std::min<int64_t>(cap, cdiv(work, 256)), 256, 0, s>>>(D, ld, n, kb0, (int)bw, A16,
+                                                                                    lda16, B16, ldb16, words);
+      APSP_LAUNCH_CHECK();
+    }
     const int64_t ec = std::min<int64_t>(bt, nt - kbb * bt), rest = nt - ec;
     if (rest == 0) continue;
     TileProblem q = p;
@@ -304,14 +330,26 @@ static int fw_wide_pass(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bo
     q.alt_if = words + 7;
     q.f32_if = words + 16;
     q.no_trace = 1;
+    double pairs = (double)(n - bw) * (double)(n - bw) * (double)bw;
     if (bt == 1) {
+      q.pk_a[0] = A16;
+      q.pk_a[1] = A16 + arows * lda16;
+      q.pk_b[0] = B16;
+      q.pk_b[1] = B16 + (kBM / 2) * ldb16;
+      q.pk_ldb = ldb16;
+      q.pk_arows = arows;
       q.tile_counter = b.counters;
       q.close_next = b.counters && kbb + 1 < nbb;
+      if (q.close_next) {  // and phase 2 of the next block
+        const double bw1 = (double)std::min<int64_t>(kBM, n - (kbb + 1) * kBM);
+        q.ntiles += 2 * rest;
+        pairs += 2.0 * bw1 * bw1 * ((double)n - bw1);
+      }
     }
     void *tev = nullptr;
     if (trace_on()) trace_begin(s, &tev);
     if ((r = launch_tgemm(kModeFwRest16, true, dtype, pA, pB, mC, q, s, &mA, &mB))) return r;
-    if (tev) trace_end(s, tev, kModeFwRest, (double)(n - bw) * (double)(n - bw) * (double)bw);
+    if (tev) trace_end(s, tev, kModeFwRest, pairs);
   }
   return APSP_OK;
 }
@@ -349,9 +387,9 @@ int closure_entry(int algo, void *d, int64_t n, int64_t ld, int dtype, const voi
   uint8_t *wsp = reinterpret_cast<uint8_t *>(ws);
   int *words = reinterpret_cast<int *>(wsp);  // [0]: largest finite weight, [1]: 0
   wsp += kFlagBytes;
-  if (cudaMemsetAsync(words, 0, 16, s) != cudaSuccess) r = APSP_ERR_CUDA;
+  if (cudaMemsetAsync(words, 0, kFlagBytes, s) != cudaSuccess) r = APSP_ERR_CUDA;
   Bound bound = {dtype == APSP_I32 ? words : nullptr, n - 1};
-  bound.counters = words + 2;  // zeroed with the bound words above
+  bound.counters = words + 40;  // three words, zeroed with the rest of the block
   void *work = d;
   int64_t ldw = ld;
   if (ld % 4 != 0) {  // repack into an aligned copy at the front of the workspace

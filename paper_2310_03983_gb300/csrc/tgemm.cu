@@ -35,10 +35,14 @@ struct TileCoords {
   int a_row, a_col, b_row, b_col, c_row, c_col;
   int m_valid, n_valid, k_len;
   bool skip;  // grouped FW: this graph does not take part in the launch
-  // Grouped 16-bit launches: packed copies of the result -- column pairs into set pa_set of
-  // the packed column panels (at the tile's rows), row pairs into set pb_set of the packed row
-  // panels (rows pb_row.., the tile's columns); -1: none.
+  // 16-bit launches: packed copies of the result -- column pairs into set pa_set of the packed
+  // column panels (at the tile's rows), row pairs into set pb_set of the packed row panels
+  // (grouped: rows pb_row.., single matrix: the set's 64 rows; the tile's columns); -1: none.
   int pa_set, pb_set, pb_row;
+  // Fused launches (TileProblem::close_next): dep -- the next block's panel tiles read this
+  // tile, so it is counted once stored; wait -- a panel tile, whose operands must be counted
+  // complete before they are loaded.
+  bool dep, wait;
 };
 
 // Tile t of a grouped FW launch: find its group and graph (all tiles of one graph are
@@ -48,6 +52,7 @@ struct TileCoords {
 template <int MODE>
 __device__ __forceinline__ TileCoords grouped_tile_coords(const TileProblem &p, int64_t t) {
   TileCoords tc;
+  tc.dep = tc.wait = false;
   unsigned rem = (unsigned)t, per = 1, row0 = 0, gnb = 1, first = 0;
   const unsigned kb = (unsigned)p.kb;
   bool found = false;
@@ -132,15 +137,6 @@ __device__ __forceinline__ TileCoords grouped_tile_coords(const TileProblem &p, 
   return tc;
 }
 
-// Phase 3 with close_next hands out the next diagonal tile (kb + 1, kb + 1) first: it moves to
-// index 0 and the tiles before it shift up by one.  In the skip-kb numbering of the remaining
-// tiles (row-major, per row) that tile is (kb, kb).
-__device__ __forceinline__ int64_t next_diag_first(const TileProblem &p, int64_t t, int64_t per_row) {
-  if (!p.close_next) return t;
-  const int64_t dg = p.kb * per_row + p.kb;
-  return t == 0 ? dg : (t <= dg ? t - 1 : t);
-}
-
 // G: a grouped launch (its own instantiation, so a single-matrix kernel carries none of the
 // grouped decode or packed-output epilogue).  alt: kModeFwRest16's 32-bit alternative (the
 // block's columns and rows of the matrix, K = the block width).
@@ -151,6 +147,7 @@ __device__ __forceinline__ TileCoords tile_coords(const TileProblem &p, int64_t 
   tc.skip = false;
   tc.pa_set = tc.pb_set = -1;
   tc.pb_row = 0;
+  tc.dep = tc.wait = false;
   if (MODE == kModeGemm) {
     // Grouped rasterisation: 8 tile-rows advance together so A slabs are reused from L2.
     const int64_t G = 8;
@@ -167,54 +164,111 @@ __device__ __forceinline__ TileCoords tile_coords(const TileProblem &p, int64_t 
     tc.m_valid = (int)(p.M - m0 < kBM ? p.M - m0 : kBM);
     tc.n_valid = (int)(p.N - n0 < kBN ? p.N - n0 : kBN);
     tc.k_len = (int)p.K;
-  } else {
-    const int64_t nb1 = p.nb - 1;
-    const int kb0 = (int)(p.kb * kBM);
-    const int bk = (int)(p.n - kb0 < kBM ? p.n - kb0 : kBM);
-    int i, j;
-    if (MODE == kModeFwPanels) {
-      if (t < nb1) {  // row panel tile (kb, j): D[kb][j] = D[kb][kb]* (x) D[kb][j]
-        j = (int)(t + (t >= p.kb));
-        tc.a_row = kb0; tc.a_col = kb0;
-        tc.b_row = kb0; tc.b_col = j * kBN;
-        tc.c_row = kb0; tc.c_col = j * kBN;
-      } else {        // column panel tile (i, kb): D[i][kb] = D[i][kb] (x) D[kb][kb]*
-        i = (int)(t - nb1);
-        i += (i >= p.kb);
-        tc.a_row = i * kBM; tc.a_col = kb0;
-        tc.b_row = kb0;     tc.b_col = kb0;
-        tc.c_row = i * kBM; tc.c_col = kb0;
-      }
-    } else if (MODE == kModeFwRest16) {  // as below, for a block of bt tiles, K in packed words
-      const int64_t bt = p.bt > 1 ? p.bt : 1;
-      const int64_t nt = (p.n + kBM - 1) / kBM, e0 = p.kb * bt;
-      const int64_t ec = nt - e0 < bt ? nt - e0 : bt, rest = nt - ec;
-      t = next_diag_first(p, t, rest);
-      i = (int)(t / rest);
-      j = (int)(t - (int64_t)i * rest);
-      i += (i >= e0) ? (int)ec : 0;
-      j += (j >= e0) ? (int)ec : 0;
-      const int k0 = alt ? (int)(e0 * kBM) : 0;
-      tc.a_row = i * kBM; tc.a_col = k0;
-      tc.b_row = k0;      tc.b_col = j * kBN;
-      tc.c_row = i * kBM; tc.c_col = j * kBN;
-    } else {          // D[i][j] = min(D[i][j], D[i][kb] (x) D[kb][j]), i, j != kb
-      t = next_diag_first(p, t, nb1);
-      i = (int)(t / nb1);
-      j = (int)(t - (int64_t)i * nb1);
-      i += (i >= p.kb);
-      j += (j >= p.kb);
-      tc.a_row = i * kBM; tc.a_col = kb0;
-      tc.b_row = kb0;     tc.b_col = j * kBN;
-      tc.c_row = i * kBM; tc.c_col = j * kBN;
-    }
+  } else if (MODE == kModeFwRest16 && p.bt > 1) {  // phase 3 of a block of bt tiles, K in packed words
+    const int64_t bt = p.bt;
+    const int64_t nt = (p.n + kBM - 1) / kBM, e0 = p.kb * bt;
+    const int64_t ec = nt - e0 < bt ? nt - e0 : bt, rest = nt - ec;
+    int i = (int)(t / rest), j = (int)(t - (t / rest) * rest);
+    i += (i >= e0) ? (int)ec : 0;
+    j += (j >= e0) ? (int)ec : 0;
+    const int k0 = alt ? (int)(e0 * kBM) : 0;
+    tc.a_row = i * kBM; tc.a_col = k0;
+    tc.b_row = k0;      tc.b_col = j * kBN;
+    tc.c_row = i * kBM; tc.c_col = j * kBN;
     tc.m_valid = (int)(p.n - tc.c_row < kBM ? p.n - tc.c_row : kBM);
     tc.n_valid = (int)(p.n - tc.c_col < kBN ? p.n - tc.c_col : kBN);
-    if (MODE == kModeFwRest16) {
-      const int64_t w = (p.bt > 1 ? p.bt : 1) * kBM, b0 = p.kb * w, len = p.n - b0 < w ? p.n - b0 : w;
-      tc.k_len = alt ? (int)len : (int)((len + 1) >> 1);
+    const int64_t w = bt * kBM, b0 = p.kb * w, len = p.n - b0 < w ? p.n - b0 : w;
+    tc.k_len = alt ? (int)len : (int)((len + 1) >> 1);
+  } else {
+    // Blocked FW over 128-vertex blocks: tile (i, j) of phase 2 (mode 1) or 3 (modes 2, 3) runs
+    // over the k range of block kblk -- kb, or kb + 1 for the panel tiles of a fused launch.
+    const int64_t nb1 = p.nb - 1;
+    const int kb = (int)p.kb;
+    int i, j, kblk = kb;
+    bool panel = MODE == kModeFwPanels;
+    if (MODE == kModeFwPanels) {
+      if (t < nb1) {  // row panel tile (kb, j): D[kb][j] = D[kb][kb]* (x) D[kb][j]
+        i = kb;
+        j = (int)(t + (t >= kb));
+      } else {        // column panel tile (i, kb): D[i][kb] = D[i][kb] (x) D[kb][kb]*
+        i = (int)(t - nb1);
+        i += (i >= kb);
+        j = kb;
+      }
+    } else if (p.close_next) {  // the fused order (TileProblem::close_next)
+      const int kb1 = kb + 1;
+      const int64_t R = nb1, R1 = nb1 - 1;
+      if (t == 0) {                 // the next diagonal tile
+        i = j = kb1;
+        tc.dep = true;
+      } else if (t < R) {           // the rest of block row kb1
+        const int x = (int)(t - 1);
+        i = kb1;
+        j = x + (x >= kb ? 2 : 0);
+        tc.dep = true;
+      } else if (t < 2 * R - 1) {   // the rest of block column kb1
+        const int x = (int)(t - R);
+        i = x + (x >= kb ? 2 : 0);
+        j = kb1;
+        tc.dep = true;
+      } else if (t < R * R) {       // the rest of phase 3, row by row
+        const int64_t u = t - (2 * R - 1);
+        const int ii = (int)(u / R1), jj = (int)(u - (u / R1) * R1);
+        i = ii + (ii >= kb ? 2 : 0);
+        j = jj + (jj >= kb ? 2 : 0);
+      } else {                      // phase 2 of block kb1: row panel tiles, then column panel tiles
+        const int v = (int)(t - R * R);
+        if (v < R) {
+          i = kb1;
+          j = v + (v >= kb1);
+        } else {
+          i = (v - (int)R) + ((v - (int)R) >= kb1);
+          j = kb1;
+        }
+        kblk = kb1;
+        panel = true;
+        tc.wait = true;
+      }
+    } else {          // D[i][j] = min(D[i][j], D[i][kb] (x) D[kb][j]), i, j != kb, row by row
+      i = (int)(t / nb1);
+      j = (int)(t - (t / nb1) * nb1);
+      i += (i >= kb);
+      j += (j >= kb);
+    }
+    const int k0 = kblk * kBM, bk = (int)(p.n - k0 < kBM ? p.n - k0 : kBM);
+    // Operands: the packed panels of block kblk (set kblk & 1: the column panel's rows i, the row
+    // panel's columns j -- for a panel tile the closed diagonal tile's packed copy on one side),
+    // or the matrix's own block kblk.
+    const bool p16 = MODE == kModeFwRest16 && !alt;
+    const int s = kblk & 1;
+    if (p16) {
+      tc.a_row = (int)(s * p.pk_arows) + i * kBM; tc.a_col = 0;
+      tc.b_row = s * (kBM / 2);                   tc.b_col = j * kBN;
+      tc.k_len = (bk + 1) >> 1;
     } else {
+      tc.a_row = i * kBM; tc.a_col = k0;
+      tc.b_row = k0;      tc.b_col = j * kBN;
       tc.k_len = bk;
+    }
+    tc.c_row = i * kBM;
+    tc.c_col = j * kBN;
+    tc.m_valid = (int)(p.n - tc.c_row < kBM ? p.n - tc.c_row : kBM);
+    tc.n_valid = (int)(p.n - tc.c_col < kBN ? p.n - tc.c_col : kBN);
+    // Packed copies of the result (phase 3 reads them from set kblk & 1; the tiles of block row /
+    // column kblk + 1 are also the next block's operands, set s ^ 1).
+    if (MODE == kModeFwPanels || p16) {
+      if (panel) {
+        if (i == kblk) {
+          tc.pb_set = s;
+          if (j == kblk + 1) tc.pa_set = s ^ 1;
+        } else {
+          tc.pa_set = s;
+          if (i == kblk + 1) tc.pb_set = s ^ 1;
+        }
+      } else if (tc.dep) {
+        if (i == kb + 1) tc.pb_set = s ^ 1;
+        if (j == kb + 1) tc.pa_set = s ^ 1;
+      }
     }
   }
   return tc;
@@ -342,6 +396,28 @@ __device__ __forceinline__ void consume(const TileProblem &p, const Smem &sm, in
         }
       }
     }
+    if (!G && (MODE == kModeFwPanels || (MODE == kModeFwRest16 && CN && !alt)) && !fstore && p.pk_a[0] &&
+        (tc.pa_set >= 0 || tc.pb_set >= 0)) {  // packed 16-bit operands of phase 3 / the next panels
+      // Columns (column pairs) and rows (row pairs) past the matrix's last vertex become CAP,
+      // the padding of a partial last k-word.
+      int v[8][8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const bool pad = tm + 16 * i >= tc.m_valid || 4 * tn + (j & 3) + 64 * (j >> 2) >= tc.n_valid;
+          v[i][j] = pad ? kCap16 : AR::to(acc[i][j]);
+        }
+      if (tc.pa_set >= 0) store_col_pairs16(v, tm, tn, p.pk_a[tc.pa_set] + (int64_t)tc.c_row * 64);
+      if (tc.pb_set >= 0) store_row_pairs16(v, tm, tn, lane, p.pk_b[tc.pb_set] + tc.c_col, p.pk_ldb);
+    }
+    if (CN && tc.dep) {  // count the tile once all of its stores are done (fused launches)
+      tile_barrier<1>();
+      if (warp == 0 && lane == 0) {
+        __threadfence();
+        counter_add_release(p.tile_counter + 2, 1);
+      }
+    }
     if (G && MODE != kModeGemm && !AR::kFloat && p.arith16 && p.pk_a[0] && (tc.pa_set >= 0 || tc.pb_set >= 0)) {
       int v[8][8];
 #pragma unroll
@@ -407,22 +483,28 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t phase = 0, cphase = 0, issued = 0, issued_par = 0, tqp = 0;
       bool c_issued = false, ok = true;
       uint32_t c_par = 0;
-      // Dynamic order: the index of the next tile is fetched while the current one is issued,
-      // so the atomic's round trip overlaps the stage waits.
-      int64_t t = dyn ? (int64_t)atomicAdd(p.tile_counter, 1) : (int64_t)blockIdx.x;
+      // Dynamic order: the next index is fetched once the current tile is issued (the producer
+      // runs about one tile ahead of the consumers, so the atomic's round trip overlaps their
+      // work; fetching earlier would hold tiles back from CTAs idle at the end of the launch).
+      int64_t t = blockIdx.x;
       while (ok) {
-        if (dyn) {  // hand the index to the consumers
+        if (dyn) {  // fetch the index and hand it to the consumers
+          t = atomicAdd(p.tile_counter, 1);
           if (!mbar_wait(&tq_empty[tqs], tqp ^ 1, p.status)) { ok = false; break; }
           tq[tqs] = t < p.ntiles ? (int)t : -1;
           mbar_arrive(&tq_full[tqs]);
           if (++tqs == kTileRing) { tqs = 0; tqp ^= 1; }
         }
         if (t >= p.ntiles) break;
-        const int64_t t_next = dyn ? (int64_t)atomicAdd(p.tile_counter, 1) : t + gridDim.x;
+        const int64_t t_next = t + gridDim.x;  // the static order's next tile
         const TileCoords tc = tile_coords<MODE, G>(p, t, alt);
         if (tc.skip) {  // the consumers skip the same tiles
           t = t_next;
           continue;
+        }
+        if (CN && tc.wait) {  // a panel tile of a fused launch: its operands must be stored first
+          if (!counter_wait(p.tile_counter + 2, (int)(2 * p.nb - 3), p.status)) { ok = false; break; }
+          fence_proxy_async_global();
         }
         const int nk = (tc.k_len + kBK - 1) / kBK;
         for (int kt = 0; kt < nk; ++kt) {
@@ -453,6 +535,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (dyn && atomicAdd(p.tile_counter + 1, 1) == (int)gridDim.x - 1) {
         p.tile_counter[0] = 0;
         p.tile_counter[1] = 0;
+        p.tile_counter[2] = 0;
       }
     }
     return;
@@ -483,7 +566,13 @@ template <int MODE> static double algorithmic_pairs(const TileProblem &p) {
   const int64_t w = (MODE == kModeFwRest16 && p.bt > 1 ? p.bt : 1) * kBM;
   const double bk = (double)(p.n - p.kb * w < w ? p.n - p.kb * w : w);
   const double rest = (double)p.n - bk;
-  return MODE == kModeFwPanels ? 2.0 * bk * bk * rest : rest * rest * bk;
+  if (MODE == kModeFwPanels) return 2.0 * bk * bk * rest;
+  double pairs = rest * rest * bk;
+  if (p.close_next) {  // a fused launch: phase 2 of the next block as well
+    const double bk1 = (double)(p.n - (p.kb + 1) * kBM < kBM ? p.n - (p.kb + 1) * kBM : kBM);
+    pairs += 2.0 * bk1 * bk1 * ((double)p.n - bk1);
+  }
+  return pairs;
 }
 
 template <typename T, int MODE, bool ACC, bool G = false, bool CN = false>

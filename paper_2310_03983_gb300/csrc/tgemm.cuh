@@ -92,28 +92,50 @@ struct TileProblem {
   // 3's operand (over the packed words it has itself finished reading); a tile in block row or
   // column kb + 1 (modes 1 and 3) writes it into set (kb + 1) & 1 as the next step's operand.
   int *pk_a[2], *pk_b[2];
+  // Single matrix (kModeFwPanels, and kModeFwRest16 with close_next; pk_a[0] set): packed
+  // copies in the same two sets -- set s of the column panel is pk_a[s] (64 words per row, pairs
+  // of consecutive columns), set s of the row panel pk_b[s] (leading dimension pk_ldb, pairs of
+  // consecutive rows); block step kb reads set kb & 1.  Panel tiles (mode 1) write their result
+  // into set kb & 1 as phase 3's operand, and tiles of block row / column kb + 1 also into set
+  // (kb + 1) & 1 (close_next above).  In kModeFwRest16 the sets sit one below the other in the
+  // operand maps: set s of A starts at row s * pk_arows, set s of B at row s * 64.
+  int64_t pk_ldb;
+  int64_t pk_arows;
   // Grouped FW (may be null): vertices of each staged graph; the k range of a graph's last
   // block stops there (the padding vertices are isolated and add nothing).
   const int *gsize;
   // Host only, for tracing: when > 0, the launch's algorithmic pairs (grouped launches, whose
   // work the host sums over the graphs of the launch).
   double trace_pairs;
-  // Added to the mode in trace records: 0, or kTracePass32 for the launches of an int32 FW's
-  // conditional 32-bit pass, or kTraceFallback for passes that normally return at once.
+  // Added to the mode in trace records: 0, or kTraceSide for launches outside the closure's
+  // main sequence (passes that normally return at once, the sub-closures and panels of a
+  // wide block), so that the dominant kernel's records stay apart.
   int trace_class;
   // int32 storage (may be null): when *f32_if is non-zero the fp32 sequence runs even though
   // the exact bound does not hold -- a pass truncated at 2^24 that is certified afterwards
   // (fw.cu).
   const int *f32_if;
   // FW phase-3 launches (kModeFwRest, and kModeFwRest16 with bt <= 1; single matrix; may be
-  // null): two device words, zero before the first such launch.  Tiles are then handed out by
-  // an atomic counter, in the order the CTAs ask for them, and the last CTA to finish resets
-  // both words for the next launch on the stream.
+  // null): three device words, zero before the first such launch.  Tiles are then handed out by
+  // an atomic counter (word 0), in the order the CTAs ask for them; word 2 counts the finished
+  // tiles that the next block's panel tiles read (fuse_next); the last CTA to finish (word 1)
+  // resets all three for the next launch on the stream.
   int *tile_counter;
-  // With tile_counter, and kb + 1 < nb: the launch also performs phase 1 of the next block.
-  // The diagonal tile (kb + 1, kb + 1) is handed out first, and after its phase-3 update the
-  // CTA's consumer warps close it by Eq. 1 in registers (diag.cuh) before storing it, while the
-  // other CTAs share the rest of the tiles.
+  // With tile_counter, and kb + 1 < nb: the launch also performs phases 1 and 2 of the next
+  // block kb1 = kb + 1.  Its tiles are handed out in this order:
+  //   the diagonal tile (kb1, kb1) -- after its phase-3 update the CTA's consumer warps close it
+  //     by Eq. 1 in registers (diag.cuh) before storing it;
+  //   the other tiles of block row kb1, then of block column kb1 (phase 3 of block kb);
+  //   the rest of phase 3 of block kb, row by row;
+  //   phase 2 of block kb1: its row panel tiles (kb1, j), then its column panel tiles (i, kb1),
+  //     each an in-place product with the closed diagonal tile; their producers wait (bounded)
+  //     until every tile of the first three kinds is stored (word 2 of tile_counter).
+  // A panel tile needs only tiles handed out before it, to CTAs that are already running, so
+  // the wait always ends.  In kModeFwRest16 (not its 32-bit alternative) every tile of block
+  // row or column kb1 also stores packed 16-bit copies (pk_a / pk_b, set (kb + 1) & 1) that the
+  // panel tiles read, and the panel tiles run on them in the semiring truncated at kCap16 (their
+  // result min(old entry, capped product), as phase 3's); they rewrite those copies in place as
+  // the next launch's operands, and tiles of block row / column kb + 2 also into set kb & 1.
   int close_next;
   // kModeFwRest16, single matrix (may be null): when *alt_if is non-zero the launch runs its 32-bit
   // alternative instead of the packed one -- the same tiles over the block's bt * 128 columns
@@ -194,7 +216,7 @@ int launch_scan_max(const void *x, int64_t rows, int64_t cols, int64_t ld, int i
 // Launch tracing (runtime.cu): when enabled, every tropical-GEMM-engine launch is bracketed
 // by two CUDA events on its stream and tagged with its mode plus TileProblem::trace_class, and
 // its algorithmic pair count.
-constexpr int kTracePass32 = 16, kTraceFallback = 32;
+constexpr int kTraceSide = 16;
 bool trace_on();
 void trace_begin(cudaStream_t s, void **ev0);
 void trace_end(cudaStream_t s, void *ev0, int mode, double pairs);

@@ -34,20 +34,53 @@ from . import (apsp_close_cta, apsp_fw, apsp_mlp_adam, apsp_mlp_backward, apsp_m
 CANDIDATES = (("fw", 0), ("rkleene", 128), ("rkleene", 256), ("rkleene", 512), ("rkleene", 1024), ("rkleene", 4096),
               ("cta", 0), ("squaring", 0))
 CTA_MAX_N = 1024  # beyond this one SM is far too slow to be worth timing
-IN_DIM = 10
+IN_DIM = 12
 FW16_MIN_N = 4096  # apsp_fw runs phase 3 on packed 16-bit pairs for int32 graphs this large
 HIDDEN = 64
+SMS = 152  # streaming multiprocessors of the GB300 the timing log was recorded on
+
+
+def squaring_products(n: int, density: float, dtype: str = "int32") -> float:
+    """About how many (min,+) squarings close a directed Erdos-Renyi graph: t squarings reach
+    shortest paths of up to 2^t edges, and one more product confirms that nothing changes.  The
+    edge count of the longest shortest path is estimated from the mean degree d = n p.  With
+    integer weights uniform in [1, 100] a path can stay on the d / 100 lightest edges of each
+    vertex when there are enough of them (about 1.5 ln n / ln(1 + d / 100) edges), and is never
+    much longer than the sparse-graph bound 7 ln n / ln d.  With continuous (lognormal) weights
+    it is about 1.2 ln n on dense graphs and 1.8 ln n on sparse ones (both measured on these
+    generators by Dijkstra's hop counts)."""
+    n = max(n, 2)
+    deg = max(n * density, 1e-9)
+    ln_n = math.log(n)
+    if dtype == "int32":
+        hops = 7.0 * ln_n / math.log(max(deg, 1.5))
+        if deg > 1.0:
+            hops = min(hops, 1.5 * ln_n / math.log1p(deg / 100.0))
+    else:
+        hops = (1.2 if deg >= 50.0 else 1.8) * ln_n
+    hops = min(max(hops, 1.0), float(n - 1))
+    return math.ceil(math.log2(hops)) + 1.0
+
+
+def full_product_waves(n: int) -> int:
+    """Waves of 128 x 128 output tiles of one full n x n product over the SMs (one tile per SM
+    at a time): a product of 13 x 13 tiles takes two waves of work on 152 SMs, 12 x 12 one."""
+    t = -(-max(n, 1) // 128)
+    return -(-t * t // SMS)
 
 
 def features(n: int, density: float, dtype: str, algo: str, param: int) -> list[float]:
     """Feature vector of a (graph, configuration) pair, each entry scaled to about [0, 1]."""
     rk = algo == "rkleene"
+    sq = algo == "squaring"
     return [math.log2(max(n, 1)) / 15.0, float(density), 1.0 if dtype == "float32" else 0.0,
             1.0 if algo == "fw" else 0.0, 1.0 if rk else 0.0, 1.0 if algo == "cta" else 0.0,
             math.log2(param) / 11.0 if rk else 0.0,
             (math.log2(max(n, 1)) - math.log2(param)) / 8.0 if rk and param else 0.0,
-            1.0 if algo == "squaring" else 0.0,
-            1.0 if algo == "fw" and dtype == "int32" and n >= FW16_MIN_N else 0.0]
+            1.0 if sq else 0.0,
+            1.0 if algo == "fw" and dtype == "int32" and n >= FW16_MIN_N else 0.0,
+            min(squaring_products(n, density, dtype), 15.0) / 15.0 if sq else 0.0,
+            math.log2(full_product_waves(n)) / 8.0]
 
 
 def applicable(n: int):
@@ -197,6 +230,9 @@ class CostModel:
     def load(cls, path: str, device=None) -> "CostModel":
         with open(path) as f:
             d = json.load(f)
+        if d.get("in_dim") != IN_DIM or d.get("hidden") != HIDDEN:
+            raise ValueError(f"{path}: a network of {d.get('in_dim')} features x {d.get('hidden')} units, "
+                             f"not {IN_DIM} x {HIDDEN}; retrain it with planner.main()")
         m = cls(device=device)
         m.y_shift = d["y_shift"]
         m.params = torch.tensor(d["params"], dtype=torch.float32, device=m.device)
@@ -209,15 +245,16 @@ DEFAULT_LOG = os.path.join(os.path.dirname(os.path.abspath(__file__)), "timings_
 
 def sweep_graphs(seed: int = 0):
     """The autotuning sweep: sizes 32..16384 (log-spaced), both dtypes, sparse and dense, and
-    very dense int32 graphs (p = 0.8, diameter 2) between 362 and 2896 vertices, where a few
-    full-size products of repeated squaring compete with Floyd-Warshall's block steps."""
+    denser int32 graphs (p = 0.6 and 0.8, shortest paths of 4 to 6 edges) between 362 and 2896
+    vertices, where a few full-size products of repeated squaring compete with Floyd-Warshall's
+    block steps."""
     import workloads
     sizes = sorted({int(round(2 ** e)) for e in np.arange(5.0, 14.01, 0.5)})
     for i, n in enumerate(sizes):
         for dt in ("int32", "float32"):
-            for p in ((0.02, 0.4, 0.8) if dt == "int32" and 362 <= n <= 2896 else (0.02, 0.4)):
+            for p in ((0.02, 0.4, 0.6, 0.8) if dt == "int32" and 362 <= n <= 2896 else (0.02, 0.4)):
                 kw = {"lo": 1, "hi": 100} if dt == "int32" else {"dist": "lognormal", "lo": 0.0, "hi": 1.0}
-                yield workloads.er_graph(n, p, dt, seed=seed * 100000 + 10 * n + (p > 0.1) + (p > 0.5), **kw)
+                yield workloads.er_graph(n, p, dt, seed=seed * 100000 + 10 * n + (p > 0.1) + (p > 0.5) + (p > 0.7), **kw)
 
 
 def main(log_path: str = DEFAULT_LOG, model_path: str = DEFAULT_MODEL, reps: int = 5):

@@ -282,13 +282,16 @@ class Server:
     """Continuous-batching APSP server on one GPU (see the module docstring)."""
 
     def __init__(self, device=None, arena_bytes: int = 8 << 30, small_max: int = 1024, slots: int = 4,
-                 planner=None, keep_results: bool = False):
+                 planner=None, keep_results: bool = False, big_slots: int = 1):
+        """big_slots: how many closures of at least 2048 vertices may share the GPU (1 keeps
+        their latency low; 2 lets one's latency-bound block steps overlap the other's work,
+        for throughput)."""
         import torch
         self.torch = torch
         self.dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.arena_elems = arena_bytes // 4
         self.pool = torch.empty(self.arena_elems, dtype=torch.int32, device=self.dev)
-        self.sched = Scheduler(Arena(self.arena_elems), small_max=small_max)
+        self.sched = Scheduler(Arena(self.arena_elems), small_max=small_max, big_slots=big_slots)
         self.slots = slots
         self.streams = [torch.cuda.Stream(self.dev) for _ in range(slots)]
         self.copy_in = torch.cuda.Stream(self.dev)

@@ -2,17 +2,17 @@
 as gpu_launches.  Each case checks the count of one call against the launch structure the
 entry point documents, so the figure the bench prints is tied to the code that launches:
 
-  * blocked FW, plain (fp32, or int32 below n = 4096): a1, the diagonal closure of block 0, then
-    per 128-vertex block the panels and the remaining tiles (Sec. 3.2's three phases; phase 3
-    of block kb also closes the diagonal tile of block kb + 1), only the first closure when the
-    whole matrix is one block;
-  * blocked FW, int32 from n = 4096: a1, the decision, then the pass: with 128-vertex blocks the
-    diagonal closure of block 0 and per block 3 launches (panels, packing, phase 3 -- on 16-bit
-    pairs or its 32-bit alternative -- which also closes the next diagonal tile) or, from
-    n = 16384, 12 per 256-vertex block (the block's own closure as two 3-phase sub-steps, two
-    panel copies, two panel products, packing, phase 3); the certificate (2); then the exact
-    int32 loop as above (1 + 2 per 128-vertex block), whose launches return at once on the
-    device when the certificate holds;
+  * blocked FW, plain (fp32, or int32 below n = 4096): a1, phases 1 and 2 of block 0 (the
+    diagonal closure, the panels), then one launch per 128-vertex block: its phase 3 (Sec. 3.2's
+    three phases), which also closes the diagonal tile of block kb + 1 and computes its panels;
+    only the first closure when the whole matrix is one block;
+  * blocked FW, int32 from n = 4096: a1, the decision, then the pass: with 128-vertex blocks
+    phases 1 and 2 of block 0 and one launch per block as above (phase 3 on 16-bit pairs or its
+    32-bit alternative; the panel tiles also leave the packed operands) or, from n = 16384, 12
+    per 256-vertex block (the block's own closure as two 3-phase sub-steps, two panel copies,
+    two panel products, packing, phase 3); the certificate (2); then the exact int32 loop as
+    above (2 + 1 per 128-vertex block), whose launches return at once on the device when the
+    certificate holds;
   * an int32 tropical product with workspace room: two bound scans, two packings, the 16-bit
     launch and the plain launch that returns at once;
   * launches captured into a CUDA graph count once, at capture.
@@ -54,15 +54,15 @@ def _fw_count(apsp, n, dtype):
 @pytest.mark.parametrize("n,dtype", [(100, "float32"), (1000, "float32"), (3000, "int32")])
 def test_fw_plain_launches(apsp, n, dtype):
     nb = -(-n // 128)
-    want = 2 if nb == 1 else 2 + 2 * nb
+    want = 2 if nb == 1 else 3 + nb
     assert _fw_count(apsp, n, dtype) == want
 
 
 @pytest.mark.parametrize("n", [4096, 16384])
 def test_fw16_launches(apsp, n):
     nb = -(-n // 128)
-    wide_pass = 12 * -(-n // 256) if n >= 16384 else 1 + 3 * nb
-    assert _fw_count(apsp, n, "int32") == 4 + wide_pass + 1 + 2 * nb
+    wide_pass = 12 * -(-n // 256) if n >= 16384 else 2 + nb
+    assert _fw_count(apsp, n, "int32") == 4 + wide_pass + 2 + nb
 
 
 def test_tropical_gemm_int32_launches(apsp):
@@ -93,8 +93,14 @@ def test_rkleene_counts_are_repeatable_and_graph_capture_counts_once(apsp):
     with torch.cuda.graph(g, stream=s):
         apsp.apsp_fw(d, ws=ws)
     captured = apsp.apsp_launch_count()
-    assert captured == 1 + 3 * 3
-    for _ in range(3):
-        g.replay()
+    assert captured == 3 + 3
+    want = torch.from_numpy(small).cuda()
+    apsp.apsp_fw(want)
     torch.cuda.synchronize()
-    assert apsp.apsp_launch_count() == captured
+    apsp.apsp_launch_count(reset=True)
+    for _ in range(3):  # each replay closes the matrix again (the tile counters restart at zero)
+        d.copy_(torch.from_numpy(small).cuda())
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(d, want)
+    assert apsp.apsp_launch_count() == 0  # replays enqueue nothing through the library

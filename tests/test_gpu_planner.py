@@ -105,20 +105,29 @@ def test_planner_regret_and_gain_on_this_gpu(apsp, tmp_path):
         tuner.measure(workloads.er_graph(n, 0.6, "int32", lo=1, hi=100, seed=n + 1), tag="train")
     rows = planner.load_rows(log)
     assert len(rows) == len(tuner.rows) > 0
+    dense_train = sorted({(r["n"], round(r["density"], 2)): 0 for r in rows if r["density"] > 0.2 and r["dtype"] == "int32"})
+    dense_train = [[n, d] + [round(next(r["ms"] for r in rows if r["n"] == n and round(r["density"], 2) == d
+                                        and r["dtype"] == "int32" and (r["algo"], r["param"]) == c), 3)
+                             for c in (("fw", 0), ("squaring", 0))] for n, d in dense_train]
     model = planner.CostModel(seed=0)
-    model.fit(rows + planner.load_rows(planner.DEFAULT_LOG), epochs=4000)
+    hist = model.fit(rows + planner.load_rows(planner.DEFAULT_LOG), epochs=4000)
     # Held-out graphs: a spread of sizes at p = 0.1, and dense int32 graphs of 1000..1600
-    # vertices (diameter 2), where a few full-size products of repeated squaring beat Floyd-
-    # Warshall's many small block steps -- graphs on which "always FW" is not the best plan.
+    # vertices (shortest paths of 4 to 6 edges), where a few full-size products of repeated
+    # squaring beat Floyd-Warshall's many small block steps -- graphs on which "always FW" is
+    # not the best plan.
     spread = [(n, 0.1) for n in (64, 128, 256, 400, 900, 1800, 2600, 3500)]
-    dense = [(n, 0.5) for n in (1050, 1250, 1450, 1600)]
-    tot = {}
+    dense = [(n, 0.5) for n in range(1000, 1601, 100)]
+    tot, picks = {}, []
     for name, graphs in (("spread", spread), ("dense", dense)):
         t = dict(model=0.0, best=0.0, fw=0.0, paper=0.0)
         for n, p in graphs:
             h = workloads.er_graph(n, p, "int32", lo=1, hi=100, seed=7 * n)
             meas = {(r["algo"], r["param"]): r["ms"] for r in tuner.measure(h, tag="held_out")}
             choice = model.choose(n, planner.density_of(h), "int32")
+            pred = model.predict_ms(n, planner.density_of(h), "int32")
+            best = min(meas, key=meas.get)
+            picks.append([n, p, "%s%d" % choice, round(meas[choice], 3), "%s%d" % best, round(meas[best], 3),
+                          round(meas[("fw", 0)], 3), round(pred[choice], 3), round(pred[best], 3)])
             t["model"] += meas[choice]
             t["best"] += min(meas.values())
             t["fw"] += meas[("fw", 0)]
@@ -130,7 +139,10 @@ def test_planner_regret_and_gain_on_this_gpu(apsp, tmp_path):
                       "gain_vs_always_fw": round(both["fw"] / both["model"] - 1.0, 4),
                       "gain_vs_always_fw_dense": round(tot["dense"]["fw"] / tot["dense"]["model"] - 1.0, 4),
                       "gain_vs_paper_rule": round(both["paper"] / both["model"] - 1.0, 4),
-                      **{f"{g}_{k}_ms": round(v, 3) for g in tot for k, v in tot[g].items()}}))
+                      **{f"{g}_{k}_ms": round(v, 3) for g in tot for k, v in tot[g].items()},
+                      "fit_loss": [round(hist[0], 4), round(hist[-1], 5)],
+                      "dense_train [n, p, fw ms, squaring ms]": dense_train,
+                      "picks [n, p, choice, ms, best, ms, fw ms, predicted choice, predicted best]": picks}))
     assert regret <= 0.25
     # where FW is not the best plan, the network must find the better one
     assert tot["dense"]["best"] < 0.95 * tot["dense"]["fw"]

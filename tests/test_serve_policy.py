@@ -160,3 +160,24 @@ def test_request_matrix_is_an_er_graph_of_its_own_parameters():
     workloads.request_matrix(pool, 8, 50, 0.3, "int32", out=big[:, :50])
     assert np.array_equal(big[:, :50], workloads.request_matrix(pool, 8, 50, 0.3, "int32"))
     assert np.all(big[:, 50:] == 0)
+
+
+def test_recorded_cost_model_matches_the_feature_vector():
+    """The trained network shipped with the package takes the planner's current feature vector,
+    and the derived features behave as documented."""
+    import json
+
+    from paper_2310_03983_gb300 import planner
+    with open(planner.DEFAULT_MODEL) as f:
+        d = json.load(f)
+    assert d["in_dim"] == planner.IN_DIM and d["hidden"] == planner.HIDDEN
+    assert len(d["params"]) == planner.IN_DIM * 64 + 64 + 64 * 64 + 64 + 64 + 1
+    for n in (32, 1000, 4096, 32768):
+        for algo, param in planner.applicable(n):
+            assert len(planner.features(n, 0.1, "int32", algo, param)) == planner.IN_DIM
+    # 12 x 12 output tiles fill one wave of 152 SMs, 13 x 13 need two
+    assert planner.full_product_waves(1536) == 1 and planner.full_product_waves(1537) == 2
+    # denser graphs settle in no more squarings than sparser ones of the same size
+    for dt in ("int32", "float32"):
+        ks = [planner.squaring_products(2048, p, dt) for p in (0.01, 0.05, 0.2, 0.8)]
+        assert ks == sorted(ks, reverse=True) and 2 <= ks[-1] <= ks[0] <= 6
