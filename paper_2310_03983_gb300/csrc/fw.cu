@@ -89,6 +89,13 @@ constexpr int kFw16Tiles = 2;
 constexpr int64_t kFw16Block = kFw16Tiles * kBM;
 constexpr int kFw16Words = (int)(kFw16Block / 2);
 constexpr int64_t kFw16WideN = 16384;
+// The plain loop (fp32, and int32 without the 16-bit pass) hands out phase-3 tiles dynamically
+// and fuses phases 1 and 2 of the next block into each phase-3 launch up to this many blocks.
+// Beyond it the static order with separate launches is faster: the fp32 instruction sequence is
+// issue-bound, and the dynamic order's consumer loop costs it about 8% per launch (measured at
+// n = 4096 .. 16384), which outweighs the saved launches once a launch has ~80 x 80 tiles
+// (fp32: n = 8192 29.9 ms fused against 31.3 static; n = 12288 99.2 against 96.9).
+constexpr int64_t kFusedMaxBlocks = 80;
 
 // w = words[0]: the largest weight of the whole graph (the exact bound); c = *cert: the largest
 // finite entry of the block being closed (the certificates' step bound).
@@ -236,14 +243,15 @@ int fw_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bound b, cu
   p.wmax = b.w;
   p.wmult = b.mult;
   if (!(panels16 && dtype == APSP_I32 && b.w && nb > 1 && inf_i > kCap16))
-    return fw_loop(d, n, ld, dtype, mA, mB, mC, p, nullptr, s, 0, b.counters);
+    return fw_loop(d, n, ld, dtype, mA, mB, mC, p, nullptr, s, 0, nb <= kFusedMaxBlocks ? b.counters : nullptr);
   int *words = const_cast<int *>(b.w);
   const int *cert = b.cert ? b.cert : b.w;
   fw_decide_kernel<<<1, 1, 0, s>>>(words, cert, inf_i > kCap24, b.mult);
   APSP_LAUNCH_CHECK();
   if ((r = fw_wide_pass(d, n, ld, dtype, inf_i, b, s, panels16, p, mA, mB, mC))) return r;
   if ((r = certify(d, ld, n, inf_i, words, cert, s))) return r;
-  return fw_loop(d, n, ld, dtype, mA, mB, mC, p, words + 6, s, kTraceSide, b.counters);
+  return fw_loop(d, n, ld, dtype, mA, mB, mC, p, words + 6, s, kTraceSide,
+                 nb <= kFusedMaxBlocks ? b.counters : nullptr);
 }
 
 // The pass over diagonal blocks of bt = 1 or 2 tiles: phases 1 and 2 exact, the block's panels

@@ -49,12 +49,21 @@ struct ArithF32 {
   // straight from a 128-bit load, the duplicated A value is built once per row and k), the
   // four adds of one duplicated A value issued back to back so it stays in the operand reuse
   // cache, then one 3-input min folds k and k+1 into each accumulator.
+  // HALF (bit 0: rows, bit 1: columns): only rows 0..63 and / or columns 0..63 of the tile are
+  // computed -- register rows i < 4 and column quads h = 0; the others keep their initial
+  // value.  Used for the last block of a padded graph, whose other half is padding.
+  template <int HALF = 0>
   static __device__ __forceinline__ void slab_full(const int *As, const int *Bs, int tm, int tn, T (&acc)[8][8]) {
+    constexpr bool MASKED = HALF != 0, fr = !(HALF & 1), fc = !(HALF & 2);
 #pragma unroll kQUnroll
     for (int q = 0; q < kSlabK / 4; ++q) {
       float4 a[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
+        if (MASKED && i >= 4 && !fr) {
+          a[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+          continue;
+        }
         const int4 v = lds128(As + a_off(tm + 16 * i, q));
         a[i] = make_float4(__int_as_float(v.x), __int_as_float(v.y), __int_as_float(v.z), __int_as_float(v.w));
       }
@@ -63,20 +72,32 @@ struct ArithF32 {
         const int *r0 = Bs + (4 * q + 2 * kp) * kSlabN + 4 * tn;
         uint64_t b0[4], b1[4];
         lds128_2x64(r0, b0[0], b0[1]);
-        lds128_2x64(r0 + 64, b0[2], b0[3]);
         lds128_2x64(r0 + kSlabN, b1[0], b1[1]);
-        lds128_2x64(r0 + kSlabN + 64, b1[2], b1[3]);
+        if (!MASKED || fc) {
+          lds128_2x64(r0 + 64, b0[2], b0[3]);
+          lds128_2x64(r0 + kSlabN + 64, b1[2], b1[3]);
+        } else {
+          b0[2] = b0[3] = b1[2] = b1[3] = 0;
+        }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
+          if (MASKED && i >= 4 && !fr) continue;
           const float a0 = kp ? a[i].z : a[i].x, a1 = kp ? a[i].w : a[i].y;
           const uint64_t aa0 = pack2(a0, a0), aa1 = pack2(a1, a1);
           uint64_t t0[4], t1[4];
 #pragma unroll
-          for (int jp = 0; jp < 4; ++jp) t0[jp] = fadd2_64(aa0, b0[jp]);
-#pragma unroll
-          for (int jp = 0; jp < 4; ++jp) t1[jp] = fadd2_64(aa1, b1[jp]);
+          for (int jp = 0; jp < 4; ++jp) {
+            if (MASKED && jp >= 2 && !fc) continue;
+            t0[jp] = fadd2_64(aa0, b0[jp]);
+          }
 #pragma unroll
           for (int jp = 0; jp < 4; ++jp) {
+            if (MASKED && jp >= 2 && !fc) continue;
+            t1[jp] = fadd2_64(aa1, b1[jp]);
+          }
+#pragma unroll
+          for (int jp = 0; jp < 4; ++jp) {
+            if (MASKED && jp >= 2 && !fc) continue;
             acc[i][2 * jp] = Ops<float>::min3(acc[i][2 * jp], lo_of(t0[jp]), lo_of(t1[jp]));
             acc[i][2 * jp + 1] = Ops<float>::min3(acc[i][2 * jp + 1], hi_of(t0[jp]), hi_of(t1[jp]));
           }
@@ -84,8 +105,10 @@ struct ArithF32 {
       }
     }
   }
+  template <int HALF = 0>
   static __device__ __forceinline__ void slab_part(const int *As, const int *Bs, int tm, int tn, int kc,
                                                    T (&acc)[8][8]) {
+    constexpr bool MASKED = HALF != 0, fr = !(HALF & 1), fc = !(HALF & 2);
     for (int k = 0; k < kc; ++k) {
       T a[8], b[8];
 #pragma unroll
@@ -95,9 +118,14 @@ struct ArithF32 {
       b[0] = from(u0.x); b[1] = from(u0.y); b[2] = from(u0.z); b[3] = from(u0.w);
       b[4] = from(u1.x); b[5] = from(u1.y); b[6] = from(u1.z); b[7] = from(u1.w);
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+      for (int i = 0; i < 8; ++i) {
+        if (MASKED && i >= 4 && !fr) continue;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = fminf(acc[i][j], __fadd_rn(a[i], b[j]));
+        for (int j = 0; j < 8; ++j) {
+          if (MASKED && j >= 4 && !fc) continue;
+          acc[i][j] = fminf(acc[i][j], __fadd_rn(a[i], b[j]));
+        }
+      }
     }
   }
 };
@@ -139,31 +167,49 @@ struct ArithInt {
     if (!P16) return v;
     return min(v & 0xFFFF, (int)((unsigned)v >> 16));
   }
-  template <typename A>
+  // HALF: as ArithF32's -- rows (bit 0) and / or columns (bit 1) 64..127 skipped.
+  template <int HALF = 0, typename A>
   static __device__ __forceinline__ void slab_full(const int *As, const int *Bs, int tm, int tn, A (&acc)[8][8]) {
+    constexpr bool MASKED = HALF != 0, fr = !(HALF & 1), fc = !(HALF & 2);
 #pragma unroll 1
     for (int q = 0; q < kSlabK / 4; ++q) {
       int4 a[8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) a[i] = lds128(As + a_off(tm + 16 * i, q));
+      for (int i = 0; i < 8; ++i) {
+        if (MASKED && i >= 4 && !fr) {
+          a[i] = make_int4(0, 0, 0, 0);
+          continue;
+        }
+        a[i] = lds128(As + a_off(tm + 16 * i, q));
+      }
 #pragma unroll
       for (int kp = 0; kp < 2; ++kp) {
         const int *r0 = Bs + (4 * q + 2 * kp) * kSlabN + 4 * tn;
-        const int4 u0 = lds128(r0), u1 = lds128(r0 + 64), w0 = lds128(r0 + kSlabN), w1 = lds128(r0 + kSlabN + 64);
+        const int4 u0 = lds128(r0), w0 = lds128(r0 + kSlabN);
+        int4 u1 = make_int4(0, 0, 0, 0), w1 = make_int4(0, 0, 0, 0);
+        if (!MASKED || fc) {
+          u1 = lds128(r0 + 64);
+          w1 = lds128(r0 + kSlabN + 64);
+        }
         const int b0[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
         const int b1[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
+          if (MASKED && i >= 4 && !fr) continue;
           const int a0 = kp ? a[i].z : a[i].x, a1 = kp ? a[i].w : a[i].y;
 #pragma unroll
-          for (int j = 0; j < 8; ++j) set_acc(acc[i][j], addmin(a1, b1[j], addmin(a0, b0[j], acc_bits(acc[i][j]))));
+          for (int j = 0; j < 8; ++j) {
+            if (MASKED && j >= 4 && !fc) continue;
+            set_acc(acc[i][j], addmin(a1, b1[j], addmin(a0, b0[j], acc_bits(acc[i][j]))));
+          }
         }
       }
     }
   }
-  template <typename A>
+  template <int HALF = 0, typename A>
   static __device__ __forceinline__ void slab_part(const int *As, const int *Bs, int tm, int tn, int kc,
                                                    A (&acc)[8][8]) {
+    constexpr bool MASKED = HALF != 0, fr = !(HALF & 1), fc = !(HALF & 2);
     for (int k = 0; k < kc; ++k) {
       int a[8];
 #pragma unroll
@@ -172,9 +218,14 @@ struct ArithInt {
       const int4 u0 = lds128(r), u1 = lds128(r + 64);
       const int b[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+      for (int i = 0; i < 8; ++i) {
+        if (MASKED && i >= 4 && !fr) continue;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) set_acc(acc[i][j], addmin(a[i], b[j], acc_bits(acc[i][j])));
+        for (int j = 0; j < 8; ++j) {
+          if (MASKED && j >= 4 && !fc) continue;
+          set_acc(acc[i][j], addmin(a[i], b[j], acc_bits(acc[i][j])));
+        }
+      }
     }
   }
 };

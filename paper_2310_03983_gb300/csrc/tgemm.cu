@@ -43,6 +43,10 @@ struct TileCoords {
   // tile, so it is counted once stored; wait -- a panel tile, whose operands must be counted
   // complete before they are loaded.
   bool dep, wait;
+  // Grouped launches: the tile's rows (half_r) / columns (half_c) 64..127 are padding of the
+  // graph's last block, so only the first half is computed (the rest keeps its initial value,
+  // which is what the padding's isolated vertices hold anyway).
+  bool half_r, half_c;
 };
 
 // Tile t of a grouped FW launch: find its group and graph (all tiles of one graph are
@@ -53,6 +57,7 @@ template <int MODE>
 __device__ __forceinline__ TileCoords grouped_tile_coords(const TileProblem &p, int64_t t) {
   TileCoords tc;
   tc.dep = tc.wait = false;
+  tc.half_r = tc.half_c = false;
   unsigned rem = (unsigned)t, per = 1, row0 = 0, gnb = 1, first = 0;
   const unsigned kb = (unsigned)p.kb;
   bool found = false;
@@ -130,8 +135,10 @@ __device__ __forceinline__ TileCoords grouped_tile_coords(const TileProblem &p, 
   tc.skip = !found || (p.gflags[q] & p.gmask) != p.gwant;
   int bk = kBM;
   if (p.gsize && !tc.skip) {
-    const int left = p.gsize[q] - kb0;
+    const int gs = p.gsize[q], left = gs - kb0;
     bk = left < kBM ? (left > 0 ? left : 1) : kBM;
+    tc.half_r = gs - (tc.c_row - base) <= kBM / 2;
+    tc.half_c = gs - tc.c_col <= kBN / 2;
   }
   tc.k_len = (MODE == kModeFwRest16 || p.arith16) ? (bk + 1) >> 1 : bk;
   return tc;
@@ -148,6 +155,7 @@ __device__ __forceinline__ TileCoords tile_coords(const TileProblem &p, int64_t 
   tc.pa_set = tc.pb_set = -1;
   tc.pb_row = 0;
   tc.dep = tc.wait = false;
+  tc.half_r = tc.half_c = false;
   if (MODE == kModeGemm) {
     // Grouped rasterisation: 8 tile-rows advance together so A slabs are reused from L2.
     const int64_t G = 8;
@@ -328,8 +336,22 @@ __device__ __forceinline__ void consume(const TileProblem &p, const Smem &sm, in
       const int *As = sm.sA + stage * (kBM * kBK);
       const int *Bs = sm.sB + stage * (kBK * kBN);
       const int kc = tc.k_len - kt * kBK;
-      if (kc >= kBK) AR::slab_full(As, Bs, tm, tn, acc);
-      else AR::slab_part(As, Bs, tm, tn, kc, acc);
+      const int half = G ? (tc.half_r ? 1 : 0) | (tc.half_c ? 2 : 0) : 0;  // uniform per tile
+      if (kc >= kBK) {
+        switch (half) {
+          case 0: AR::slab_full(As, Bs, tm, tn, acc); break;
+          case 1: AR::template slab_full<1>(As, Bs, tm, tn, acc); break;
+          case 2: AR::template slab_full<2>(As, Bs, tm, tn, acc); break;
+          default: AR::template slab_full<3>(As, Bs, tm, tn, acc); break;
+        }
+      } else {
+        switch (half) {
+          case 0: AR::slab_part(As, Bs, tm, tn, kc, acc); break;
+          case 1: AR::template slab_part<1>(As, Bs, tm, tn, kc, acc); break;
+          case 2: AR::template slab_part<2>(As, Bs, tm, tn, kc, acc); break;
+          default: AR::template slab_part<3>(As, Bs, tm, tn, kc, acc); break;
+        }
+      }
       __syncwarp();
       if (lane == 0) mbar_arrive(&sm.empty[stage]);
       if (++stage == kStages) { stage = 0; phase ^= 1; }

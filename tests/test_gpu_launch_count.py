@@ -5,13 +5,15 @@ entry point documents, so the figure the bench prints is tied to the code that l
   * blocked FW, plain (fp32, or int32 below n = 4096): a1, phases 1 and 2 of block 0 (the
     diagonal closure, the panels), then one launch per 128-vertex block: its phase 3 (Sec. 3.2's
     three phases), which also closes the diagonal tile of block kb + 1 and computes its panels;
-    only the first closure when the whole matrix is one block;
+    only the first closure when the whole matrix is one block (beyond 80 blocks: three launches
+    per block);
   * blocked FW, int32 from n = 4096: a1, the decision, then the pass: with 128-vertex blocks
     phases 1 and 2 of block 0 and one launch per block as above (phase 3 on 16-bit pairs or its
     32-bit alternative; the panel tiles also leave the packed operands) or, from n = 16384, 12
     per 256-vertex block (the block's own closure as two 3-phase sub-steps, two panel copies,
     two panel products, packing, phase 3); the certificate (2); then the exact int32 loop as
-    above (2 + 1 per 128-vertex block), whose launches return at once on the device when the
+    above (2 + 1 per 128-vertex block; beyond 80 blocks 3 per block -- diagonal, panels, phase 3
+    in launches of their own), whose launches return at once on the device when the
     certificate holds;
   * an int32 tropical product with workspace room: two bound scans, two packings, the 16-bit
     launch and the plain launch that returns at once;
@@ -51,10 +53,10 @@ def _fw_count(apsp, n, dtype):
     return _count(apsp, lambda: apsp.apsp_fw(d))
 
 
-@pytest.mark.parametrize("n,dtype", [(100, "float32"), (1000, "float32"), (3000, "int32")])
+@pytest.mark.parametrize("n,dtype", [(100, "float32"), (1000, "float32"), (3000, "int32"), (12288, "float32")])
 def test_fw_plain_launches(apsp, n, dtype):
     nb = -(-n // 128)
-    want = 2 if nb == 1 else 3 + nb
+    want = 2 if nb == 1 else (3 + nb if nb <= 80 else 1 + 3 * nb)
     assert _fw_count(apsp, n, dtype) == want
 
 
@@ -62,7 +64,8 @@ def test_fw_plain_launches(apsp, n, dtype):
 def test_fw16_launches(apsp, n):
     nb = -(-n // 128)
     wide_pass = 12 * -(-n // 256) if n >= 16384 else 2 + nb
-    assert _fw_count(apsp, n, "int32") == 4 + wide_pass + 2 + nb
+    int32_pass = 2 + nb if nb <= 80 else 3 * nb
+    assert _fw_count(apsp, n, "int32") == 4 + wide_pass + int32_pass
 
 
 def test_tropical_gemm_int32_launches(apsp):
