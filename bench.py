@@ -322,6 +322,29 @@ def copy_parts(host_in, host_out, dev, reps: int = 3):
     return {"h2d": round(statistics.median(h2d), 2), "d2h": round(statistics.median(d2h), 2)}
 
 
+def huge_page_share(t) -> float | None:
+    """Fraction of a host tensor's bytes that the kernel backs with transparent huge pages
+    (AnonHugePages of its mapping in /proc/self/smaps), or None where that is not readable.
+    The GPU reaches pinned host memory through its own translations of the host pages; with
+    base pages a copy after a closure pays tens of thousands of translation misses."""
+    addr = t.data_ptr()
+    try:
+        with open("/proc/self/smaps") as f:
+            inside = False
+            for line in f:
+                head = line.split()
+                if head and "-" in head[0] and len(head) >= 5 and ":" not in head[0]:
+                    lo, hi = (int(x, 16) for x in head[0].split("-"))
+                    inside = lo <= addr < hi
+                elif inside and line.startswith("Rss:"):
+                    rss = int(line.split()[1])
+                elif inside and line.startswith("AnonHugePages:"):
+                    return round(int(line.split()[1]) / max(rss, 1), 3)
+    except (OSError, ValueError, UnboundLocalError):
+        return None
+    return None
+
+
 def spin_up(fn, seconds: float = 1.0):
     """Run fn (untimed) until `seconds` of wall time have passed: an idle GPU takes a while to
     reach its full clocks, and a short warm-up would leave the start of the timed region slow."""
@@ -539,6 +562,7 @@ def run_ours(args, w, rank, world, local_rank):
         e2e_parts = copy_parts(host, out_host, dev)
         e2e_parts["e2e_median"] = round(statistics.median(e2e_ms), 2)
         e2e_parts["e2e_samples"] = [round(x, 2) for x in e2e_ms]
+        e2e_parts["host_huge_page_share"] = {"in": huge_page_share(host), "out": huge_page_share(out_host)}
         if w["algo"] != "gemm":
             e2e_parts["inside_e2e"] = e2e_inside
             e2e_parts["dominant_kernel_ms_per_timed_step"] = round(k_ms / max(1, args.steps), 2)

@@ -125,13 +125,13 @@ int tropical_gemm(void *C, const void *A, const void *B, int64_t M, int64_t N, i
  * whose (n - 1) * largest finite weight < 2^24 run in exact fp32 arithmetic on their bit
  * patterns; others in int32), when ld is not a multiple of 4 an aligned copy of the matrix
  * (n x round_up(n, 4) elements), and last, for int32 with n >= 4096, room for a 16-bit pass
- * over 256-vertex diagonal blocks (the two panels packed into 16-bit pairs, 2 x 128 x
- * round_up(n, 4) words, and copies of the two 256-wide panels, 2 x 256 x round_up(n, 4)
- * elements).  With that room, and a largest weight of at most 0x0FFF, phase 3 runs on the
- * packed pairs (two (min,+) pairs per DPX operation) in the (min,+) semiring truncated at
- * 0x3FFF; a device-side certificate (largest stored value below 0x3FFF plus the largest weight
- * stays below 0x3FFF) proves the result exact, and otherwise the int32 Floyd-Warshall runs
- * again over it.  With the same room, an int32 matrix whose largest weight is above 0x0FFF and
+ * (the two panels packed into 16-bit pairs, 2 x 128 x round_up(n, 128) words, and copies of
+ * the two 256-wide panels, 256 x round_up(n, 4) + n x 256 elements; apsp_fw_workspace_bytes
+ * gives the total).  With that room, and a largest weight of at most 0x0FFF, phases 2 and 3
+ * run on the packed pairs (two (min,+) pairs per DPX operation) in the (min,+) semiring
+ * truncated at 0x3FFF; a device-side certificate (largest stored value below 0x3FFF plus the
+ * largest weight stays below 0x3FFF) proves the result exact, and otherwise the int32
+ * Floyd-Warshall runs again over it.  With the same room, an int32 matrix whose largest weight is above 0x0FFF and
  * at most 2^22, and too large for the exact fp32 bound, runs phase 3 in fp32 on its bit patterns
  * truncated at 2^24, certified the same way (largest stored value below 2^24 plus the largest
  * weight stays below 2^24), else followed by the exact int32 loop.  Results are bit-exact either

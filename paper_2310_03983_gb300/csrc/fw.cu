@@ -222,6 +222,44 @@ static int fw_wide_pass(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bo
                         void *panels16, const TileProblem &p, const CUtensorMap &mA, const CUtensorMap &mB,
                         const CUtensorMap &mC);
 
+// Phase 2 of a bw-vertex block at kb0 on packed 16-bit pairs (A16: the packed column panel, n
+// rows x lda16 words; B16: the packed row panel, leading dimension ldb16; both written by
+// fw_pack16_kernel from the panels before this phase, so each holds D* as well): the row panel
+// D[kb0.., :] = min(itself, D* (x) row panel) and the column panel D[:, kb0..] = min(itself,
+// column panel (x) D*), in the semiring truncated at kCap16 (a capped result means "at least
+// the cap" and leaves the old entry).  Both launches return at once unless words[4] is set.
+static int panels16_truncated(int *D, int64_t ld, int64_t n, int64_t kb0, int64_t bw, int *A16, int64_t lda16,
+                              int *B16, int64_t ldb16, const TileProblem &base, int *words, cudaStream_t s) {
+  int r;
+  const int64_t kw = (bw + 1) >> 1;
+  for (int side = 0; side < 2; ++side) {
+    // side 0: the row panel (bw x n) = D* rows of A16 (x) B16; side 1: the column panel (n x bw)
+    // = A16 (x) the D* columns of B16.
+    const int64_t M = side ? n : bw, N = side ? bw : n;
+    int *A = side ? A16 : A16 + kb0 * lda16;
+    int *B = side ? B16 + kb0 : B16;
+    int *C = side ? D + kb0 : D + kb0 * ld;
+    CUtensorMap mA, mB, mC;
+    if ((r = make_operand_maps(A, M, kw, lda16, APSP_I32, &mA, nullptr, nullptr))) return r;
+    if ((r = make_operand_maps(B, kw, N, ldb16, APSP_I32, nullptr, &mB, nullptr))) return r;
+    if ((r = make_operand_maps(C, M, N, ld, APSP_I32, nullptr, nullptr, &mC))) return r;
+    TileProblem q = {};
+    q.M = M; q.N = N; q.K = kw;
+    q.tiles_m = cdiv(M, kBM);
+    q.tiles_n = cdiv(N, kBN);
+    q.ntiles = q.tiles_m * q.tiles_n;
+    q.C = C;
+    q.ldc = ld;
+    q.inf_i = base.inf_i;
+    q.status = base.status;
+    q.arith16 = 1;
+    q.run_if = words + 4;
+    q.trace_class = kTraceSide;
+    if ((r = launch_tgemm(kModeGemm, true, APSP_I32, mA, mB, mC, q, s))) return r;
+  }
+  return APSP_OK;
+}
+
 // Closes the n x n block at d (16-byte aligned, ld % 4 == 0, already normalised) in place.
 // panels16 (may be null): fw16_panel_bytes(n) of device scratch; with it an int32 closure runs
 // the pass above: phase 3 on packed 16-bit pairs when its largest weight (step) is at most
@@ -314,12 +352,22 @@ static int fw_wide_pass(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bo
       ps.C = sub;
       if ((r = fw_loop(sub, bw, ld, dtype, dA, dB, dC, ps, nullptr, s, kTraceSide))) return r;
       // Phase 2: the row panel becomes D* (x) (row panel) and the column panel (column panel) (x)
-      // D*, each one exact product (D* is closed, so its zero diagonal keeps the old entry) read
-      // from a copy of the panel; the block's own entries are reproduced (D* (x) D* = D*).
-      if ((r = launch_copy2d(Rc, ldp, rowp, ld, bw, n, s))) return r;
-      if ((r = gemm_aligned(rowp, ld, sub, ld, Rc, ldp, bw, n, bw, dtype, false, inf_i, b, s))) return r;
-      if ((r = launch_copy2d(Cc, kFw16Block, colp, ld, n, bw, s))) return r;
-      if ((r = gemm_aligned(colp, ld, Cc, kFw16Block, sub, ld, n, bw, bw, dtype, false, inf_i, b, s))) return r;
+      // D*; D* is closed, so its zero diagonal keeps the old entry and the block's own entries
+      // are reproduced (D* (x) D* = D*).  With the 16-bit pass in use (words[4]) both products
+      // run truncated on packed copies of the panels -- which hold D* in both forms -- in place,
+      // folded as min(old entry, capped product) like phase 3.  In the 32-bit alternative
+      // (words[7]) each is one exact product read from an int32 copy of its panel.
+      const int64_t work = 2 * n * ((bw + 1) >> 1);
+      fw_pack16_kernel<<<(int)std::min<int64_t>(cap, cdiv(work, 256)), 256, 0, s>>>(D, ld, n, kb0, (int)bw, A16,
+                                                                                    lda16, B16, ldb16, words);
+      APSP_LAUNCH_CHECK();
+      if ((r = panels16_truncated(D, ld, n, kb0, bw, A16, lda16, B16, ldb16, p, words, s))) return r;
+      const int *alt = words + 7;
+      if ((r = launch_copy2d(Rc, ldp, rowp, ld, bw, n, s, alt))) return r;
+      if ((r = gemm_aligned(rowp, ld, sub, ld, Rc, ldp, bw, n, bw, dtype, false, inf_i, b, s, {}, alt))) return r;
+      if ((r = launch_copy2d(Cc, kFw16Block, colp, ld, n, bw, s, alt))) return r;
+      if ((r = gemm_aligned(colp, ld, Cc, kFw16Block, sub, ld, n, bw, bw, dtype, false, inf_i, b, s, {}, alt)))
+        return r;
     }
     // Phase 3, K = bw: on the packed panels, or the 32-bit alternative.
     if (bt > 1) {
