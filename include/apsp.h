@@ -374,8 +374,20 @@ int64_t apsp_launch_count(int reset);
  *   2: int32 two adds then 3-input min            3: fp32 add then 2-input min
  *   4: fp32 two adds then 3-input min             5: fp32 packed pair add then 3-input min
  *   6: as 5 on subnormal operands (int32 bit patterns below 2^24 read as fp32)
+ *   7: packed 16-bit pairs, one DPX add-min (__viaddmin_s16x2) for two pairs
+ *   8: packed 16-bit pairs, SIMD add then SIMD min
+ * Variants 0-6 perform blocks*threads*iters*64 pairs, 7-8 blocks*threads*iters*128.
+ * Variants 9-11 time the fp32 slab arithmetic of the tropical-GEMM engine in isolation, on
+ * one CTA of threads = 256 per block (anything else: APSP_ERR_ARG) with four 128 x 32 and
+ * 32 x 128 operand slabs resident in shared memory (128 KiB of dynamic shared memory); each
+ * iteration is one 128 x 128 x 32 slab, so blocks*iters*524288 pairs:
+ *   9:  the engine's instruction sequence reading its operands from shared memory;
+ *   10: the same packed adds and 3-input mins on operands held in registers;
+ *   11: as 10 plus one integer XOR per 16 pairs (other work on the ALU pipe, which also
+ *       executes the 3-input min).
  * Writes a checksum per thread to sink (device, blocks*threads int32) so nothing is dead
- * code.  Time it with events on `stream`; pairs performed = blocks*threads*iters*64. */
+ * code; for variants 9-11, thread 0 of each block writes instead the SM clocks its block
+ * spent in the loop, divided by 1024.  Time it with events on `stream`. */
 int apsp_probe_minplus(int variant, int blocks, int threads, int iters, void *sink,
                        void *stream);
 

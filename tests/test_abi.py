@@ -63,6 +63,13 @@ def test_host_side_calls_without_gpu():
     assert h(None, -1, 0, 0, None, 0, None, 0, None) == 1
     assert h(None, 4, 4, 7, None, 0, None, 0, None) == 1
     assert h(None, 0, 0, 0, None, 0, None, 0, None) == 0
+    # the slab probes run 256 threads per block (the engine's consumer layout) and nothing else
+    pr = lib.apsp_probe_minplus
+    pr.restype = ctypes.c_int
+    pr.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    for v in (9, 10, 11):
+        assert pr(v, 1, 128, 1, ctypes.c_void_p(16), None) == 1
+    assert pr(12, 1, 256, 1, ctypes.c_void_p(16), None) == 1
 
 
 def _staged_model(ns, count, packed=True):
