@@ -185,6 +185,15 @@ __device__ __forceinline__ void tma_load_2d(void *smem_dst, const CUtensorMap *m
       : "memory");
 }
 
+// Programmatic dependent launch (PTX griddepcontrol).  A kernel launched with
+// launch_pdl() may be scheduled while the kernel before it on the stream is still running, so
+// that its CTAs are resident and set up when that kernel ends.  pdl_wait() returns once every
+// prerequisite grid has completed and its memory operations are visible; kernels launched that
+// way call it before touching global memory.  pdl_trigger() allows the next kernel on the
+// stream to be scheduled.  Both are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ int4 lds128(const void *p) {
   int4 v;
   asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
@@ -225,6 +234,28 @@ inline int64_t round_up(int64_t a, int64_t b) { return cdiv(a, b) * b; }
 
 // Number of SMs of the current device (cached per device).
 int sm_count();
+
+// Whether launch_pdl() sets the programmatic-serialization attribute: on unless the
+// environment variable APSP_PDL is "0" when the library first launches.
+bool pdl_enabled();
+
+// Launches kernel k with the programmatic-serialization attribute (see pdl_wait()); k must
+// call pdl_wait() before any global memory access.  Without the attribute (APSP_PDL=0) it is
+// an ordinary launch.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
 
 // Workspace the library allocates for a call made without one: stream-ordered, from a
 // per-device pool that keeps freed memory for the next call (runtime.cu).

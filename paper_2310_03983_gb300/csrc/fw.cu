@@ -21,6 +21,8 @@ namespace apsp {
 // (diag.cuh).  int32 tiles are relaxed in int32 (exact for any weights), float32 in fp32.
 template <bool FLOAT>
 __global__ void __launch_bounds__(256) fw_diag_kernel(int *d, int64_t ld, int64_t n, int64_t kb, const int *run_if) {
+  pdl_wait();
+  pdl_trigger();
   if (run_if && !*run_if) return;
   __shared__ __align__(16) int buf[512];
   const int64_t kb0 = kb * kBM;
@@ -36,9 +38,9 @@ __global__ void __launch_bounds__(256) fw_diag_kernel(int *d, int64_t ld, int64_
 
 int launch_fw_diag(void *d, int64_t ld, int64_t n, int64_t kb, int dtype, cudaStream_t s, const int *run_if) {
   if (dtype == APSP_I32)
-    fw_diag_kernel<false><<<1, 256, 0, s>>>(reinterpret_cast<int *>(d), ld, n, kb, run_if);
+    launch_pdl(fw_diag_kernel<false>, 1, 256, 0, s, reinterpret_cast<int *>(d), ld, n, kb, run_if);
   else
-    fw_diag_kernel<true><<<1, 256, 0, s>>>(reinterpret_cast<int *>(d), ld, n, kb, run_if);
+    launch_pdl(fw_diag_kernel<true>, 1, 256, 0, s, reinterpret_cast<int *>(d), ld, n, kb, run_if);
   APSP_LAUNCH_CHECK();
   return APSP_OK;
 }
@@ -100,6 +102,8 @@ constexpr int64_t kFusedMaxBlocks = 80;
 // w = words[0]: the largest weight of the whole graph (the exact bound); c = *cert: the largest
 // finite entry of the block being closed (the certificates' step bound).
 __global__ void fw_decide_kernel(int *words, const int *cert, int may24, int64_t mult) {
+  pdl_wait();
+  pdl_trigger();
   const int w = words[0], c = *cert;
   const int use16 = c <= kUse16MaxWeight;
   words[4] = use16;
@@ -115,6 +119,8 @@ __global__ void fw_decide_kernel(int *words, const int *cert, int may24, int64_t
 __global__ void __launch_bounds__(256) fw_pack16_kernel(const int *d, int64_t ld, int64_t n, int64_t kb0, int bw,
                                                         int *A16, int64_t lda16, int *B16, int64_t ldb16,
                                                         const int *words) {
+  pdl_wait();
+  pdl_trigger();
   if (!words[4]) return;
   const int kw = (bw + 1) >> 1;
   const int64_t na = n * kw, total = na + (int64_t)kw * n;
@@ -145,6 +151,8 @@ __device__ __forceinline__ int cap_in_use(const int *words) {
 // words[5] = largest stored value below the cap in use, and every entry at or above it becomes
 // the sentinel (nothing when the closure ran exact).
 __global__ void __launch_bounds__(256) trunc_certify_kernel(int *d, int64_t ld, int64_t n, int inf, int *words) {
+  pdl_wait();
+  pdl_trigger();
   const int cap = cap_in_use(words);
   if (!cap) return;
   int m = 0;
@@ -162,15 +170,17 @@ __global__ void __launch_bounds__(256) trunc_certify_kernel(int *d, int64_t ld, 
 // words[6] = 1 when the largest stored value below the cap plus the step bound *cert reaches the
 // cap (the truncated result cannot be certified).
 __global__ void trunc_verdict_kernel(int *words, const int *cert) {
+  pdl_wait();
+  pdl_trigger();
   const int cap = cap_in_use(words);
   words[6] = cap && (int64_t)words[5] + (int64_t)*cert >= cap;
 }
 
 static int certify(void *d, int64_t ld, int64_t n, int inf, int *words, const int *cert, cudaStream_t s) {
   const int64_t grid = std::min<int64_t>(n, (int64_t)sm_count() * 8);
-  trunc_certify_kernel<<<(int)grid, 256, 0, s>>>(reinterpret_cast<int *>(d), ld, n, inf, words);
+  launch_pdl(trunc_certify_kernel, (int)grid, 256, 0, s, reinterpret_cast<int *>(d), ld, n, inf, words);
   APSP_LAUNCH_CHECK();
-  trunc_verdict_kernel<<<1, 1, 0, s>>>(words, cert);
+  launch_pdl(trunc_verdict_kernel, 1, 1, 0, s, words, cert);
   APSP_LAUNCH_CHECK();
   return APSP_OK;
 }
@@ -284,7 +294,7 @@ int fw_closure(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bound b, cu
     return fw_loop(d, n, ld, dtype, mA, mB, mC, p, nullptr, s, 0, nb <= kFusedMaxBlocks ? b.counters : nullptr);
   int *words = const_cast<int *>(b.w);
   const int *cert = b.cert ? b.cert : b.w;
-  fw_decide_kernel<<<1, 1, 0, s>>>(words, cert, inf_i > kCap24, b.mult);
+  launch_pdl(fw_decide_kernel, 1, 1, 0, s, words, cert, (int)(inf_i > kCap24), b.mult);
   APSP_LAUNCH_CHECK();
   if ((r = fw_wide_pass(d, n, ld, dtype, inf_i, b, s, panels16, p, mA, mB, mC))) return r;
   if ((r = certify(d, ld, n, inf_i, words, cert, s))) return r;
@@ -343,14 +353,16 @@ static int fw_wide_pass(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bo
         if ((r = launch_tgemm(kModeFwPanels, false, dtype, mA, mB, mC, pp, s))) return r;
       }
     } else {
-      // Phase 1: close the diagonal block (itself a small blocked Floyd-Warshall, exact).
+      // Phase 1: close the diagonal block (itself a small blocked Floyd-Warshall, exact), with
+      // the next tile's phases 1 and 2 inside each phase-3 launch when the counters are there
+      // (four launches for a two-tile block instead of six).
       CUtensorMap dA, dB, dC;
       if ((r = make_operand_maps(sub, bw, bw, ld, dtype, &dA, &dB, &dC))) return r;
       TileProblem ps = p;
       ps.n = bw;
       ps.nb = cdiv(bw, kBM);
       ps.C = sub;
-      if ((r = fw_loop(sub, bw, ld, dtype, dA, dB, dC, ps, nullptr, s, kTraceSide))) return r;
+      if ((r = fw_loop(sub, bw, ld, dtype, dA, dB, dC, ps, nullptr, s, kTraceSide, b.counters))) return r;
       // Phase 2: the row panel becomes D* (x) (row panel) and the column panel (column panel) (x)
       // D*; D* is closed, so its zero diagonal keeps the old entry and the block's own entries
       // are reproduced (D* (x) D* = D*).  With the 16-bit pass in use (words[4]) both products
@@ -358,8 +370,8 @@ static int fw_wide_pass(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bo
       // folded as min(old entry, capped product) like phase 3.  In the 32-bit alternative
       // (words[7]) each is one exact product read from an int32 copy of its panel.
       const int64_t work = 2 * n * ((bw + 1) >> 1);
-      fw_pack16_kernel<<<(int)std::min<int64_t>(cap, cdiv(work, 256)), 256, 0, s>>>(D, ld, n, kb0, (int)bw, A16,
-                                                                                    lda16, B16, ldb16, words);
+      launch_pdl(fw_pack16_kernel, (int)std::min<int64_t>(cap, cdiv(work, 256)), 256, 0, s, D, ld, n, kb0, (int)bw,
+                 A16, lda16, B16, ldb16, words);
       APSP_LAUNCH_CHECK();
       if ((r = panels16_truncated(D, ld, n, kb0, bw, A16, lda16, B16, ldb16, p, words, s))) return r;
       const int *alt = words + 7;
@@ -372,8 +384,8 @@ static int fw_wide_pass(void *d, int64_t n, int64_t ld, int dtype, int inf_i, Bo
     // Phase 3, K = bw: on the packed panels, or the 32-bit alternative.
     if (bt > 1) {
       const int64_t work = 2 * n * ((bw + 1) >> 1);
-      fw_pack16_kernel<<<(int)std::min<int64_t>(cap, cdiv(work, 256)), 256, 0, s>>>(D, ld, n, kb0, (int)bw, A16,
-                                                                                    lda16, B16, ldb16, words);
+      launch_pdl(fw_pack16_kernel, (int)std::min<int64_t>(cap, cdiv(work, 256)), 256, 0, s, D, ld, n, kb0, (int)bw,
+                 A16, lda16, B16, ldb16, words);
       APSP_LAUNCH_CHECK();
     }
     const int64_t ec = std::min<int64_t>(bt, nt - kbb * bt), rest = nt - ec;

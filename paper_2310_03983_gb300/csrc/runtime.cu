@@ -1,6 +1,7 @@
 // runtime.cu -- host runtime of libapsp: status word, device queries, TMA descriptor
 // encoding, sentinel handling and the small C-ABI helpers.
 #include <atomic>
+#include <cstdlib>
 #include <math.h>
 #include <mutex>
 #include <string.h>
@@ -36,6 +37,14 @@ int sm_count() {
     cached[dev].store(v, std::memory_order_relaxed);
   }
   return v;
+}
+
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char *e = std::getenv("APSP_PDL");
+    return !(e && e[0] == '0' && e[1] == 0);
+  }();
+  return on;
 }
 
 // Library workspace pool: a stream-ordered memory pool per device that keeps freed blocks

@@ -462,6 +462,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     tgemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
                  const __grid_constant__ CUtensorMap mC, const __grid_constant__ TileProblem p,
                  const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mB2) {
+  pdl_wait();  // the previous kernel on the stream has completed (programmatic launch)
+  pdl_trigger();
   if ((p.skip && *p.skip) || (p.run_if && !*p.run_if)) return;  // uniform, before any barrier exists
   const bool alt = MODE == kModeFwRest16 && !G && p.alt_if && *p.alt_if;  // uniform
   extern __shared__ uint8_t smem_raw[];
@@ -615,7 +617,7 @@ static int launch_one(const CUtensorMap &mA, const CUtensorMap &mB, const CUtens
   void *ev = nullptr;
   const bool tr = trace_on() && !p.no_trace;
   if (tr) trace_begin(s, &ev);
-  k<<<grid, kThreads, kSmemBytes + 1024, s>>>(mA, mB, mC, p, mA2, mB2);
+  launch_pdl(k, grid, kThreads, kSmemBytes + 1024, s, mA, mB, mC, p, mA2, mB2);
   APSP_LAUNCH_CHECK();
   if (tr) trace_end(s, ev, MODE + p.trace_class, algorithmic_pairs<MODE>(p));
   return APSP_OK;
@@ -677,6 +679,8 @@ __device__ __forceinline__ int cap16(int v, int inf) { return v >= inf ? kCap16 
 
 __global__ void __launch_bounds__(256) pack16_a_kernel(const int *A, int64_t lda, int64_t M, int64_t K, int *A16,
                                                        int64_t ld16, int inf, int *words) {
+  pdl_wait();
+  pdl_trigger();
   if (!fits16(words)) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) words[4] = 1;
   const int64_t kw = (K + 1) >> 1;
@@ -693,6 +697,8 @@ __global__ void __launch_bounds__(256) pack16_a_kernel(const int *A, int64_t lda
 
 __global__ void __launch_bounds__(256) pack16_b_kernel(const int *B, int64_t ldb, int64_t K, int64_t N, int *B16,
                                                        int64_t ld16, int inf, int *words) {
+  pdl_wait();
+  pdl_trigger();
   if (!fits16(words)) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) words[4] = 1;
   const int64_t kw = (K + 1) >> 1;
@@ -711,7 +717,7 @@ int launch_pack16_a(const int *A, int64_t lda, int64_t M, int64_t K, int *A16, i
                     cudaStream_t s) {
   if (M == 0 || K == 0) return APSP_OK;
   const int64_t cap = (int64_t)sm_count() * 8;
-  pack16_a_kernel<<<(int)(M < cap ? M : cap), 256, 0, s>>>(A, lda, M, K, A16, ld16, inf, words);
+  launch_pdl(pack16_a_kernel, (int)(M < cap ? M : cap), 256, 0, s, A, lda, M, K, A16, ld16, inf, words);
   APSP_LAUNCH_CHECK();
   return APSP_OK;
 }
@@ -721,7 +727,7 @@ int launch_pack16_b(const int *B, int64_t ldb, int64_t K, int64_t N, int *B16, i
   const int64_t kw = (K + 1) >> 1;
   if (kw == 0 || N == 0) return APSP_OK;
   const int64_t cap = (int64_t)sm_count() * 8;
-  pack16_b_kernel<<<(int)(kw < cap ? kw : cap), 256, 0, s>>>(B, ldb, K, N, B16, ld16, inf, words);
+  launch_pdl(pack16_b_kernel, (int)(kw < cap ? kw : cap), 256, 0, s, B, ldb, K, N, B16, ld16, inf, words);
   APSP_LAUNCH_CHECK();
   return APSP_OK;
 }
@@ -791,6 +797,8 @@ int launch_tgemm_generic(void *C, const void *A, const void *B, int64_t M, int64
 // ------------------------------------ copy --------------------------------------------
 __global__ void __launch_bounds__(256) copy2d_kernel(int *dst, int64_t ldd, const int *src, int64_t lds, int64_t rows,
                                                      int64_t cols, bool vec, const int *run_if) {
+  pdl_wait();
+  pdl_trigger();
   if (run_if && !*run_if) return;
   for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
     const int *s = src + r * lds;
@@ -811,8 +819,8 @@ int launch_copy2d(void *dst, int64_t ldd, const void *src, int64_t lds, int64_t 
   const bool vec = reinterpret_cast<uintptr_t>(dst) % 16 == 0 && reinterpret_cast<uintptr_t>(src) % 16 == 0 &&
                    ldd % 4 == 0 && lds % 4 == 0;
   const int64_t cap = (int64_t)sm_count() * 8;
-  copy2d_kernel<<<(int)(rows < cap ? rows : cap), 256, 0, s>>>((int *)dst, ldd, (const int *)src, lds, rows, cols, vec,
-                                                               run_if);
+  launch_pdl(copy2d_kernel, (int)(rows < cap ? rows : cap), 256, 0, s, (int *)dst, ldd, (const int *)src, lds, rows,
+             cols, vec, run_if);
   APSP_LAUNCH_CHECK();
   return APSP_OK;
 }

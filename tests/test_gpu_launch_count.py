@@ -9,8 +9,10 @@ entry point documents, so the figure the bench prints is tied to the code that l
     per block);
   * blocked FW, int32 from n = 4096: a1, the decision, then the pass: with 128-vertex blocks
     phases 1 and 2 of block 0 and one launch per block as above (phase 3 on 16-bit pairs or its
-    32-bit alternative; the panel tiles also leave the packed operands) or, from n = 16384, 15
-    per 256-vertex block (the block's own closure as two 3-phase sub-steps; packing of the
+    32-bit alternative; the panel tiles also leave the packed operands) or, from n = 16384, 13
+    per 256-vertex block (the block's own closure in four launches: the first tile's diagonal
+    closure and panels, then one phase-3 launch per tile, the first of which also closes the
+    second tile and computes its panels; packing of the
     panels, the two truncated 16-bit panel products; the two panel copies and two exact panel
     products of the 32-bit alternative, which return at once when the 16-bit pass is in use;
     packing of the finished panels; phase 3); the certificate (2); then the exact int32 loop as
@@ -65,7 +67,7 @@ def test_fw_plain_launches(apsp, n, dtype):
 @pytest.mark.parametrize("n", [4096, 16384])
 def test_fw16_launches(apsp, n):
     nb = -(-n // 128)
-    wide_pass = 15 * -(-n // 256) if n >= 16384 else 2 + nb
+    wide_pass = 13 * -(-n // 256) if n >= 16384 else 2 + nb
     int32_pass = 2 + nb if nb <= 80 else 3 * nb
     assert _fw_count(apsp, n, "int32") == 4 + wide_pass + int32_pass
 
