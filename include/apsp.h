@@ -26,7 +26,12 @@
  *    stronger, checkable condition).  A negative entry, or a NaN, is a data error.
  *  - stream: a cudaStream_t passed as void* (NULL = the legacy default stream).  Every call
  *    is asynchronous on that stream and may be captured into a CUDA graph provided the
- *    caller supplies the workspace (ws != NULL).
+ *    caller supplies the workspace (ws != NULL).  The kernels of the closures and products
+ *    are launched with programmatic dependent launch: the next kernel's blocks may be
+ *    scheduled while the previous kernel on the stream drains, and each waits for it to
+ *    complete before touching memory, so stream order holds for the caller's work as well.
+ *    Setting the environment variable APSP_PDL=0 before the first call launches them
+ *    without that attribute.
  *  - ws / ws_bytes: caller workspace in device memory (256-byte aligned, at least the size
  *    reported by the matching *_workspace_bytes function).  ws == NULL makes the library
  *    allocate it on `stream` from its own stream-ordered pool and free it after the work
