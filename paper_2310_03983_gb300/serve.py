@@ -25,7 +25,7 @@ from __future__ import annotations
 import bisect
 import collections
 import time
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import numpy as np
 

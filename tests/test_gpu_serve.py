@@ -4,7 +4,6 @@ Every served result must equal the same request closed alone (int32 bit-exact; f
 1e-5 relative, in fact identical because the plan depends only on the request), a sample must
 match the oracle, the arena must never exceed its budget, and both kinds of launch (batched and
 solo) must occur."""
-import numpy as np
 import pytest
 import torch
 

@@ -113,7 +113,6 @@ class _NumpyHostArena:
 def test_feeder_makes_every_request_within_the_arena():
     """The feeder makes each request's matrix (in arrival order, on worker threads) into the
     host arena, waits for room when the arena is full, and the matrices are the request's own."""
-    import threading
     import workloads
     from paper_2310_03983_gb300.serve import Feeder, stream_requests
     pool = workloads.RequestPool(seed=1, size_u=1 << 20, size_w=1 << 18, threads=2)

@@ -11,7 +11,6 @@ This file is named to be collected last.
 """
 import ctypes
 
-import numpy as np
 import pytest
 import torch
 
